@@ -1,0 +1,324 @@
+"""Benchmark: voxel-iterations/s of the filtered-property FFT homogenisation hot path on GB300.
+
+Workload (one "step"): the 2D resolution sweep of the centred-disk cell -- grids 45, 135, 405
+and 1215 per side, contrasts 10 and 0.1, no filter / Voigt / Reuss / 2-layer filters (radius 1
+pixel, 16x16 subgrid), 3 unit Mandel load cases -- i.e. 32 cells x 3 loads.  A step runs the
+whole path: filter build (classification, subgrid sampling, homogenisation rule), the
+fixed-point solve of every cell and load to convergence, and C_eff.  The FP32 form batches all
+96 (cell, load) problems in one launch sequence (FP32 fields and FFTs, FP64 reductions); the
+FP64 plain form solves one cell at a time in FP64.  Both stop on e_n < 1e-6.
+
+value = sum over (cell, load) of n^2 * iterations, divided by the step time (FP32 batched).
+Inputs are synthetic (seeded geometry; no dataset).  The working set (~1.8 GB of state) is
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hom_inputs as H  # noqa: E402
+
+SIZES = (45, 135, 405, 1215)
+CONTRASTS = (10.0, 0.1)
+RULES = (H.RULE_NONE, H.RULE_VOIGT, H.RULE_REUSS, H.RULE_TWO_LAYER)
+TOL = 1e-6
+MAX_ITER = 3000
+METRIC = "voxel-iterations/s (2D resolution sweep, FP32 batched, e_n < 1e-6)"
+UNIT = "voxel-it/s"
+
+
+def workload():
+    cells, phases = H.resolution_sweep_cells(SIZES, CONTRASTS, RULES, vf=0.2, radius_px=1.0, subgrid=16)
+    c0 = []
+    for cell in cells:
+        pair = phases[cell.matrix_phase:cell.matrix_phase + 2]
+        c0.append(H.mean_lame(pair))
+    return cells, phases, np.array(c0)
+
+
+def config_dict(extra=None):
+    d = {"workload": "2D centred-disk resolution sweep: n in %s, contrasts %s, filters none/Voigt/Reuss/2-layer "
+                     "(r = 1 px, S = 16), 3 Mandel unit loads, 32 cells x 3 loads per step" % (list(SIZES), list(CONTRASTS)),
+         "tolerance": "e_n < %g" % TOL, "l2": "working set > L2 (no flush needed)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.stop = threading.Event()
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.stop.is_set():
+                break
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        self.stop.set()
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for name, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def golden_ceff():
+    p = os.path.join(ROOT, "tests", "golden", "sweep2d_ceff.json")
+    if not os.path.exists(p):
+        return {}
+    return {(e["n"], e["contrast"], e["rule"]): np.array(e["ceff"]) for e in json.load(open(p))["cells"]}
+
+
+def ceff_errors(cells, phases, mean_sigma, gold):
+    import paper_1412_3228_gb300 as hom
+    C = hom.hom_effective_stiffness(np.eye(3), mean_sigma, 2)
+    errs = []
+    for i, cell in enumerate(cells):
+        contrast = round(phases[cell.matrix_phase + 1][1] / phases[cell.matrix_phase][1], 6)
+        key = (cell.n, contrast, H.RULE_NAMES[cell.rule])
+        if key in gold:
+            g = gold[key]
+            errs.append(float(np.abs(C[i] - g).max() / np.abs(g).max()))
+    return (max(errs) if errs else None), len(errs)
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1412_3228_gb300 as hom
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cells, phases, c0 = workload()
+    E = np.eye(3)
+    stream = torch.cuda.current_stream()
+
+    def step(stats=False, precision=hom.HOM_FP32, host_fields=False, fields=False, subset=None):
+        cs = cells if subset is None else [cells[i] for i in subset]
+        cc = c0 if subset is None else c0[subset]
+        mat = hom.hom_filter_build(cs, phases)
+        r = hom.hom_solve(mat, E, cc, precision=precision, criterion=hom.HOM_CRIT_EN, tol=TOL, max_iter=MAX_ITER,
+                          fields=fields, host_fields=host_fields, stats=stats)
+        C = hom.hom_effective_stiffness(E, r["mean_sigma"], 2)
+        return r, C
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    # ---- timed region: K steps of the FP32 batched form, per-kernel events on the launch stream
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    vox_it = 0.0
+    kstats = {}
+    launches = 0
+    with ClockSampler(dev.index) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            r, C = step(stats=True)
+            vox_it += float(np.sum([[c.n ** 2 * it for it in r["iterations"][i]] for i, c in enumerate(cells)]))
+            for k, v in r["stats"].items():
+                s = kstats.setdefault(k, dict(launches=0, ms=0.0, bytes=0.0))
+                s["launches"] += v["launches"]
+                s["ms"] += v["ms"]
+                s["bytes"] += v["bytes"]
+            launches += sum(v["launches"] for v in r["stats"].values()) + 1  # + the filter-build kernel
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], device=dev)
+    vi_t = torch.tensor([vox_it], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(vi_t, op=torch.distributed.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    value = float(vi_t.item()) / (ms_max / 1e3)
+    fp32_err, ncmp = ceff_errors(cells, phases, r["mean_sigma"], golden_ceff())
+    iters = r["iterations"]
+
+    # ---- end to end: the public API with host outputs (fields and C_eff back on the host)
+    e2e_ms, e2e_vi, d2h = 0.0, 0.0, 0
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        re_, Ce = step(host_fields=True, fields=True)
+        e2e_vi += float(np.sum([[c.n ** 2 * it for it in re_["iterations"][i]] for i, c in enumerate(cells)]))
+        d2h = (re_["eps"].numel() + re_["sigma"].numel()) * re_["eps"].element_size() + re_["mean_sigma"].nbytes + \
+            re_["iterations"].nbytes * 2 + re_["err"].nbytes * 2
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - te) * 1e3 / max(1, args.steps)
+    h2d = sum(48 * len(c.prims) + 40 for c in cells) + 16 * len(phases) + 8 * E.size + 16 * len(cells)
+
+    # ---- FP64 plain form: one cell at a time, FP64 everywhere (one untimed warm-up pass first)
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        for i in range(len(cells)):
+            step(precision=hom.HOM_FP64, subset=[i])
+        torch.cuda.synchronize()
+        tf = time.perf_counter()
+        ms64, vi64, ms_f64 = 0.0, 0.0, []
+        for i in range(len(cells)):
+            r64, C64 = step(precision=hom.HOM_FP64, subset=[i])
+            vi64 += float(sum(cells[i].n ** 2 * it for it in r64["iterations"][0]))
+            ms_f64.append(r64["mean_sigma"][0])
+        torch.cuda.synchronize()
+        ms64 = (time.perf_counter() - tf) * 1e3
+        err64, _ = ceff_errors(cells, phases, np.array(ms_f64), golden_ceff())
+        fp64 = {"value": vi64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "ceff_max_rel_err": err64}
+
+    # ---- roofline of the dominant kernel (largest share of kernel time)
+    peak, peak_kind = measured_peak_hbm()
+    dom = max((k for k in kstats if k in ("row", "green", "yfwd", "yinv")), key=lambda k: kstats[k]["ms"])
+    ach = kstats[dom]["bytes"] / (kstats[dom]["ms"] / 1e3) / 1e9
+    total_kms = sum(v["ms"] for v in kstats.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": peak_kind,
+                "traffic": None,
+                "bytes_per_launch": kstats[dom]["bytes"] / max(1, kstats[dom]["launches"]),
+                "kernel_share": {k: round(v["ms"] / total_kms, 4) for k, v in kstats.items() if v["ms"] > 0},
+                "achieved_gbs": {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) for k, v in kstats.items()
+                                 if v["ms"] > 0 and v["bytes"] > 0}}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 reductions)", "data": "synthetic",
+            "config": config_dict({"parallelism": "replicas x%d (independent cells per rank)" % world,
+                                   "cells": len(cells), "loads": 3}),
+            "e2e": {"value": e2e_vi / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk.summary(),
+            "iterations": {"max": int(iters.max()), "min": int(iters.min()),
+                           "per_rule": {H.RULE_NAMES[rr]: int(np.mean([iters[i].mean() for i, c in enumerate(cells)
+                                                                        if c.rule == rr])) for rr in RULES}},
+            "ceff_max_rel_err_vs_oracle": fp32_err, "ceff_cells_compared": ncmp,
+            "fp64_plain": fp64}
+    if rank == 0 and not args.skip_cpu:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+def cpu_baseline(args, iters=4):
+    """The oracle as it stands, on a bounded sample of the workload: the 405^2 Voigt cell
+    (contrast 10), 3 loads x `iters` fixed iterations, plus its filter build."""
+    import oracle as O
+    cells, phases, c0 = workload()
+    idx = [i for i, c in enumerate(cells) if c.n == 405 and c.rule == H.RULE_VOIGT][0]
+    cell = cells[idx]
+    t = time.perf_counter()
+    fb = O.filter_build(cell, phases)
+    O.solve(fb["ctilde"], 2, cell.n, c0[idx][0], c0[idx][1], np.eye(3), tol=-1.0, max_iter=iters)
+    dt = time.perf_counter() - t
+    vi = cell.n ** 2 * iters * 3
+    return {"value": vi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "405^2 Voigt cell, contrast 10: filter build + 3 loads x %d iterations (%.1f s)" % (iters, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
+    import oracle as O  # noqa: F401
+    for _ in range(args.warmup):
+        cpu_baseline(args, iters=2)
+    t = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, iters=2))
+    dt = time.perf_counter() - t
+    value = float(np.mean([v["value"] for v in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

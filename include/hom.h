@@ -1,0 +1,243 @@
+/*
+ * hom.h -- C ABI of the GB300 library for FFT-based homogenisation of periodic elastic cells
+ * with filtered material properties (L. Gelebart and F. Ouaki, "Filtering material properties
+ * to improve FFT-based methods for numerical homogenization", arXiv 1412.3228).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a):
+ *   1. the per-voxel filtered stiffness c~(x_a) = HR(c, w(x_a)) of section 2: phase volume
+ *      fractions inside a ball of radius r pixels around each grid point, counted on a refined
+ *      grid, combined by the Voigt (eq. 3), Reuss (eq. 4) or 2-layer (eqs. 5-a, 5-b) rule;
+ *   2. the basic fixed-point scheme of section 2 (eqs. 1-a, 1-b, 2): tau = (c~ - c0):eps,
+ *      forward real FFT, Green operator Gamma0 on the truncated odd frequency set J with
+ *      eps_hat(0) = E, inverse FFT, stress-equilibrium check -- for many cells and load cases
+ *      at once;
+ *   3. the effective stiffness C_eff from the volume-averaged stresses;
+ *   4. the adjoint (reverse-mode) derivative of a loss on C_eff and on the local stresses.
+ *
+ * Conventions shared by every call
+ *   - Grids are odd, n voxels per side, n = 3^a 5^b 7^c, 3 <= n <= 2187.  The cell side is 1 and
+ *     the grid points are voxel centres x_a = (a + 1/2)/n.
+ *   - Strains, stresses and stiffnesses use Mandel notation: 2D (plane strain) vectors hold
+ *     (11, 22, sqrt2*12), nc = 3; 3D vectors hold (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
+ *     nc = 6.  A stiffness is an nc x nc symmetric matrix stored "packed": its upper triangle
+ *     row by row, ns = nc(nc+1)/2 values (6 in 2D, 21 in 3D).
+ *   - Real per-voxel fields are laid out [cell][load][component][z][y][x], x fastest; cells are
+ *     concatenated in the order given.  A cell's voxel offset is the sum of n^dim over the
+ *     cells before it.
+ *   - Every call is asynchronous on the given CUDA stream (NULL = legacy default stream) unless
+ *     stated otherwise.  Pointers documented "host or device" may be either (unified
+ *     addressing); pointers documented "device" must be device memory of the current device.
+ *   - Caller-owned buffers are never freed by the library.  The library owns only cached FFT
+ *     plans and solver workspace, which hom_release() frees.
+ *   - Every function returns an int status: HOM_OK or one of the HOM_ERR_* codes below; the
+ *     message of the last failure on the calling host thread is given by hom_last_error().
+ *     No C++ exception crosses this interface.  The library is not re-entrant: calls that use
+ *     the solver workspace must not run concurrently from several host threads.
+ */
+#ifndef HOM_H
+#define HOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define HOM_OK 0
+#define HOM_ERR_INVALID_ARG 1       /* a pointer, size or option is invalid                   */
+#define HOM_ERR_UNSUPPORTED_SIZE 2  /* even n, a prime factor other than 3, 5, 7, n too large  */
+#define HOM_ERR_NOT_CONVERGED 3     /* some load case hit max_iter; every output is still set  */
+#define HOM_ERR_DIVERGED 4          /* some load case diverged (non-finite or growing error)  */
+#define HOM_ERR_TIMEOUT 5           /* a device-side wait ran out of its budget               */
+#define HOM_ERR_CUDA 6              /* a CUDA runtime call failed (message has the detail)    */
+#define HOM_ERR_OOM 7               /* workspace allocation failed                            */
+#define HOM_ERR_CAPACITY 8          /* mixed-voxel table too small; mixed_count = needed size */
+#define HOM_ERR_NOT_IMPL 9          /* requested combination is not implemented               */
+
+/* ------------------------------------------------------------------ enumerations */
+#define HOM_PRIM_DISK 0    /* 2D disk: centre[0..1], radius                                     */
+#define HOM_PRIM_SPHERE 1  /* 3D sphere: centre[0..2], radius                                   */
+#define HOM_PRIM_SLAB 2    /* slab of full thickness `radius` normal to axis `axis`, centred at */
+                           /* centre[axis] (periodic)                                           */
+
+#define HOM_RULE_NONE 0      /* c~(x_a) = c(x_a): phase of the grid point itself               */
+#define HOM_RULE_VOIGT 1     /* eq. (3): sum_i f_i c_i                                          */
+#define HOM_RULE_REUSS 2     /* eq. (4): (sum_i f_i c_i^-1)^-1                                  */
+#define HOM_RULE_TWO_LAYER 3 /* eqs. (5-a), (5-b): two-phase laminate with the interface normal */
+
+#define HOM_FP32 0 /* FP32 fields, FFTs and Green operator; FP64 residual norm and averages   */
+#define HOM_FP64 1 /* FP64 everywhere                                                          */
+
+#define HOM_CRIT_E 0  /* e   = sqrt(sum_k |xi_k . sigma_hat(k)|^2) / ||sigma_hat(0)||          */
+#define HOM_CRIT_EN 1 /* e_n = sqrt(sum_{k!=0} |(xi_k/|xi_k|) . sigma_hat(k)|^2) / ||sigma_hat(0)|| */
+
+#define HOM_STATUS_CONVERGED 0
+#define HOM_STATUS_MAX_ITER 1
+#define HOM_STATUS_DIVERGED 2
+
+#define HOM_MIXED_BIT 0x80000000u /* label bit: the voxel's stiffness is in the mixed table   */
+
+/* ------------------------------------------------------------------ inputs */
+
+/* One analytic inclusion of a cell (cell units, periodic).  A fine-grid sample belongs to the
+ * first primitive of the cell's list that contains it, else to the cell's matrix phase.
+ * Disks/spheres need radius + filter radius < 1/2 of the cell; slabs need thickness < 1. */
+typedef struct hom_primitive {
+  int32_t kind;      /* HOM_PRIM_*                                          */
+  int32_t phase;     /* index into the phase table of the call              */
+  int32_t axis;      /* slab normal axis (0 = x, 1 = y, 2 = z)              */
+  int32_t reserved;  /* must be 0                                           */
+  double centre[3];  /* centre in cell units; centre[2] ignored in 2D       */
+  double radius;     /* disk/sphere radius, or slab full thickness          */
+} hom_primitive;
+
+/* A periodic unit cell on an n^dim grid with its filter (section 2).  radius_px is the filter
+ * radius in voxel units (0.5 = circle inscribed in a pixel); subgrid S is the refinement of the
+ * grid on which indicator functions are averaged: the fine points are (j + 1/2)/(S n) per axis
+ * and a fine point is inside the ball of voxel a when its distance to x_a is <= radius_px / n. */
+typedef struct hom_cell {
+  int32_t dim;          /* 2 or 3                                                 */
+  int32_t n;            /* voxels per side (odd, 3^a 5^b 7^c)                     */
+  int32_t matrix_phase; /* phase of points outside every primitive                */
+  int32_t rule;         /* HOM_RULE_*                                             */
+  double radius_px;     /* filter radius in voxel units, 0 < radius_px <= (n-1)/2 */
+  int32_t subgrid;      /* S, 1 <= S <= 64                                        */
+  int32_t nprim;        /* number of primitives                                   */
+  const hom_primitive* prims; /* host array of nprim primitives                   */
+} hom_cell;
+
+/* Isotropic phase given by its Lame constants (3D moduli; 2D cells are plane strain). */
+typedef struct hom_phase {
+  double lambda;
+  double mu;
+} hom_phase;
+
+/* ------------------------------------------------------------------ filtered material */
+
+/* Filtered stiffness field of a batch of cells, written by hom_filter_build into caller-owned
+ * device buffers.  Each voxel has a 32-bit label: a phase index (the voxel's filter ball holds a
+ * single phase, c~ = c_phase exactly), or HOM_MIXED_BIT | m where m indexes the mixed table.
+ * For every mixed entry m:  c64/c32[m*ns .. m*ns+ns) packed c~ (FP64 and the same values
+ * rounded to FP32), phases[2m], phases[2m+1] the two phases a < b present, frac[m] the volume
+ * fraction of phase b, normal[3m..3m+3) the interface normal used by the 2-layer rule (zeros for
+ * other rules), voxel[m] the global voxel index.  Mixed entries are in no particular order. */
+typedef struct hom_material {
+  uint32_t* label;          /* device [sum_c n_c^dim]                             */
+  double* mixed_c64;        /* device [mixed_capacity * ns]                       */
+  float* mixed_c32;         /* device [mixed_capacity * ns]                       */
+  int32_t* mixed_phases;    /* device [mixed_capacity * 2]                        */
+  double* mixed_frac;       /* device [mixed_capacity]                            */
+  double* mixed_normal;     /* device [mixed_capacity * 3]                        */
+  int64_t* mixed_voxel;     /* device [mixed_capacity]                            */
+  int64_t mixed_capacity;   /* entries available in the mixed arrays              */
+  double* phase_c64;        /* device [nphase * ns]: packed c of every phase      */
+  float* phase_c32;         /* device [nphase * ns]                               */
+  int32_t nphase;           /* number of phases                                   */
+  int32_t dim;              /* set by hom_filter_build                            */
+  int64_t mixed_count;      /* set by hom_filter_build (host-visible on return)   */
+} hom_material;
+
+/* ------------------------------------------------------------------ solver options / outputs */
+
+typedef struct hom_solve_opts {
+  int32_t precision;      /* HOM_FP32 or HOM_FP64                                       */
+  int32_t criterion;      /* HOM_CRIT_E or HOM_CRIT_EN                                  */
+  double tol;             /* stop when the chosen error < tol                           */
+  int32_t max_iter;       /* maximum number of Green-operator applications              */
+  int32_t check_every;    /* iterations launched between host polls (>= 1; 0 = default) */
+  int32_t diverge_window; /* consecutive error increases that flag divergence (0 = off)  */
+  int32_t use_graph;      /* 1: replay each poll interval as a captured CUDA graph       */
+} hom_solve_opts;
+
+/* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every
+ * launch; the call then synchronises the stream before returning). */
+#define HOM_NKERNEL 8
+#define HOM_K_FILTER 0   /* filter build (classification, sampling, rule)                */
+#define HOM_K_ROW 1      /* row pass: inverse x-FFT, constitutive, forward x-FFT          */
+#define HOM_K_YFWD 2     /* 3D: forward y-FFT pass                                        */
+#define HOM_K_GREEN 3    /* last-axis pass: forward FFT, Green operator, residual, inverse */
+#define HOM_K_YINV 4     /* 3D: inverse y-FFT pass                                        */
+#define HOM_K_CONTROL 5  /* convergence control and FP64 reductions                       */
+#define HOM_K_OUTPUT 6   /* final real fields                                             */
+#define HOM_K_INIT 7     /* initial state                                                 */
+typedef struct hom_kernel_stats {
+  int64_t launches[HOM_NKERNEL];
+  double ms[HOM_NKERNEL];      /* summed CUDA-event durations of the launches              */
+  double bytes[HOM_NKERNEL];   /* algorithmic HBM bytes of the work the launches performed */
+  double voxel_iterations;     /* sum over (cell, load) of n^dim * iterations               */
+} hom_kernel_stats;
+
+/* Outputs of hom_solve (all caller-owned). */
+typedef struct hom_result {
+  void* eps;            /* optional, host or device: real strain field of the returned iterate,
+                           [cell][load][nc][voxels], float (HOM_FP32) or double (HOM_FP64)   */
+  void* sigma;          /* optional, same layout: stress field c~ : eps                         */
+  double* mean_sigma;   /* required, host or device [ncells][L][nc]: <sigma> (FP64)            */
+  int32_t* iterations;  /* optional host [ncells*L]: Green-operator applications performed     */
+  int32_t* status;      /* optional host [ncells*L]: HOM_STATUS_*                              */
+  double* err;          /* optional host [ncells*L]: e of the returned iterate                  */
+  double* err_n;        /* optional host [ncells*L]: e_n of the returned iterate                */
+  hom_kernel_stats* stats; /* optional host: per-kernel timing                                  */
+} hom_result;
+
+/* ------------------------------------------------------------------ entry points */
+
+/* Filtered stiffness of every voxel of every cell (section 2, "Filtering mechanical
+ * properties"; eqs. 3, 4, 5-a, 5-b).
+ *   cells/ncells    host array of cells, all of the same dim
+ *   phases/nphase   host phase table; primitives and matrices index into it
+ *   mat             caller-owned outputs (see hom_material); mat->nphase must equal nphase
+ *   stream          cudaStream_t or NULL
+ * Volume fractions are exact sample counts on the refined grid (integer arithmetic plus a fixed
+ * sequence of IEEE FP64 operations, no fused multiply-add), so they match any implementation
+ * following the same recipe.  A voxel whose samples all share one phase keeps that phase's
+ * stiffness exactly.  The 2-layer rule uses the normal from the centre of the primitive whose
+ * surface is nearest to x_a (or the slab normal) and needs exactly two phases in the ball.
+ * Synchronises the stream (the mixed-voxel count is returned in mat->mixed_count).  If the mixed
+ * table is too small the labels are written, mat->mixed_count is set to the number needed and
+ * HOM_ERR_CAPACITY is returned: grow the mixed arrays and call again. */
+int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* phases, int32_t nphase,
+                     hom_material* mat, void* stream);
+
+/* Basic fixed-point scheme (section 2, eqs. 1-a, 1-b and 2) for every cell and load case.
+ *   cells/ncells  the same cells given to hom_filter_build, in the same order
+ *   mat           the filtered material built for them
+ *   E             host [ncells][L][nc] macroscopic strains (Mandel)
+ *   L             load cases per cell (1 <= L <= 8)
+ *   c0            host [ncells][2]: (lambda0, mu0) of the isotropic reference medium per cell
+ *   opts          solver options
+ *   out           outputs (see hom_result)
+ * Per (cell, load) the iteration starts from eps = E and stops at the first iterate whose
+ * equilibrium error (opts->criterion) is below opts->tol, after opts->max_iter Green-operator
+ * applications, or on divergence; the returned fields and <sigma> are those of that iterate.
+ * Returns HOM_OK when every load case converged, HOM_ERR_NOT_CONVERGED / HOM_ERR_DIVERGED
+ * otherwise (all outputs still written).  Synchronises the stream before returning. */
+int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
+              const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
+
+/* Effective stiffness from mean stresses: <sigma^(l)> = C_eff E^(l) for the L = nc linearly
+ * independent load cases of each cell, so C_eff = S^T (E^T)^-1 (with the nc unit Mandel strains
+ * as loads, column l of C_eff is <sigma^(l)>).  Computed in FP64 on the host.
+ *   ncells, dim   batch description
+ *   E             host [ncells][nc][nc] load cases (row l = E^(l))
+ *   mean_sigma    host or device [ncells][nc][nc] (row l = <sigma^(l)>, as hom_solve writes)
+ *   C_out         host [ncells][nc][nc] row-major
+ * Returns HOM_ERR_INVALID_ARG if some E is singular.  Synchronous. */
+int hom_effective_stiffness(int32_t ncells, int32_t dim, const double* E, const double* mean_sigma,
+                            double* C_out);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* hom_last_error(void);
+
+/* Frees cached FFT plans and solver workspace on every device the library used. */
+void hom_release(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t hom_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOM_H */

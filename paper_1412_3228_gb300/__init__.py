@@ -1,0 +1,332 @@
+"""Python binding of libhom, the GB300 library for FFT-based homogenisation with filtered
+material properties (Gélébart & Ouaki, arXiv 1412.3228).
+
+This module only marshals arguments: every step of the computation runs in the CUDA kernels of
+libhom.so (built in-tree by `_build_lib.build()`).  PyTorch provides device memory and streams.
+The functions carry the C ABI's names (include/hom.h):
+
+    hom_filter_build(cells, phases)          -> Material   (section 2, eqs. 3, 4, 5)
+    hom_solve(material, E, c0, ...)          -> dict       (section 2, eqs. 1-a, 1-b, 2)
+    hom_effective_stiffness(E, mean_sigma)   -> ndarray    (C_eff from mean stresses)
+
+There is no CPU fallback: if the library or a CUDA device is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhom.so")
+
+# constants of include/hom.h
+HOM_OK = 0
+HOM_ERR_NOT_CONVERGED = 3
+HOM_ERR_DIVERGED = 4
+HOM_ERR_CAPACITY = 8
+HOM_FP32, HOM_FP64 = 0, 1
+HOM_CRIT_E, HOM_CRIT_EN = 0, 1
+HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", -1: "active"}
+HOM_MIXED_BIT = 0x80000000
+HOM_NKERNEL = 8
+KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "init"]
+
+EXPORTED = ["hom_filter_build", "hom_solve", "hom_effective_stiffness", "hom_last_error", "hom_release",
+            "hom_version"]
+
+
+class HomError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("libhom error %d: %s" % (code, msg))
+        self.code = code
+
+
+class hom_primitive(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("phase", ctypes.c_int32), ("axis", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("centre", ctypes.c_double * 3), ("radius", ctypes.c_double)]
+
+
+class hom_cell(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32), ("matrix_phase", ctypes.c_int32),
+                ("rule", ctypes.c_int32), ("radius_px", ctypes.c_double), ("subgrid", ctypes.c_int32),
+                ("nprim", ctypes.c_int32), ("prims", ctypes.POINTER(hom_primitive))]
+
+
+class hom_phase(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class hom_material(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_void_p), ("mixed_c64", ctypes.c_void_p), ("mixed_c32", ctypes.c_void_p),
+                ("mixed_phases", ctypes.c_void_p), ("mixed_frac", ctypes.c_void_p),
+                ("mixed_normal", ctypes.c_void_p), ("mixed_voxel", ctypes.c_void_p),
+                ("mixed_capacity", ctypes.c_int64), ("phase_c64", ctypes.c_void_p),
+                ("phase_c32", ctypes.c_void_p), ("nphase", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("mixed_count", ctypes.c_int64)]
+
+
+class hom_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("criterion", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class hom_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * HOM_NKERNEL), ("ms", ctypes.c_double * HOM_NKERNEL),
+                ("bytes", ctypes.c_double * HOM_NKERNEL), ("voxel_iterations", ctypes.c_double)]
+
+
+class hom_result(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("mean_sigma", ctypes.c_void_p),
+                ("iterations", ctypes.c_void_p), ("status", ctypes.c_void_p), ("err", ctypes.c_void_p),
+                ("err_n", ctypes.c_void_p), ("stats", ctypes.POINTER(hom_kernel_stats))]
+
+
+_lib_handle = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libhom.so (raises if it was not built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhom.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        h = ctypes.CDLL(LIB_PATH)
+        h.hom_filter_build.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_phase),
+                                       ctypes.c_int32, ctypes.POINTER(hom_material), ctypes.c_void_p]
+        h.hom_solve.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
+                                ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(hom_solve_opts), ctypes.POINTER(hom_result), ctypes.c_void_p]
+        h.hom_effective_stiffness.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        h.hom_last_error.restype = ctypes.c_char_p
+        h.hom_version.restype = ctypes.c_int32
+        _lib_handle = h
+    return _lib_handle
+
+
+def _check(code: int, allow=(HOM_OK,)) -> int:
+    if code not in allow:
+        raise HomError(code, lib().hom_last_error().decode())
+    return code
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def ns_of(dim: int) -> int:
+    return 6 if dim == 2 else 21
+
+
+def nc_of(dim: int) -> int:
+    return 3 if dim == 2 else 6
+
+
+# ---------------------------------------------------------------------------------------------
+# marshalling of the seeded inputs (hom_inputs.Cell / Primitive or any object with the same
+# attributes)
+
+@dataclasses.dataclass
+class _CellArray:
+    cells: ctypes.Array
+    keep: list
+    dims: List[int]
+    ns: List[int]
+
+
+def _marshal_cells(cells) -> _CellArray:
+    arr = (hom_cell * len(cells))()
+    keep = []
+    for i, c in enumerate(cells):
+        prims = (hom_primitive * max(1, len(c.prims)))()
+        for j, p in enumerate(c.prims):
+            prims[j].kind = p.kind
+            prims[j].phase = p.phase
+            prims[j].axis = getattr(p, "axis", 0)
+            prims[j].reserved = 0
+            for d in range(3):
+                prims[j].centre[d] = float(p.centre[d])
+            prims[j].radius = float(p.radius)
+        keep.append(prims)
+        arr[i].dim = c.dim
+        arr[i].n = c.n
+        arr[i].matrix_phase = c.matrix_phase
+        arr[i].rule = c.rule
+        arr[i].radius_px = float(c.radius_px)
+        arr[i].subgrid = int(c.subgrid)
+        arr[i].nprim = len(c.prims)
+        arr[i].prims = ctypes.cast(prims, ctypes.POINTER(hom_primitive))
+    return _CellArray(arr, keep, [c.dim for c in cells], [c.n for c in cells])
+
+
+@dataclasses.dataclass
+class Material:
+    """Filtered stiffness of a batch of cells (device tensors owned by this object)."""
+    cells: list
+    dim: int
+    label: torch.Tensor          # int32 view of the uint32 labels, [sum n^dim]
+    mixed_c64: torch.Tensor
+    mixed_c32: torch.Tensor
+    mixed_phases: torch.Tensor
+    mixed_frac: torch.Tensor
+    mixed_normal: torch.Tensor
+    mixed_voxel: torch.Tensor
+    phase_c64: torch.Tensor
+    phase_c32: torch.Tensor
+    mixed_count: int
+    struct: hom_material
+    marshalled: _CellArray
+
+    def voxel_offsets(self) -> List[int]:
+        off, out = 0, []
+        for c in self.cells:
+            out.append(off)
+            off += c.n ** c.dim
+        return out
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def hom_filter_build(cells: Sequence, phases: Sequence[Tuple[float, float]], device=None, stream=None,
+                     capacity: Optional[int] = None) -> Material:
+    """Filtered stiffness of every voxel (section 2, eqs. 3-5); see include/hom.h."""
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    cells = list(cells)
+    dim = cells[0].dim
+    nvox = sum(c.n ** c.dim for c in cells)
+    ns = ns_of(dim)
+    nphase = len(phases)
+    ph = (hom_phase * nphase)()
+    for i, (lam, mu) in enumerate(phases):
+        ph[i].lambda_ = float(lam)
+        ph[i].mu = float(mu)
+    mc = _marshal_cells(cells)
+    label = torch.empty(nvox, dtype=torch.int32, device=device)
+    phase_c64 = torch.empty(nphase * ns, dtype=torch.float64, device=device)
+    phase_c32 = torch.empty(nphase * ns, dtype=torch.float32, device=device)
+    cap = capacity if capacity is not None else max(1024, nvox // 16)
+    for _attempt in range(2):
+        mixed = dict(
+            mixed_c64=torch.empty(cap * ns, dtype=torch.float64, device=device),
+            mixed_c32=torch.empty(cap * ns, dtype=torch.float32, device=device),
+            mixed_phases=torch.empty(cap * 2, dtype=torch.int32, device=device),
+            mixed_frac=torch.empty(cap, dtype=torch.float64, device=device),
+            mixed_normal=torch.empty(cap * 3, dtype=torch.float64, device=device),
+            mixed_voxel=torch.empty(cap, dtype=torch.int64, device=device))
+        st = hom_material(label=_ptr(label), mixed_c64=_ptr(mixed["mixed_c64"]), mixed_c32=_ptr(mixed["mixed_c32"]),
+                          mixed_phases=_ptr(mixed["mixed_phases"]), mixed_frac=_ptr(mixed["mixed_frac"]),
+                          mixed_normal=_ptr(mixed["mixed_normal"]), mixed_voxel=_ptr(mixed["mixed_voxel"]),
+                          mixed_capacity=cap, phase_c64=_ptr(phase_c64), phase_c32=_ptr(phase_c32),
+                          nphase=nphase, dim=dim, mixed_count=0)
+        with torch.cuda.device(device):
+            code = lib().hom_filter_build(mc.cells, len(cells), ph, nphase, ctypes.byref(st), _stream_handle(stream))
+        if code == HOM_ERR_CAPACITY:
+            cap = int(st.mixed_count)
+            continue
+        _check(code)
+        return Material(cells, dim, label, phase_c64=phase_c64, phase_c32=phase_c32,
+                        mixed_count=int(st.mixed_count), struct=st, marshalled=mc, **mixed)
+    raise HomError(HOM_ERR_CAPACITY, "mixed table did not fit after resizing")
+
+
+def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: int = HOM_FP64,
+              criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
+              host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
+              stats: bool = False, stream=None, allow_not_converged: bool = True) -> dict:
+    """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
+
+    E: [ncells, L, nc] (or [L, nc], shared by every cell) Mandel macroscopic strains.
+    c0: [ncells, 2] (or [2]) Lamé constants of the reference medium.
+    Returns a dict with eps / sigma fields ([sum over cells of L*nc*n^dim], flat, cell-major),
+    mean_sigma [ncells, L, nc], iterations / status / err / err_n [ncells, L] and the kernel
+    statistics when stats=True."""
+    cells = material.cells
+    ncells = len(cells)
+    dim = material.dim
+    nc = nc_of(dim)
+    E = np.asarray(E, dtype=np.float64)
+    if E.ndim == 2:
+        E = np.broadcast_to(E, (ncells,) + E.shape)
+    L = E.shape[1]
+    E = np.ascontiguousarray(E)
+    c0 = np.ascontiguousarray(np.broadcast_to(np.asarray(c0, dtype=np.float64), (ncells, 2)))
+    device = material.label.device
+    ftype = torch.float32 if precision == HOM_FP32 else torch.float64
+    nfield = sum(L * nc * c.n ** c.dim for c in cells)
+    eps = sig = None
+    if fields:
+        if host_fields:
+            eps = torch.empty(nfield, dtype=ftype, pin_memory=True)
+            sig = torch.empty(nfield, dtype=ftype, pin_memory=True)
+        else:
+            eps = torch.empty(nfield, dtype=ftype, device=device)
+            sig = torch.empty(nfield, dtype=ftype, device=device)
+    mean_sigma = np.zeros((ncells, L, nc))
+    iters = np.zeros((ncells, L), dtype=np.int32)
+    status = np.zeros((ncells, L), dtype=np.int32)
+    err = np.zeros((ncells, L))
+    err_n = np.zeros((ncells, L))
+    st = hom_kernel_stats() if stats else None
+    res = hom_result(eps=_ptr(eps), sigma=_ptr(sig), mean_sigma=mean_sigma.ctypes.data,
+                     iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
+                     err_n=err_n.ctypes.data, stats=ctypes.pointer(st) if st is not None else None)
+    opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
+                          check_every=int(check_every), diverge_window=int(diverge_window),
+                          use_graph=int(bool(use_graph)))
+    with torch.cuda.device(device):
+        code = lib().hom_solve(material.marshalled.cells, ncells, ctypes.byref(material.struct),
+                               E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L,
+                               c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                               ctypes.byref(res), _stream_handle(stream))
+    allowed = (HOM_OK, HOM_ERR_NOT_CONVERGED, HOM_ERR_DIVERGED) if allow_not_converged else (HOM_OK,)
+    _check(code, allowed)
+    out = dict(eps=eps, sigma=sig, mean_sigma=mean_sigma, iterations=iters, status=status, err=err,
+               err_n=err_n, code=code, E=E, L=L)
+    if st is not None:
+        out["stats"] = {KERNEL_NAMES[k]: dict(launches=int(st.launches[k]), ms=float(st.ms[k]),
+                                              bytes=float(st.bytes[k])) for k in range(HOM_NKERNEL)}
+        out["voxel_iterations"] = float(st.voxel_iterations)
+    return out
+
+
+def hom_effective_stiffness(E, mean_sigma, dim: int) -> np.ndarray:
+    """C_eff [ncells, nc, nc] from nc linearly independent load cases per cell."""
+    nc = nc_of(dim)
+    S = np.ascontiguousarray(np.asarray(mean_sigma, dtype=np.float64).reshape(-1, nc, nc))
+    ncells = S.shape[0]
+    E = np.asarray(E, dtype=np.float64)
+    if E.ndim == 2:
+        E = np.broadcast_to(E, (ncells, nc, nc))
+    E = np.ascontiguousarray(E)
+    C = np.zeros((ncells, nc, nc))
+    _check(lib().hom_effective_stiffness(ncells, dim, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ctypes.c_void_p(S.ctypes.data),
+                                         C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return C
+
+
+def field_views(result: dict, cells, dim: int) -> List[torch.Tensor]:
+    """Split a flat field (result['eps'] or result['sigma']) per cell into [L, nc, (n,) n, n]."""
+    nc = nc_of(dim)
+    L = result["L"]
+    views, off = {}, 0
+    out = {"eps": [], "sigma": []}
+    for key in ("eps", "sigma"):
+        f = result[key]
+        off = 0
+        for c in cells:
+            size = L * nc * c.n ** c.dim
+            out[key].append(None if f is None else f[off:off + size].view((L, nc) + (c.n,) * c.dim))
+            off += size
+    return out

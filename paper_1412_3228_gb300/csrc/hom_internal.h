@@ -1,0 +1,68 @@
+// Host-side internals shared by the library's translation units: error reporting, the FFT
+// plan cache and the device-side descriptor structs of the filter and solver kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hom.h"
+#include "hom_common.cuh"
+
+namespace hom {
+
+// ------------------------------------------------------------------ errors
+int set_error(int code, const char* fmt, ...);
+#define HOM_CUDA_TRY(call)                                                                 \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return ::hom::set_error(HOM_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+  } while (0)
+
+// ------------------------------------------------------------------ plans
+// Returns the device-resident plan of length n whose radices do not exceed max_radix (built
+// and uploaded on first use), or an error.
+int get_plan(int n, int max_radix, Plan* out);
+
+// Device scratch owned by the library (grown on demand, freed by hom_release).
+int get_workspace(size_t bytes, void** ptr);
+
+// ------------------------------------------------------------------ validation
+bool grid_supported(int n);
+
+// ------------------------------------------------------------------ kernel descriptors
+struct FCell {           // one cell of the filter build
+  int dim, n, matrix_phase, rule, S, nprim, prim0;
+  double radius_px;
+  long long vox_off;
+  long long block0;      // first thread block of this cell
+};
+struct FPrim {
+  int kind, phase, axis, pad;
+  double c[3];
+  double radius;
+};
+
+struct CellDev {         // one cell of the solver
+  int dim, n, H, Hp, nc, nrows, plan;
+  long long nv;
+  long long vox_off;     // voxel offset (labels)
+  long long fld_off;     // element offset of the cell in the real output fields
+  long long ws_off;      // complex-element offset of the cell in the mixed-domain arrays
+  long long g_off;       // complex-element offset of the cell in the displacement-like array
+  double lam0, mu0;
+  int rtask0, rtask1;    // row-pass task range
+};
+
+struct TaskR { int cell, row0, nrows, pad; };              // rows [row0, row0+nrows) x all loads
+struct TaskL { int cell, load, kx0, ntk, fixed, pad; };    // lines along one axis, kx tile
+
+// Per (cell, load) pair
+struct PairDev { int cell, load, ctask0, ctask1; };
+
+}  // namespace hom

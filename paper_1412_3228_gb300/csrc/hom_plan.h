@@ -1,0 +1,87 @@
+// Host-side construction of FFT plans: radix factorisation, digit-reversal permutation and
+// the FP64 twiddle table w[t] = exp(-2 pi i t / n) (rounded to FP32 for the FP32 path).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <functional>
+#include <utility>
+#include <vector>
+
+namespace hom {
+
+struct HostPlan {
+  int n = 0;
+  std::vector<int> radix;       // DIT order
+  std::vector<int> span;        // product of the radices before each stage
+  std::vector<uint16_t> perm;   // position of index k in the digit-reversed layout
+  std::vector<double> tw;       // interleaved (re, im) of exp(-2 pi i t / n)
+};
+
+// Factor n into the register radices {3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49} (each at most
+// `max_radix`) with the fewest stages, then the smallest largest radix.  Returns false if n has
+// a prime factor other than 3, 5, 7.
+inline bool factorize(int n, std::vector<int>& radix, int max_radix = 45) {
+  static const int kRadices[] = {45, 35, 27, 25, 21, 15, 9, 7, 5, 3, 49};
+  radix.clear();
+  if (n < 3 || (n % 2) == 0) return false;
+  int m = n;
+  for (int r : {3, 5, 7})
+    while (m % r == 0) m /= r;
+  if (m != 1) return false;
+  std::vector<int> best, cur;
+  std::function<void(int)> search = [&](int rem) {
+    if (rem == 1) {
+      auto key = [](const std::vector<int>& v) {
+        int mx = 0;
+        for (int r : v) mx = std::max(mx, r);
+        return std::make_pair((int)v.size(), mx);
+      };
+      if (best.empty() || key(cur) < key(best)) best = cur;
+      return;
+    }
+    if (!best.empty() && (int)cur.size() + 1 > (int)best.size()) return;
+    for (int r : kRadices) {
+      if (r > max_radix || rem % r != 0) continue;
+      if (!cur.empty() && r > cur.back()) continue;  // non-increasing order: one ordering per multiset
+      cur.push_back(r);
+      search(rem / r);
+      cur.pop_back();
+    }
+  };
+  search(n);
+  radix = best;
+  return !radix.empty();
+}
+
+inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
+  p.n = n;
+  if (!factorize(n, p.radix, max_radix)) return false;
+  const int m = (int)p.radix.size();
+  p.span.assign(m, 1);
+  for (int s = 1; s < m; ++s) p.span[s] = p.span[s - 1] * p.radix[s - 1];
+  // P(k): the last DIT stage splits k = d + r k' into block d of length n/r, recursively.
+  p.perm.assign(n, 0);
+  for (int k = 0; k < n; ++k) {
+    int pos = 0, kk = k, len = n;
+    for (int s = m - 1; s >= 0; --s) {
+      const int r = p.radix[s];
+      len /= r;
+      pos += (kk % r) * len;
+      kk /= r;
+    }
+    p.perm[k] = (uint16_t)pos;
+  }
+  p.tw.assign(2 * (size_t)n, 0.0);
+  const double two_pi = 6.28318530717958647692528676656;
+  for (int t = 0; t < n; ++t) {
+    // angle reduced to [0, 2 pi) exactly in integers before the FP64 evaluation
+    const double a = two_pi * (double)t / (double)n;
+    p.tw[2 * t] = std::cos(a);
+    p.tw[2 * t + 1] = -std::sin(a);
+  }
+  return true;
+}
+
+}  // namespace hom

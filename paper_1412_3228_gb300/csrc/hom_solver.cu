@@ -1,0 +1,1023 @@
+// Basic fixed-point scheme of section 2 (eqs. 1-a, 1-b, 2) for a batch of cells x load cases.
+//
+// State between passes lives in HBM in a "mixed" representation: transformed along x (half
+// spectrum kx = 0..(n-1)/2, rows padded to Hp entries), real along y (and z); layout
+// [load][z][y][kx][component] complex per cell.  One iteration (2D) is two passes:
+//   row pass   : inverse x-DFT of eps (pairs of real rows packed into one complex line),
+//                sigma = c~ : eps, FP64 partial sums of sigma, tau = sigma - c0 : eps,
+//                forward x-DFT of tau (eq. 1-b)
+//   Green pass : forward y-DFT of tau, then per wave vector xi on J (eq. 2):
+//                   r = tau_hat . xi - K0(xi) g      (= sigma_hat . xi: equilibrium residual)
+//                   g' = K0(xi)^-1 (tau_hat . xi)    eps_hat' = -sym(xi (x) g') (k != 0)
+//                   eps_hat'(0) = E
+//                then the inverse y-DFT, written to the other eps buffer.
+// g is the displacement-like vector of the current iterate (eps_hat = -sym(xi (x) g)); keeping
+// it lets the Green pass evaluate the equilibrium residual of the current iterate from tau_hat
+// alone.  In 3D the y transforms are separate passes (forward before, inverse after the
+// z-direction Green pass).  A small control kernel reduces the FP64 partial sums per
+// (cell, load), applies the stopping rule and deactivates finished load cases; later passes
+// skip inactive ones.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
+#include "hom_internal.h"
+
+namespace hom {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLoads = 8;
+
+struct SolveArgs {
+  const CellDev* cells;
+  const Plan* plans;
+  const uint32_t* label;
+  const float* mixed_c32;
+  const double* mixed_c64;
+  const float* phase_c32;
+  const double* phase_c64;
+  const double* E;  // [ncells][L][nc]
+  void* eps[2];
+  void* tau;
+  void* g;
+  double* partR;    // [ntaskR][L][nc]
+  double* partC;    // [ntaskC][2]
+  const TaskR* tR;
+  const TaskL* tC;
+  const TaskL* tY;
+  const PairDev* pairs;
+  int npairs;
+  int* active;
+  int* iters;
+  int* status;
+  double* err;
+  double* errn;
+  double* mean_sigma;  // [npairs][nc]
+  double* last_err;
+  int* grow;
+  int* it_dev;
+  int* nactive;
+  unsigned int* done;
+  unsigned long long* bytes;  // [HOM_NKERNEL]
+  int L, criterion, max_iter, diverge_window;
+  double tol;
+  void* out_eps;
+  void* out_sig;
+};
+
+template <typename T> __device__ __forceinline__ const T* mixed_tab(const SolveArgs& A);
+template <> __device__ __forceinline__ const float* mixed_tab<float>(const SolveArgs& A) { return A.mixed_c32; }
+template <> __device__ __forceinline__ const double* mixed_tab<double>(const SolveArgs& A) { return A.mixed_c64; }
+template <typename T> __device__ __forceinline__ const T* phase_tab(const SolveArgs& A);
+template <> __device__ __forceinline__ const float* phase_tab<float>(const SolveArgs& A) { return A.phase_c32; }
+template <> __device__ __forceinline__ const double* phase_tab<double>(const SolveArgs& A) { return A.phase_c64; }
+
+// Kahan-compensated accumulation in the field precision (the cross-thread part is FP64).
+template <typename T> struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    T y = x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Sum K doubles over the block; thread 0 gets the totals in out[].  Every thread must call.
+template <int K>
+__device__ void block_sum(double (&v)[K], double (&out)[K]) {
+  __shared__ double red[kThreads / 32][K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[w][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kThreads / 32; ++i) s += red[i][k];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void load_plan(const SolveArgs& A, int idx, Plan& sp) {
+  if (threadIdx.x == 0) sp = A.plans[idx];
+  __syncthreads();
+}
+
+// Shared-memory layout of the pass kernels: the length-n twiddle table, then the lines.
+template <typename V>
+__device__ __forceinline__ V* stage_twiddles(unsigned char* smem, const Plan& sp) {
+  V* tw = reinterpret_cast<V*>(smem);
+  const V* src = twiddles<V>(sp);
+  for (int i = threadIdx.x; i < sp.n; i += blockDim.x) tw[i] = src[i];
+  return tw;
+}
+
+__device__ __forceinline__ int signed_freq(int k, int n) { return k <= (n - 1) / 2 ? k : k - n; }
+
+// ------------------------------------------------------------------ row pass
+// OUT = false: one iteration's row pass (eps -> tau).  OUT = true: final fields of the returned
+// iterate (eps and sigma real, written to the output arrays), no forward transform.
+template <typename T, int DIM, bool OUT, int MAXR>
+__global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
+  using V = typename Cx<T>::V;
+  constexpr int NC = DIM == 2 ? 3 : 6;
+  constexpr int NS = DIM == 2 ? 6 : 21;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Plan sp;
+  __shared__ int s_al[kMaxLoads], s_par[kMaxLoads], s_nal;
+  const TaskR t = A.tR[blockIdx.x];
+  const CellDev c = A.cells[t.cell];
+  const int it = *A.it_dev;
+  if (threadIdx.x == 0) {
+    int nal = 0;
+    for (int l = 0; l < A.L; ++l) {
+      const int cl = t.cell * A.L + l;
+      if (OUT || A.active[cl]) {
+        s_al[nal] = l;
+        s_par[nal] = OUT ? (A.iters[cl] & 1) : (it & 1);
+        ++nal;
+      }
+    }
+    s_nal = nal;
+  }
+  load_plan(A, c.plan, sp);
+  const int nal = s_nal;
+  if (nal == 0) return;
+  const int n = c.n, H = c.H, Hp = c.Hp;
+  const V* tw = stage_twiddles<V>(smem_raw, sp);
+  V* s = reinterpret_cast<V*>(smem_raw) + n;
+  const int nreal = t.nrows * nal * NC;
+  const int nlines = (nreal + 1) >> 1;
+  const size_t load_stride = (size_t)c.nrows * Hp * NC;
+  const V zero = mk(T(0), T(0));
+
+  auto gaddr = [&](int q, int kx, int& par) -> size_t {
+    const int per_row = nal * NC;
+    const int rl = q / per_row;
+    const int rem = q - rl * per_row;
+    const int la = rem / NC;
+    const int comp = rem - la * NC;
+    par = s_par[la];
+    return c.ws_off + (size_t)s_al[la] * load_stride + ((size_t)(t.row0 + rl) * Hp + kx) * NC + comp;
+  };
+
+  // 1. two real rows per complex line, Hermitian-extended half spectra
+  for (int i = threadIdx.x; i < nlines * H; i += kThreads) {
+    const int line = i / H, kx = i - line * H;
+    const int q0 = 2 * line, q1 = q0 + 1;
+    int par;
+    size_t ad = gaddr(q0, kx, par);
+    V a = static_cast<const V*>(A.eps[par])[ad];
+    V b = zero;
+    if (q1 < nreal) {
+      ad = gaddr(q1, kx, par);
+      b = static_cast<const V*>(A.eps[par])[ad];
+    }
+    V* z = s + (size_t)line * n;
+    if (kx == 0) {
+      z[0] = mk(a.x, b.x);
+    } else {
+      z[kx] = mk(a.x - b.y, a.y + b.x);      // A + iB
+      z[n - kx] = mk(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
+    }
+  }
+  __syncthreads();
+  // 2. inverse x-DFT (natural -> digit-reversed positions)
+  fft_dif<false, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
+
+  // 3. constitutive update at every grid point of the task's rows
+  const int npts = t.nrows * n;
+  const T lam0 = (T)c.lam0, mu2 = (T)(2.0 * c.mu0);
+  for (int la = 0; la < nal; ++la) {
+    const int l = s_al[la];
+    Acc<T> acc[NC];
+    for (int p = threadIdx.x; p < npts; p += kThreads) {
+      const int rl = p / n, x = p - rl * n;
+      const int pos = HOM_LDG(sp.perm + x);
+      const size_t vox = (size_t)(t.row0 + rl) * n + x;
+      const uint32_t lab = HOM_LDG(A.label + c.vox_off + vox);
+      const T* src = (lab & HOM_MIXED_BIT) ? mixed_tab<T>(A) + (size_t)(lab & ~HOM_MIXED_BIT) * NS
+                                           : phase_tab<T>(A) + (size_t)lab * NS;
+      T C[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) C[k] = HOM_LDG(src + k);
+      T e[NC];
+      const int q0 = (rl * nal + la) * NC;
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const int q = q0 + k;
+        const V zz = s[(size_t)(q >> 1) * n + pos];
+        e[k] = (q & 1) ? zz.y : zz.x;
+      }
+      T sg[NC];
+#pragma unroll
+      for (int I = 0; I < NC; ++I) {
+        T acc_i = T(0);
+#pragma unroll
+        for (int J = 0; J < NC; ++J) acc_i += C[packed_index(NC, I, J)] * e[J];
+        sg[I] = acc_i;
+      }
+      if (OUT) {
+        const size_t base = c.fld_off + (size_t)l * NC * c.nv + vox;
+        T* oe = static_cast<T*>(A.out_eps);
+        T* os = static_cast<T*>(A.out_sig);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          if (oe) oe[base + (size_t)k * c.nv] = e[k];
+          if (os) os[base + (size_t)k * c.nv] = sg[k];
+        }
+      } else {
+        T tr = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) tr += e[k];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const T c0e = mu2 * e[k] + (k < DIM ? lam0 * tr : T(0));
+          const T tau = sg[k] - c0e;
+          const int q = q0 + k;
+          V* zz = s + (size_t)(q >> 1) * n + pos;
+          if (q & 1) zz->y = tau; else zz->x = tau;
+          acc[k].add(sg[k]);
+        }
+      }
+    }
+    if (!OUT) {
+      double v[NC], tot[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) v[k] = acc[k].value();
+      block_sum<NC>(v, tot);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) A.partR[((size_t)blockIdx.x * A.L + l) * NC + k] = tot[k];
+      }
+    }
+  }
+  if (OUT) {
+    if (threadIdx.x == 0)
+      atomicAdd(A.bytes + HOM_K_OUTPUT,
+                (unsigned long long)((size_t)nal * t.nrows * NC * (H * sizeof(V) + 2 * (size_t)n * sizeof(T)) +
+                                     (size_t)t.nrows * n * 4));
+    return;
+  }
+  __syncthreads();
+  // 4. forward x-DFT (digit-reversed -> natural)
+  fft_dit<true, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
+  // 5. split the two real rows of each line and store the half spectra of tau
+  V* tau = static_cast<V*>(A.tau);
+  for (int i = threadIdx.x; i < nlines * H; i += kThreads) {
+    const int line = i / H, kx = i - line * H;
+    const V* z = s + (size_t)line * n;
+    const V zk = z[kx];
+    const V zm = z[kx == 0 ? 0 : n - kx];
+    const V a = mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));   // (Z[k] + conj Z[n-k]) / 2
+    const V b = mk(T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x));   // (Z[k] - conj Z[n-k]) / 2i
+    const int q0 = 2 * line;
+    int par;
+    tau[gaddr(q0, kx, par)] = a;
+    if (q0 + 1 < nreal) tau[gaddr(q0 + 1, kx, par)] = b;
+  }
+  if (threadIdx.x == 0)
+    atomicAdd(A.bytes + HOM_K_ROW,
+              (unsigned long long)(2 * (size_t)nreal * H * sizeof(V) + (size_t)t.nrows * n * 4));
+}
+
+// ------------------------------------------------------------------ Green pass
+// Lines along the last axis (y in 2D, z in 3D with ky fixed) for a tile of kx and one load.
+template <typename T, int DIM, int MAXR>
+__global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
+  using V = typename Cx<T>::V;
+  constexpr int NC = DIM == 2 ? 3 : 6;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Plan sp;
+  const TaskL t = A.tC[blockIdx.x];
+  const int cl = t.cell * A.L + t.load;
+  if (!A.active[cl]) return;
+  const CellDev c = A.cells[t.cell];
+  load_plan(A, c.plan, sp);
+  const int it = *A.it_dev;
+  const int n = c.n, Hp = c.Hp, ntk = t.ntk;
+  const V* tw = stage_twiddles<V>(smem_raw, sp);
+  V* s = reinterpret_cast<V*>(smem_raw) + n;
+  const int nl = ntk * NC;
+  const size_t rowstride = DIM == 2 ? (size_t)Hp * NC : (size_t)n * Hp * NC;
+  const size_t base = c.ws_off + (size_t)t.load * c.nrows * Hp * NC +
+                      (DIM == 3 ? (size_t)t.fixed * Hp * NC : 0) + (size_t)t.kx0 * NC;
+  const V* in = static_cast<const V*>(A.tau);
+  V* out = DIM == 2 ? static_cast<V*>(A.eps[(it + 1) & 1]) : static_cast<V*>(A.tau);
+
+  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
+    const int j = i / nl, w = i - j * nl;
+    s[(size_t)w * n + j] = in[base + (size_t)j * rowstride + w];
+  }
+  __syncthreads();
+  fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+
+  // Green operator at every wave vector of the tile (spectrum at digit-reversed positions)
+  const T two_pi = T(6.28318530717958647692528676656);
+  const T mu0 = (T)c.mu0;
+  const T lpm = (T)(c.lam0 + c.mu0);
+  const T ratio = (T)((c.lam0 + c.mu0) / (c.lam0 + 2.0 * c.mu0));
+  const T inv_nv = (T)(1.0 / (double)c.nv);
+  const T rs2 = T(0.707106781186547524400844362105);
+  const double* Eld = A.E + ((size_t)t.cell * A.L + t.load) * NC;
+  V* gbuf = static_cast<V*>(A.g);
+  const size_t gbase = c.g_off + (size_t)t.load * c.nrows * Hp * DIM + (size_t)t.kx0 * DIM;
+  const size_t grow_stride = DIM == 2 ? (size_t)Hp * DIM : (size_t)n * Hp * DIM;
+  const size_t gfix = DIM == 3 ? (size_t)t.fixed * Hp * DIM : 0;
+  Acc<T> r2acc, rnacc;
+  for (int i = threadIdx.x; i < ntk * n; i += kThreads) {
+    const int kk = i / ntk, kxl = i - kk * ntk;
+    const int kx = t.kx0 + kxl;
+    const int pos = HOM_LDG(sp.perm + kk);
+    V* tv[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) tv[k] = s + (size_t)(kxl * NC + k) * n + pos;
+    V* gp = gbuf + gbase + gfix + (size_t)kk * grow_stride + (size_t)kxl * DIM;
+    T xi[DIM];
+    xi[0] = two_pi * (T)kx;
+    if (DIM == 2) {
+      xi[1] = two_pi * (T)signed_freq(kk, n);
+    } else {
+      xi[1] = two_pi * (T)signed_freq(t.fixed, n);
+      xi[DIM - 1] = two_pi * (T)signed_freq(kk, n);
+    }
+    const bool k0 = kx == 0 && kk == 0 && (DIM == 2 || t.fixed == 0);
+    if (k0) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) *tv[k] = mk((T)Eld[k], T(0));
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gp[d] = mk(T(0), T(0));
+      continue;
+    }
+    // tensor components of tau_hat
+    V tt[DIM][DIM];
+    if (DIM == 2) {
+      tt[0][0] = *tv[0];
+      tt[1][1] = *tv[1];
+      tt[0][1] = tt[1][0] = rs2 * *tv[2];
+    } else {
+      tt[0][0] = *tv[0];
+      tt[1][1] = *tv[1];
+      tt[DIM - 1][DIM - 1] = *tv[2];
+      tt[1][DIM - 1] = tt[DIM - 1][1] = rs2 * *tv[3];
+      tt[0][DIM - 1] = tt[DIM - 1][0] = rs2 * *tv[4];
+      tt[0][1] = tt[1][0] = rs2 * *tv[5];
+    }
+    V v[DIM], gv[DIM];
+    T q2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      q2 += xi[a] * xi[a];
+      V acc = mk(T(0), T(0));
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) acc = acc + xi[b] * tt[a][b];
+      v[a] = acc;
+      gv[a] = gp[a];
+    }
+    V xg = mk(T(0), T(0)), xv = mk(T(0), T(0));
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      xg = xg + xi[a] * gv[a];
+      xv = xv + xi[a] * v[a];
+    }
+    // equilibrium residual of the current iterate: r = tau_hat xi - K0 g
+    T r2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const V r = v[a] - (mu0 * q2) * gv[a] - (lpm * xi[a]) * xg;
+      r2 += r.x * r.x + r.y * r.y;
+    }
+    const T wgt = kx == 0 ? T(1) : T(2);
+    r2acc.add(wgt * r2);
+    rnacc.add(wgt * r2 / q2);
+    // g' = K0^-1 (tau_hat xi);  eps_hat' = -sym(xi (x) g') / N_v
+    const T inv_mq = T(1) / (mu0 * q2);
+    const T rq = ratio / q2;
+    V w[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      w[a] = inv_mq * (v[a] - (rq * xi[a]) * xv);
+      gp[a] = w[a];
+    }
+    if (DIM == 2) {
+      *tv[0] = (-xi[0] * inv_nv) * w[0];
+      *tv[1] = (-xi[1] * inv_nv) * w[1];
+      *tv[2] = (-rs2 * inv_nv) * (xi[0] * w[1] + xi[1] * w[0]);
+    } else {
+      *tv[0] = (-xi[0] * inv_nv) * w[0];
+      *tv[1] = (-xi[1] * inv_nv) * w[1];
+      *tv[2] = (-xi[2] * inv_nv) * w[2];
+      *tv[3] = (-rs2 * inv_nv) * (xi[1] * w[2] + xi[2] * w[1]);
+      *tv[4] = (-rs2 * inv_nv) * (xi[0] * w[2] + xi[2] * w[0]);
+      *tv[5] = (-rs2 * inv_nv) * (xi[0] * w[1] + xi[1] * w[0]);
+    }
+  }
+  {
+    double vv[2] = {r2acc.value(), rnacc.value()}, tot[2];
+    block_sum<2>(vv, tot);  // contains the barrier before the inverse transform
+    if (threadIdx.x == 0) {
+      A.partC[2 * (size_t)blockIdx.x] = tot[0];
+      A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
+    }
+  }
+  fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
+    const int j = i / nl, w = i - j * nl;
+    out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + j];
+  }
+  if (threadIdx.x == 0)
+    atomicAdd(A.bytes + HOM_K_GREEN,
+              (unsigned long long)(2 * (size_t)n * nl * sizeof(V) + 2 * (size_t)n * ntk * DIM * sizeof(V)));
+}
+
+// ------------------------------------------------------------------ 3D y passes
+template <typename T, bool FWD, int MAXR>
+__global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
+  using V = typename Cx<T>::V;
+  constexpr int NC = 6;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Plan sp;
+  const TaskL t = A.tY[blockIdx.x];
+  const int cl = t.cell * A.L + t.load;
+  if (!A.active[cl]) return;
+  const CellDev c = A.cells[t.cell];
+  load_plan(A, c.plan, sp);
+  const int it = *A.it_dev;
+  const int n = c.n, Hp = c.Hp, nl = t.ntk * NC;
+  const V* tw = stage_twiddles<V>(smem_raw, sp);
+  V* s = reinterpret_cast<V*>(smem_raw) + n;
+  const size_t rowstride = (size_t)Hp * NC;
+  const size_t base = c.ws_off + (size_t)t.load * c.nrows * Hp * NC + (size_t)t.fixed * n * Hp * NC +
+                      (size_t)t.kx0 * NC;
+  const V* in = static_cast<const V*>(A.tau);
+  V* out = FWD ? static_cast<V*>(A.tau) : static_cast<V*>(A.eps[(it + 1) & 1]);
+  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
+    const int j = i / nl, w = i - j * nl;
+    const int pos = FWD ? j : HOM_LDG(sp.perm + j);
+    s[(size_t)w * n + pos] = in[base + (size_t)j * rowstride + w];
+  }
+  __syncthreads();
+  if (FWD) fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+  else fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
+    const int j = i / nl, w = i - j * nl;
+    const int pos = FWD ? HOM_LDG(sp.perm + j) : j;
+    out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + pos];
+  }
+  if (threadIdx.x == 0)
+    atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)n * nl * sizeof(V)));
+}
+
+// ------------------------------------------------------------------ control
+// One warp per (cell, load): FP64 compensated sums of the partials, equilibrium errors,
+// stopping rule.  The last block to finish counts the active pairs and advances the iteration.
+__global__ void __launch_bounds__(kThreads) k_control(SolveArgs A, int nc) {
+  __shared__ bool s_last;
+  __shared__ int s_cnt[kThreads / 32];
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int it = *A.it_dev;
+  if (warp < A.npairs && A.active[warp]) {
+    const PairDev pr = A.pairs[warp];
+    const CellDev c = A.cells[pr.cell];
+    double sum[6], cmp[6];
+    for (int k = 0; k < 6; ++k) sum[k] = cmp[k] = 0.0;
+    for (int tk = c.rtask0 + lane; tk < c.rtask1; tk += 32) {
+      const double* p = A.partR + ((size_t)tk * A.L + pr.load) * nc;
+      for (int k = 0; k < nc; ++k) {
+        const double x = p[k];
+        const double tt = sum[k] + x;  // Neumaier
+        cmp[k] += fabs(sum[k]) >= fabs(x) ? (sum[k] - tt) + x : (x - tt) + sum[k];
+        sum[k] = tt;
+      }
+    }
+    double r2 = 0.0, rn2 = 0.0;
+    for (int tk = pr.ctask0 + lane; tk < pr.ctask1; tk += 32) {
+      r2 += A.partC[2 * (size_t)tk];
+      rn2 += A.partC[2 * (size_t)tk + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      for (int k = 0; k < nc; ++k) {
+        const double os = __shfl_down_sync(0xffffffffu, sum[k], o);
+        const double oc = __shfl_down_sync(0xffffffffu, cmp[k], o);
+        const double tt = sum[k] + os;
+        cmp[k] += (fabs(sum[k]) >= fabs(os) ? (sum[k] - tt) + os : (os - tt) + sum[k]) + oc;
+        sum[k] = tt;
+      }
+      r2 += __shfl_down_sync(0xffffffffu, r2, o);
+      rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
+    }
+    if (lane == 0) {
+      double den2 = 0.0;
+      for (int k = 0; k < nc; ++k) {
+        const double tot = sum[k] + cmp[k];
+        A.mean_sigma[(size_t)warp * nc + k] = tot / (double)c.nv;
+        den2 += tot * tot;
+      }
+      const double den = sqrt(den2);
+      const double e = sqrt(r2) / den, en = sqrt(rn2) / den;
+      A.err[warp] = e;
+      A.errn[warp] = en;
+      const double crit = A.criterion == HOM_CRIT_E ? e : en;
+      int st = -1;
+      if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
+      else if (crit < A.tol) st = HOM_STATUS_CONVERGED;
+      else if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
+      else if (A.diverge_window > 0) {
+        int gcount = crit > A.last_err[warp] ? A.grow[warp] + 1 : 0;
+        A.grow[warp] = gcount;
+        if (gcount >= A.diverge_window) st = HOM_STATUS_DIVERGED;
+      }
+      A.last_err[warp] = crit;
+      if (st >= 0) {
+        A.status[warp] = st;
+        A.iters[warp] = it;
+        A.active[warp] = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    int cnt = 0;
+    for (int p = threadIdx.x; p < A.npairs; p += blockDim.x) cnt += ((volatile int*)A.active)[p] ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) s_cnt[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += s_cnt[i];
+      *A.nactive = tot;
+      *A.it_dev = it + 1;
+      *A.done = 0u;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ initial state
+// eps = E: the stored x-spectrum holds E at kx = 0 of every row (see the scaling convention in
+// the row pass: stored = (1/n) x-DFT, so the unnormalised inverse gives eps back).
+template <typename T>
+__global__ void k_init(SolveArgs A, int ncells, int nc) {
+  using V = typename Cx<T>::V;
+  for (int cell = blockIdx.y; cell < ncells; cell += gridDim.y) {
+    const CellDev c = A.cells[cell];
+    const long long items = (long long)A.L * c.nrows * nc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < items; i += (long long)gridDim.x * blockDim.x) {
+      const int comp = (int)(i % nc);
+      const long long r = i / nc;
+      const long long row = r % c.nrows;
+      const int l = (int)(r / c.nrows);
+      const size_t ad = c.ws_off + ((size_t)l * c.nrows + row) * c.Hp * nc + comp;
+      static_cast<V*>(A.eps[0])[ad] = mk((T)A.E[((size_t)cell * A.L + l) * nc + comp], T(0));
+    }
+  }
+}
+
+__global__ void k_init_pairs(SolveArgs A) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < A.npairs) {
+    A.active[p] = 1;
+    A.iters[p] = 0;
+    A.status[p] = -1;
+    A.grow[p] = 0;
+    A.last_err[p] = INFINITY;
+  }
+  if (p == 0) {
+    *A.it_dev = 0;
+    *A.nactive = A.npairs;
+    *A.done = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+// Opt a kernel in to `bytes` of dynamic shared memory (needed above 48 KB).
+template <typename K>
+int allow_smem(K kernel, size_t bytes) {
+  cudaFuncAttributes fa{};
+  HOM_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+  int dev = 0, optin = 0;
+  HOM_CUDA_TRY(cudaGetDevice(&dev));
+  HOM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (bytes + fa.sharedSizeBytes > (size_t)optin)
+    return set_error(HOM_ERR_UNSUPPORTED_SIZE, "kernel needs %zu bytes of shared memory, device allows %d",
+                     bytes + fa.sharedSizeBytes, optin);
+  if ((int)bytes > fa.maxDynamicSharedSizeBytes)
+    HOM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return HOM_OK;
+}
+
+struct Layout {
+  std::vector<CellDev> cells;
+  std::vector<Plan> plans;
+  std::vector<TaskR> tR;
+  std::vector<TaskL> tC, tY;
+  std::vector<PairDev> pairs;
+  size_t ws_elems = 0, g_elems = 0, fld_elems = 0;
+  size_t smem_row = 0, smem_green = 0, smem_y = 0;
+};
+
+size_t smem_budget() {
+  const char* e = std::getenv("HOM_SMEM_BUDGET");
+  size_t b = e ? (size_t)std::atoll(e) : (size_t)64 * 1024;
+  return std::min<size_t>(std::max<size_t>(b, 8 * 1024), 227 * 1024);
+}
+
+int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize, int max_radix, const double* c0,
+                 Layout& lay) {
+  const int nc = nc_of(dim);
+  const size_t budget = smem_budget();
+  const size_t kMaxSmem = 227 * 1024;
+  long long vox = 0;
+  std::vector<int> plan_n;
+  for (int ci = 0; ci < ncells; ++ci) {
+    const hom_cell& k = cells[ci];
+    CellDev c{};
+    c.dim = dim;
+    c.n = k.n;
+    c.H = (k.n + 1) / 2;
+    c.Hp = (c.H + 7) / 8 * 8;
+    c.nc = nc;
+    c.nrows = dim == 2 ? k.n : k.n * k.n;
+    c.nv = (long long)c.nrows * k.n;
+    auto itp = std::find(plan_n.begin(), plan_n.end(), k.n);
+    if (itp == plan_n.end()) {
+      Plan p;
+      int rc = get_plan(k.n, max_radix, &p);
+      if (rc != HOM_OK) return rc;
+      plan_n.push_back(k.n);
+      lay.plans.push_back(p);
+      c.plan = (int)lay.plans.size() - 1;
+    } else {
+      c.plan = (int)(itp - plan_n.begin());
+    }
+    c.vox_off = vox;
+    c.fld_off = (long long)lay.fld_elems;
+    c.ws_off = (long long)lay.ws_elems;
+    c.g_off = (long long)lay.g_elems;
+    c.lam0 = c0[2 * ci];
+    c.mu0 = c0[2 * ci + 1];
+    vox += c.nv;
+    lay.fld_elems += (size_t)L * nc * c.nv;
+    lay.ws_elems += (size_t)L * c.nrows * c.Hp * nc;
+    lay.g_elems += (size_t)L * c.nrows * c.Hp * dim;
+    // row-pass tasks: as many rows as fit in the shared-memory budget with every load active
+    const size_t line_bytes = (size_t)k.n * vsize;  // one line; the twiddle table is one more
+    auto row_lines = [&](int rows) { return (size_t)((rows * L * nc + 1) / 2) + 1; };
+    int r = 1;
+    while (r < c.nrows && row_lines(r + 1) * line_bytes <= budget) ++r;
+    const size_t need_r = row_lines(r) * line_bytes;
+    if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
+    lay.smem_row = std::max(lay.smem_row, need_r);
+    c.rtask0 = (int)lay.tR.size();
+    for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), 0});
+    c.rtask1 = (int)lay.tR.size();
+    // Green-pass and y-pass tiles of kx
+    int ntk = (int)std::max<size_t>(1, (budget - std::min(budget, line_bytes)) / ((size_t)nc * line_bytes));
+    ntk = std::min(ntk, c.H);
+    const size_t need_l = ((size_t)ntk * nc + 1) * line_bytes;
+    if (need_l > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "line of n = %d does not fit on chip", k.n);
+    lay.smem_green = std::max(lay.smem_green, need_l);
+    lay.smem_y = std::max(lay.smem_y, need_l);
+    for (int l = 0; l < L; ++l) {
+      PairDev pd{ci, l, (int)lay.tC.size(), 0};
+      const int nfix = dim == 2 ? 1 : k.n;
+      for (int f = 0; f < nfix; ++f)
+        for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tC.push_back(TaskL{ci, l, kx0, std::min(ntk, c.H - kx0), f, 0});
+      pd.ctask1 = (int)lay.tC.size();
+      lay.pairs.push_back(pd);
+      if (dim == 3)
+        for (int z = 0; z < k.n; ++z)
+          for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tY.push_back(TaskL{ci, l, kx0, std::min(ntk, c.H - kx0), z, 0});
+    }
+    lay.cells.push_back(c);
+  }
+  return HOM_OK;
+}
+
+struct Timer {
+  hom_kernel_stats* stats;
+  cudaStream_t st;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  void begin(int kind) {
+    if (!stats) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    ev.push_back({kind, {a, b}});
+  }
+  void end() {
+    if (!stats) return;
+    cudaEventRecord(ev.back().second.second, st);
+  }
+  void collect() {
+    if (!stats) return;
+    for (auto& e : ev) {
+      float ms = 0.f;
+      cudaEventSynchronize(e.second.second);
+      cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+      stats->ms[e.first] += ms;
+      stats->launches[e.first] += 1;
+      cudaEventDestroy(e.second.first);
+      cudaEventDestroy(e.second.second);
+    }
+    ev.clear();
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T, int DIM, int MAXR>
+int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L, const double* c0,
+              const hom_solve_opts* opts, hom_result* out, cudaStream_t st) {
+  using V = typename Cx<T>::V;
+  const int nc = nc_of(DIM);
+  Layout lay;
+  int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, lay);
+  if (rc != HOM_OK) return rc;
+  const int npairs = ncells * L;
+  const bool want_fields = out->eps || out->sigma;
+  const bool eps_dev = is_device_ptr(out->eps), sig_dev = is_device_ptr(out->sigma);
+  const bool need_stage = want_fields && ((out->eps && !eps_dev) || (out->sigma && !sig_dev));
+
+  // workspace carve-up
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_eps0 = take(lay.ws_elems * sizeof(V)), o_eps1 = take(lay.ws_elems * sizeof(V)),
+               o_tau = take(lay.ws_elems * sizeof(V)), o_g = take(lay.g_elems * sizeof(V));
+  const size_t o_partR = take(lay.tR.size() * (size_t)L * nc * sizeof(double));
+  const size_t o_partC = take(lay.tC.size() * 2 * sizeof(double));
+  const size_t o_cells = take(lay.cells.size() * sizeof(CellDev)), o_plans = take(lay.plans.size() * sizeof(Plan));
+  const size_t o_tR = take(lay.tR.size() * sizeof(TaskR)), o_tC = take(lay.tC.size() * sizeof(TaskL)),
+               o_tY = take(std::max<size_t>(1, lay.tY.size()) * sizeof(TaskL));
+  const size_t o_pairs = take(lay.pairs.size() * sizeof(PairDev));
+  const size_t o_E = take((size_t)npairs * nc * sizeof(double));
+  const size_t o_int = take((size_t)npairs * 4 * sizeof(int) + 64);
+  const size_t o_dbl = take((size_t)npairs * (3 + nc) * sizeof(double));
+  const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
+  const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
+  const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
+  const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
+  void* wsv = nullptr;
+  rc = get_workspace(off, &wsv);
+  if (rc != HOM_OK) return rc;
+  unsigned char* ws = static_cast<unsigned char*>(wsv);
+  {
+    std::vector<unsigned char> h(host_hi - host_lo, 0);
+    auto put = [&](size_t o, const void* src, size_t b) {
+      if (b) std::memcpy(h.data() + (o - host_lo), src, b);
+    };
+    put(o_cells, lay.cells.data(), lay.cells.size() * sizeof(CellDev));
+    put(o_plans, lay.plans.data(), lay.plans.size() * sizeof(Plan));
+    put(o_tR, lay.tR.data(), lay.tR.size() * sizeof(TaskR));
+    put(o_tC, lay.tC.data(), lay.tC.size() * sizeof(TaskL));
+    put(o_tY, lay.tY.data(), lay.tY.size() * sizeof(TaskL));
+    put(o_pairs, lay.pairs.data(), lay.pairs.size() * sizeof(PairDev));
+    put(o_E, E, (size_t)npairs * nc * sizeof(double));
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + host_lo, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+  }
+  HOM_CUDA_TRY(cudaMemsetAsync(ws + o_eps0, 0, lay.ws_elems * sizeof(V), st));
+  HOM_CUDA_TRY(cudaMemsetAsync(ws + o_g, 0, lay.g_elems * sizeof(V), st));
+  HOM_CUDA_TRY(cudaMemsetAsync(ws + o_bytes, 0, HOM_NKERNEL * sizeof(unsigned long long), st));
+
+  SolveArgs A{};
+  A.cells = reinterpret_cast<const CellDev*>(ws + o_cells);
+  A.plans = reinterpret_cast<const Plan*>(ws + o_plans);
+  A.label = mat->label;
+  A.mixed_c32 = mat->mixed_c32;
+  A.mixed_c64 = mat->mixed_c64;
+  A.phase_c32 = mat->phase_c32;
+  A.phase_c64 = mat->phase_c64;
+  A.E = reinterpret_cast<const double*>(ws + o_E);
+  A.eps[0] = ws + o_eps0;
+  A.eps[1] = ws + o_eps1;
+  A.tau = ws + o_tau;
+  A.g = ws + o_g;
+  A.partR = reinterpret_cast<double*>(ws + o_partR);
+  A.partC = reinterpret_cast<double*>(ws + o_partC);
+  A.tR = reinterpret_cast<const TaskR*>(ws + o_tR);
+  A.tC = reinterpret_cast<const TaskL*>(ws + o_tC);
+  A.tY = reinterpret_cast<const TaskL*>(ws + o_tY);
+  A.pairs = reinterpret_cast<const PairDev*>(ws + o_pairs);
+  A.npairs = npairs;
+  int* ib = reinterpret_cast<int*>(ws + o_int);
+  A.active = ib;
+  A.iters = ib + npairs;
+  A.status = ib + 2 * npairs;
+  A.grow = ib + 3 * npairs;
+  A.it_dev = ib + 4 * npairs;
+  A.nactive = ib + 4 * npairs + 1;
+  A.done = reinterpret_cast<unsigned int*>(ib + 4 * npairs + 2);
+  double* db = reinterpret_cast<double*>(ws + o_dbl);
+  A.err = db;
+  A.errn = db + npairs;
+  A.last_err = db + 2 * npairs;
+  A.mean_sigma = db + 3 * npairs;
+  A.bytes = reinterpret_cast<unsigned long long*>(ws + o_bytes);
+  A.L = L;
+  A.criterion = opts->criterion;
+  A.max_iter = opts->max_iter;
+  A.diverge_window = opts->diverge_window;
+  A.tol = opts->tol;
+  A.out_eps = out->eps ? (eps_dev ? out->eps : (void*)(ws + o_stage_e)) : nullptr;
+  A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
+
+  if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
+  if ((rc = allow_smem(k_row<T, DIM, true, MAXR>, lay.smem_row)) != HOM_OK) return rc;
+  if ((rc = allow_smem(k_green<T, DIM, MAXR>, lay.smem_green)) != HOM_OK) return rc;
+  if (DIM == 3) {
+    if ((rc = allow_smem(k_ypass<T, true, MAXR>, lay.smem_y)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_ypass<T, false, MAXR>, lay.smem_y)) != HOM_OK) return rc;
+  }
+
+  Timer tm{out->stats, st, {}};
+  const unsigned nR = (unsigned)lay.tR.size(), nC = (unsigned)lay.tC.size(), nY = (unsigned)lay.tY.size();
+  const unsigned nCtl = (unsigned)((npairs * 32 + kThreads - 1) / kThreads);
+  tm.begin(HOM_K_INIT);
+  k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
+  {
+    dim3 grid(64, (unsigned)std::min(ncells, 65535));
+    k_init<T><<<grid, 256, 0, st>>>(A, ncells, nc);
+  }
+  tm.end();
+  HOM_CUDA_TRY(cudaGetLastError());
+
+  const int check = opts->check_every > 0 ? opts->check_every : 8;
+  int host_nactive = npairs;
+  int launched = 0;
+  auto one_iteration = [&]() {
+    tm.begin(HOM_K_ROW);
+    k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
+    tm.end();
+    if (DIM == 3) {
+      tm.begin(HOM_K_YFWD);
+      k_ypass<T, true, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
+      tm.end();
+    }
+    tm.begin(HOM_K_GREEN);
+    k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
+    tm.end();
+    if (DIM == 3) {
+      tm.begin(HOM_K_YINV);
+      k_ypass<T, false, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
+      tm.end();
+    }
+    tm.begin(HOM_K_CONTROL);
+    k_control<<<nCtl, kThreads, 0, st>>>(A, nc);
+    tm.end();
+  };
+  // Graphs are captured on a private stream (the legacy default stream cannot be captured) and
+  // launched on the caller's stream.
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  while (host_nactive > 0) {
+    const int remaining = opts->max_iter + 1 - launched;
+    if (remaining <= 0) break;  // the control kernel has stopped every pair by now
+    const int k = std::min(check, remaining);
+    if (opts->use_graph && !out->stats) {
+      if (!gexec) {
+        cudaGraph_t graph;
+        HOM_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        const cudaStream_t user = st;
+        st = cap_stream;  // the launch lambdas and the timer use `st`
+        HOM_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < check; ++i) one_iteration();
+        const cudaError_t ce = cudaStreamEndCapture(cap_stream, &graph);
+        st = user;
+        if (ce != cudaSuccess) {
+          cudaStreamDestroy(cap_stream);
+          return set_error(HOM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        }
+        HOM_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
+        cudaGraphDestroy(graph);
+      }
+      HOM_CUDA_TRY(cudaGraphLaunch(gexec, st));
+      launched += check;
+    } else {
+      for (int i = 0; i < k; ++i) one_iteration();
+      launched += k;
+    }
+    HOM_CUDA_TRY(cudaGetLastError());
+    HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (host_nactive > 0) return set_error(HOM_ERR_TIMEOUT, "iteration control did not terminate");
+
+  if (want_fields) {
+    tm.begin(HOM_K_OUTPUT);
+    k_row<T, DIM, true, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
+    tm.end();
+    HOM_CUDA_TRY(cudaGetLastError());
+    if (out->eps && !eps_dev)
+      HOM_CUDA_TRY(cudaMemcpyAsync(out->eps, ws + o_stage_e, lay.fld_elems * sizeof(T), cudaMemcpyDeviceToHost, st));
+    if (out->sigma && !sig_dev)
+      HOM_CUDA_TRY(cudaMemcpyAsync(out->sigma, ws + o_stage_s, lay.fld_elems * sizeof(T), cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<int> h_it(npairs), h_st(npairs);
+  std::vector<double> h_e(npairs), h_en(npairs);
+  unsigned long long h_bytes[HOM_NKERNEL];
+  HOM_CUDA_TRY(cudaMemcpyAsync(out->mean_sigma, A.mean_sigma, (size_t)npairs * nc * sizeof(double), cudaMemcpyDefault, st));
+  HOM_CUDA_TRY(cudaMemcpyAsync(h_it.data(), A.iters, npairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HOM_CUDA_TRY(cudaMemcpyAsync(h_st.data(), A.status, npairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HOM_CUDA_TRY(cudaMemcpyAsync(h_e.data(), A.err, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HOM_CUDA_TRY(cudaMemcpyAsync(h_en.data(), A.errn, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  HOM_CUDA_TRY(cudaMemcpyAsync(h_bytes, A.bytes, sizeof(h_bytes), cudaMemcpyDeviceToHost, st));
+  HOM_CUDA_TRY(cudaStreamSynchronize(st));
+  tm.collect();
+  if (out->iterations) std::memcpy(out->iterations, h_it.data(), npairs * sizeof(int));
+  if (out->status) std::memcpy(out->status, h_st.data(), npairs * sizeof(int));
+  if (out->err) std::memcpy(out->err, h_e.data(), npairs * sizeof(double));
+  if (out->err_n) std::memcpy(out->err_n, h_en.data(), npairs * sizeof(double));
+  if (out->stats) {
+    for (int k = 0; k < HOM_NKERNEL; ++k) out->stats->bytes[k] += (double)h_bytes[k];
+    double vi = 0.0;
+    for (int p = 0; p < npairs; ++p) vi += (double)lay.cells[lay.pairs[p].cell].nv * h_it[p];
+    out->stats->voxel_iterations += vi;
+  }
+  int worst = HOM_OK;
+  for (int p = 0; p < npairs; ++p) {
+    if (h_st[p] == HOM_STATUS_DIVERGED) worst = HOM_ERR_DIVERGED;
+    else if (h_st[p] == HOM_STATUS_MAX_ITER && worst == HOM_OK) worst = HOM_ERR_NOT_CONVERGED;
+  }
+  if (worst == HOM_ERR_DIVERGED) set_error(worst, "a load case diverged");
+  if (worst == HOM_ERR_NOT_CONVERGED) set_error(worst, "a load case reached max_iter");
+  return worst;
+}
+
+}  // namespace
+}  // namespace hom
+
+using namespace hom;
+
+extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
+                         const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
+  if (!cells || ncells <= 0 || !mat || !E || !c0 || !opts || !out || !out->mean_sigma)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: null or empty argument");
+  if (L < 1 || L > kMaxLoads) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: L must be in [1, %d]", kMaxLoads);
+  if (opts->precision != HOM_FP32 && opts->precision != HOM_FP64)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown precision");
+  if (opts->criterion != HOM_CRIT_E && opts->criterion != HOM_CRIT_EN)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown criterion");
+  if (opts->max_iter < 0 || opts->check_every < 0 || opts->diverge_window < 0)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: negative option");
+  if (!mat->label || !mat->phase_c32 || !mat->phase_c64)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material not built");
+  const int dim = cells[0].dim;
+  for (int c = 0; c < ncells; ++c) {
+    if (cells[c].dim != dim || (dim != 2 && dim != 3))
+      return set_error(HOM_ERR_INVALID_ARG, "hom_solve: every cell must share dim 2 or 3");
+    if (!grid_supported(cells[c].n))
+      return set_error(HOM_ERR_UNSUPPORTED_SIZE, "hom_solve: cell %d grid %d unsupported", c, cells[c].n);
+    if (!(c0[2 * c + 1] > 0.0) || !(c0[2 * c] + 2.0 * c0[2 * c + 1] > 0.0))
+      return set_error(HOM_ERR_INVALID_ARG, "hom_solve: reference medium of cell %d is not positive", c);
+  }
+  if (mat->dim != dim) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material built for another dimension");
+  cudaGetLastError();  // do not report an error left behind by an unrelated earlier call
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Largest register radix of the FFT stages: FP32 kernels are compiled for 27 and 45, FP64 ones
+  // for 15 (HOM_MAX_RADIX32 selects the FP32 variant).
+  const char* env = std::getenv("HOM_MAX_RADIX32");
+  const int r32 = env ? std::atoi(env) : 27;
+  if (opts->precision == HOM_FP32) {
+    if (r32 >= 45)
+      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st)
+                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st);
+    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st)
+                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st);
+  }
+  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st)
+                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st);
+}

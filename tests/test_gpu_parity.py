@@ -1,0 +1,250 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars: filter counts bit-exact, filtered stiffness within 1e-12 relative (FP64, different
+formulas on each side for the 2-layer rule); FP64 solves within 1e-10 relative on C_eff and on
+the local fields with identical iteration counts; FP32 solves within 1e-5 relative on C_eff."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import hom_inputs as H
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+hom = pytest.importorskip("paper_1412_3228_gb300")
+from gpu_helpers import cell_fields, dense_ctilde, unpack  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    torch.cuda.set_device(0)
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+FILTER_CASES = [
+    ("disk45-voigt", lambda: H.centred_disk_cell(45, rule=H.RULE_VOIGT), 10.0),
+    ("disk45-reuss", lambda: H.centred_disk_cell(45, rule=H.RULE_REUSS), 0.1),
+    ("disk45-2layer", lambda: H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER, radius_px=0.55), 10.0),
+    ("disk45-none", lambda: H.centred_disk_cell(45, rule=H.RULE_NONE), 10.0),
+    ("disk25-tie", lambda: H.centred_disk_cell(25, radius=0.2, rule=H.RULE_VOIGT, subgrid=5), 10.0),
+    ("slab27-2layer", lambda: H.laminate_cell(27, 2, 0.37, axis=1, centre=0.43, rule=H.RULE_TWO_LAYER,
+                                              subgrid=8), 0.1),
+    ("sph15-2layer", lambda: H.rsa_spheres_cell(15, seed=1015, vf=0.15, rmin=0.1, rmax=0.15, subgrid=6, gap_voxels=1.0), 10.0),
+    ("sph9-reuss", lambda: H.rsa_spheres_cell(9, seed=9, vf=0.15, rmin=0.12, rmax=0.18, rule=H.RULE_REUSS,
+                                              subgrid=4, gap_voxels=1.0), 0.1),
+]
+
+
+@pytest.mark.parametrize("name,make,contrast", FILTER_CASES, ids=[c[0] for c in FILTER_CASES])
+def test_filter_build_parity(name, make, contrast):
+    cell = make()
+    phases = H.two_phases(contrast)
+    mat = hom.hom_filter_build([cell], phases)
+    fb = O.filter_build(cell, phases)
+    dim = cell.dim
+    nc = O.nc_of(dim)
+    got, mixed = dense_ctilde(mat, 0)
+    ref = fb["ctilde"].reshape(-1, nc, nc)
+    np.testing.assert_array_equal(mixed, fb["mixed"].ravel())
+    assert _rel(unpack(got, nc), ref) < 1e-12
+    # pure voxels carry the phase stiffness itself (the oracle forms shear terms as sqrt2*sqrt2*mu,
+    # one rounding away from 2 mu)
+    pure = ~mixed
+    np.testing.assert_allclose(unpack(got, nc)[pure], ref[pure], rtol=4e-16, atol=0)
+    if cell.rule != H.RULE_NONE and mat.mixed_count:
+        # volume fractions are exact sample counts
+        vox = mat.mixed_voxel[:mat.mixed_count].cpu().numpy()
+        frac = mat.mixed_frac[:mat.mixed_count].cpu().numpy()
+        ph = mat.mixed_phases[:2 * mat.mixed_count].cpu().numpy().reshape(-1, 2)
+        counts = fb["counts"].reshape(-1, len(phases))
+        np.testing.assert_array_equal(frac, counts[vox, ph[:, 1]] / fb["M"])
+    # FP32 copy is the rounded FP64 value
+    got32, _ = dense_ctilde(mat, 0, fp64=False)
+    np.testing.assert_array_equal(got32, got.astype(np.float32))
+
+
+def _solve_both(cells, phases, E, precision, criterion, tol, max_iter=2000, c0=None):
+    mat = hom.hom_filter_build(cells, phases)
+    if c0 is None:
+        c0 = [H.mean_lame(phases)] * len(cells)
+    res = hom.hom_solve(mat, E, c0, precision=precision, criterion=criterion, tol=tol, max_iter=max_iter)
+    refs = []
+    for i, cell in enumerate(cells):
+        fb = O.filter_build(cell, phases)
+        refs.append(O.solve(fb["ctilde"], cell.dim, cell.n, c0[i][0], c0[i][1], np.asarray(E), tol=tol,
+                            max_iter=max_iter, criterion=criterion))
+    return mat, res, refs
+
+
+SOLVE_FP64 = [
+    ("disk45-voigt-c10", [lambda: H.centred_disk_cell(45, rule=H.RULE_VOIGT)], 10.0),
+    ("disk45-2layer-c0.1", [lambda: H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER)], 0.1),
+    ("disk27-none-c10", [lambda: H.centred_disk_cell(27, rule=H.RULE_NONE)], 10.0),
+    ("disk75-reuss-c10", [lambda: H.centred_disk_cell(75, rule=H.RULE_REUSS)], 10.0),
+]
+
+
+@pytest.mark.parametrize("name,makers,contrast", SOLVE_FP64, ids=[c[0] for c in SOLVE_FP64])
+def test_solve_fp64_2d_parity(name, makers, contrast):
+    cells = [m() for m in makers]
+    phases = H.two_phases(contrast)
+    E = np.eye(3)
+    mat, res, refs = _solve_both(cells, phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    eps = cell_fields(res, cells, 2, "eps")
+    sig = cell_fields(res, cells, 2, "sigma")
+    for i, ref in enumerate(refs):
+        assert list(res["iterations"][i]) == list(ref["iterations"])
+        assert all(s == 0 for s in res["status"][i])
+        C = hom.hom_effective_stiffness(E, res["mean_sigma"][i:i + 1], 2)[0]
+        Cref = O.effective_stiffness(ref["mean_sigma"], E)
+        assert _rel(C, Cref) < 1e-10
+        assert _rel(eps[i], ref["eps"]) < 1e-10
+        assert _rel(sig[i], ref["sigma"]) < 1e-10
+        for l in range(3):
+            assert abs(res["err"][i, l] - ref["errors"][l][-1]) < 1e-6 * ref["errors"][l][-1] + 1e-14
+
+
+def test_solve_fp64_3d_parity():
+    cell = H.rsa_spheres_cell(15, seed=1015, vf=0.15, rmin=0.1, rmax=0.15, subgrid=6, gap_voxels=1.0)
+    phases = H.two_phases(10.0)
+    E = np.eye(6)
+    mat, res, refs = _solve_both([cell], phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    ref = refs[0]
+    assert list(res["iterations"][0]) == list(ref["iterations"])
+    C = hom.hom_effective_stiffness(E, res["mean_sigma"], 3)[0]
+    Cref = O.effective_stiffness(ref["mean_sigma"], E)
+    assert _rel(C, Cref) < 1e-10
+    assert _rel(cell_fields(res, [cell], 3, "eps")[0], ref["eps"]) < 1e-10
+    assert _rel(cell_fields(res, [cell], 3, "sigma")[0], ref["sigma"]) < 1e-10
+
+
+def test_solve_fp32_2d_parity():
+    cells = [H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER), H.centred_disk_cell(45, rule=H.RULE_VOIGT)]
+    phases = H.two_phases(10.0)
+    E = np.eye(3)
+    mat, res, refs = _solve_both(cells, phases, E, hom.HOM_FP32, hom.HOM_CRIT_EN, 1e-6)
+    eps = cell_fields(res, cells, 2, "eps")
+    for i, ref in enumerate(refs):
+        C = hom.hom_effective_stiffness(E, res["mean_sigma"][i:i + 1], 2)[0]
+        Cref = O.effective_stiffness(ref["mean_sigma"], E)
+        assert _rel(C, Cref) < 1e-5
+        assert all(abs(int(a) - int(b)) <= 2 for a, b in zip(res["iterations"][i], ref["iterations"]))
+        # local fields: L2 and max errors relative to the field scale
+        d = eps[i] - ref["eps"]
+        assert np.sqrt(np.mean(d ** 2)) / np.sqrt(np.mean(ref["eps"] ** 2)) < 1e-5
+        assert _rel(eps[i], ref["eps"]) < 1e-4
+
+
+def test_solve_fp32_3d_parity():
+    cell = H.rsa_spheres_cell(15, seed=1015, vf=0.15, rmin=0.1, rmax=0.15, subgrid=6, gap_voxels=1.0)
+    phases = H.two_phases(0.1)
+    E = np.eye(6)
+    mat, res, refs = _solve_both([cell], phases, E, hom.HOM_FP32, hom.HOM_CRIT_EN, 1e-6)
+    C = hom.hom_effective_stiffness(E, res["mean_sigma"], 3)[0]
+    Cref = O.effective_stiffness(refs[0]["mean_sigma"], E)
+    assert _rel(C, Cref) < 1e-5
+
+
+def test_uneven_batch_matches_per_cell_oracle():
+    """Cells of different sizes, rules and contrasts in one launch sequence."""
+    base = [H.centred_disk_cell(15, rule=H.RULE_VOIGT), H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER),
+            H.centred_disk_cell(27, rule=H.RULE_REUSS), H.centred_disk_cell(5, rule=H.RULE_NONE, radius=0.2)]
+    contrasts = [10.0, 0.1, 3.0, 20.0]
+    phases, cells = [], []
+    for cell, c in zip(base, contrasts):
+        cells.append(H.remap_phases(cell, len(phases)))
+        phases.extend(H.two_phases(c))
+    c0 = [H.mean_lame(phases[2 * i:2 * i + 2]) for i in range(len(cells))]
+    E = np.eye(3)
+    mat = hom.hom_filter_build(cells, phases)
+    res = hom.hom_solve(mat, E, c0, precision=hom.HOM_FP64, criterion=hom.HOM_CRIT_E, tol=1e-9, max_iter=2000)
+    eps = cell_fields(res, cells, 2, "eps")
+    for i, cell in enumerate(cells):
+        fb = O.filter_build(cell, phases)
+        ref = O.solve(fb["ctilde"], 2, cell.n, c0[i][0], c0[i][1], E, tol=1e-9, max_iter=2000)
+        assert list(res["iterations"][i]) == list(ref["iterations"])
+        assert _rel(res["mean_sigma"][i], ref["mean_sigma"]) < 1e-10
+        assert _rel(eps[i], ref["eps"]) < 1e-10
+
+
+def test_homogeneous_and_laminate_edge_cases():
+    phases = H.two_phases(10.0)
+    # homogeneous cell: converged at iteration 0, eps = E
+    for dim, n in [(2, 3), (3, 5)]:
+        nc = O.nc_of(dim)
+        cell = H.homogeneous_cell(n, dim)
+        mat = hom.hom_filter_build([cell], phases)
+        E = np.eye(nc)
+        res = hom.hom_solve(mat, E, [3.0, 2.0], precision=hom.HOM_FP64, tol=1e-12, max_iter=5)
+        assert (res["iterations"] == 0).all() and (res["status"] == 0).all()
+        C = hom.hom_effective_stiffness(E, res["mean_sigma"], dim)[0]
+        np.testing.assert_allclose(C, O.isotropic_mandel(*phases[0], dim), atol=1e-13)
+    # grid-aligned laminate on the smallest grids is exact
+    from closed_forms import backus
+    for n, m in [(3, 1), (5, 2), (9, 5)]:
+        centre = 0.5 if m % 2 == 1 else 0.5 + 0.5 / n
+        cell = H.laminate_cell(n, 2, m / n, axis=0, centre=centre)
+        mat = hom.hom_filter_build([cell], phases)
+        res = hom.hom_solve(mat, np.eye(3), H.mean_lame(phases), precision=hom.HOM_FP64, tol=1e-13, max_iter=3000)
+        C = hom.hom_effective_stiffness(np.eye(3), res["mean_sigma"], 2)[0]
+        assert _rel(C, backus(2, m / n, phases)) < 1e-11
+
+
+def test_max_iter_and_divergence_status():
+    cell = H.centred_disk_cell(15, rule=H.RULE_VOIGT)
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build([cell], phases)
+    lam0, mu0 = H.mean_lame(phases)
+    res = hom.hom_solve(mat, np.eye(3), [lam0, mu0], precision=hom.HOM_FP64, tol=1e-14, max_iter=3)
+    assert res["code"] == hom.HOM_ERR_NOT_CONVERGED
+    assert (res["status"] == 1).all() and (res["iterations"] == 3).all()
+    ref = O.solve(O.filter_build(cell, phases)["ctilde"], 2, 15, lam0, mu0, np.eye(3), tol=1e-14, max_iter=3)
+    assert _rel(res["mean_sigma"][0], ref["mean_sigma"]) < 1e-10
+    # a reference medium far below the optimal one (alpha < 1) makes the basic scheme diverge
+    res = hom.hom_solve(mat, np.eye(3), [0.05 * lam0, 0.05 * mu0], precision=hom.HOM_FP64, tol=1e-8,
+                        max_iter=400, diverge_window=10)
+    assert res["code"] == hom.HOM_ERR_DIVERGED
+    assert (res["status"] == 2).any()
+
+
+def test_host_outputs_graphs_and_repeatability():
+    cells = [H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER)]
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build(cells, phases)
+    c0 = H.mean_lame(phases)
+    kw = dict(precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-6, max_iter=500)
+    a = hom.hom_solve(mat, np.eye(3), c0, **kw)
+    b = hom.hom_solve(mat, np.eye(3), c0, host_fields=True, **kw)
+    c = hom.hom_solve(mat, np.eye(3), c0, use_graph=True, check_every=4, **kw)
+    for r in (b, c):
+        assert np.array_equal(r["mean_sigma"], a["mean_sigma"])
+        assert np.array_equal(r["iterations"], a["iterations"])
+        assert torch.equal(r["eps"].cpu(), a["eps"].cpu())
+        assert torch.equal(r["sigma"].cpu(), a["sigma"].cpu())
+
+
+def test_kernel_stats_count_the_work():
+    cells = [H.centred_disk_cell(45, rule=H.RULE_VOIGT)]
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build(cells, phases)
+    r = hom.hom_solve(mat, np.eye(3), H.mean_lame(phases), precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN,
+                      tol=1e-6, max_iter=500, stats=True)
+    st = r["stats"]
+    total_it = int(r["iterations"].sum())
+    assert st["row"]["launches"] >= r["iterations"].max() + 1
+    assert st["green"]["ms"] > 0 and st["row"]["ms"] > 0
+    n, H_ = 45, 23
+    # Green pass: read + write of 3 complex FP32 components and of the 2-vector g per bin
+    per_it = 2 * 45 * H_ * (3 + 2) * 8
+    assert st["green"]["bytes"] == per_it * (total_it + 3)
+    assert r["voxel_iterations"] == n * n * total_it
