@@ -294,8 +294,33 @@ def run_reference(args):
             "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(args):
+    """Small fixed case for ncu captures: two 1215^2 cells (Voigt and 2-layer, contrast 10), 3 loads,
+    exactly `args.iters` fixed-point iterations in FP32 (or FP64 with --fp64-case)."""
+    import torch
+
+    import paper_1412_3228_gb300 as hom
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    torch.cuda.set_device(0)
+    cells, phases, c0 = workload()
+    pick = [i for i, c in enumerate(cells) if c.n == args.profile_n and c.rule in (H.RULE_VOIGT, H.RULE_TWO_LAYER)
+            and abs(phases[c.matrix_phase + 1][1] / phases[c.matrix_phase][1] - 10.0) < 1e-9]
+    mat = hom.hom_filter_build([cells[i] for i in pick], phases)
+    prec = hom.HOM_FP64 if args.fp64_case else hom.HOM_FP32
+    r = hom.hom_solve(mat, np.eye(3), c0[pick], precision=prec, criterion=hom.HOM_CRIT_EN, tol=-1.0,
+                      max_iter=args.iters, fields=False)
+    torch.cuda.synchronize()
+    print("profile case: %d cells of n=%d, %d iterations, status %s" % (len(pick), args.profile_n, args.iters,
+                                                                          r["status"].ravel().tolist()))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-case", action="store_true", help="run only the small fixed ncu case")
+    ap.add_argument("--profile-n", type=int, default=1215)
+    ap.add_argument("--iters", type=int, default=4)
+    ap.add_argument("--fp64-case", action="store_true")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -305,6 +330,9 @@ def main():
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))

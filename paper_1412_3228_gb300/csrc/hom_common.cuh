@@ -112,6 +112,24 @@ HOM_HD void dft7(V* v) {
   for (int p = 0; p < 7; ++p) v[p] = out[p];
 }
 
+// Register DFTs.  dft_small<R> transforms v[0..R) in place; for a composite R the results come
+// out in a fixed, compile-time order: X[k] is left in v[out_pos<R>(k)].  Prime radices keep the
+// natural order.
+template <int R> HOM_HD constexpr int split_a() {  // R = A * B with A the first factor
+  return R == 9 ? 3 : R == 15 ? 3 : R == 21 ? 3 : R == 25 ? 5 : R == 27 ? 3 : R == 35 ? 5 : R == 45 ? 5 : R == 49 ? 7 : 1;
+}
+template <int R> HOM_HD constexpr bool is_prime_radix() { return R == 3 || R == 5 || R == 7; }
+
+template <int R> HOM_HD constexpr int out_pos(int k) {
+  if constexpr (is_prime_radix<R>()) {
+    return k;
+  } else {
+    constexpr int A = split_a<R>(), B = R / A;
+    // block ka = k mod A holds X[ka + A kb] at offset out_pos<B>(kb)
+    return B * (k % A) + out_pos<B>(k / A);
+  }
+}
+
 template <int R, bool FWD, typename V, typename T> HOM_HD void dft_small(V* v);
 
 // Composite register DFT of size R = A * B (Cooley-Tukey inside the registers):
@@ -128,27 +146,18 @@ HOM_HD void dft_composite(V* v) {
     dft_small<A, FWD, V, T>(t);
 #pragma unroll
     for (int ka = 0; ka < A; ++ka) {
+      const V x = t[out_pos<A>(ka)];
       const int m = (nb * ka) % R;
       if (m == 0) {
-        v[B * ka + nb] = t[ka];
+        v[B * ka + nb] = x;
       } else {
         const V w = mk((T)tw_cos(R, m), FWD ? (T)(-tw_sin(R, m)) : (T)tw_sin(R, m));
-        v[B * ka + nb] = cmul(t[ka], w);
+        v[B * ka + nb] = cmul(x, w);
       }
     }
   }
-  V out[R];
 #pragma unroll
-  for (int ka = 0; ka < A; ++ka) {
-    V t[B];
-#pragma unroll
-    for (int nb = 0; nb < B; ++nb) t[nb] = v[B * ka + nb];
-    dft_small<B, FWD, V, T>(t);
-#pragma unroll
-    for (int kb = 0; kb < B; ++kb) out[ka + A * kb] = t[kb];
-  }
-#pragma unroll
-  for (int k = 0; k < R; ++k) v[k] = out[k];
+  for (int ka = 0; ka < A; ++ka) dft_small<B, FWD, V, T>(v + B * ka);
 }
 
 template <int R, bool FWD, typename V, typename T>
@@ -156,25 +165,25 @@ HOM_HD void dft_small(V* v) {
   if constexpr (R == 3) dft3<FWD, V, T>(v);
   else if constexpr (R == 5) dft5<FWD, V, T>(v);
   else if constexpr (R == 7) dft7<FWD, V, T>(v);
-  else if constexpr (R == 9) dft_composite<3, 3, FWD, V, T>(v);
-  else if constexpr (R == 15) dft_composite<3, 5, FWD, V, T>(v);
-  else if constexpr (R == 25) dft_composite<5, 5, FWD, V, T>(v);
-  else if constexpr (R == 27) dft_composite<3, 9, FWD, V, T>(v);
-  else if constexpr (R == 45) dft_composite<5, 9, FWD, V, T>(v);
-  else if constexpr (R == 21) dft_composite<3, 7, FWD, V, T>(v);
-  else if constexpr (R == 35) dft_composite<5, 7, FWD, V, T>(v);
-  else if constexpr (R == 49) dft_composite<7, 7, FWD, V, T>(v);
-  else static_assert(R == 3, "unsupported radix");
+  else dft_composite<split_a<R>(), R / split_a<R>(), FWD, V, T>(v);
 }
 
-// Quotient of a / d (0 <= a < 2^22, 1 <= d < 2^12) through a float reciprocal, corrected to exact.
-HOM_HD int fast_div(int a, int d, float inv_d) {
-  int q = (int)((float)a * inv_d);
-  const int r = a - q * d;
-  if (r < 0) --q;
-  else if (r >= d) ++q;
-  return q;
-}
+// Enumerates the flat indices f = tid, tid + step, ... < total as pairs (a, b) with f = a * nb + b,
+// updating the pair with carries instead of dividing.
+struct Iter2 {
+  int a, b, da, db, nb;
+  HOM_HD Iter2(int f0, int step, int nb_) : nb(nb_) {
+    a = f0 / nb;
+    b = f0 - a * nb;
+    da = step / nb;
+    db = step - da * nb;
+  }
+  HOM_HD void next() {
+    b += db;
+    a += da;
+    if (b >= nb) { b -= nb; ++a; }
+  }
+};
 
 // ------------------------------------------------------------------ FFT plan
 // Device-resident description of the transform of one length.
@@ -193,21 +202,19 @@ template <> HOM_HD const float2* twiddles<float2>(const Plan& p) { return p.tw32
 template <> HOM_HD const double2* twiddles<double2>(const Plan& p) { return p.tw64; }
 
 // One DIT stage (radix R, span L) over `nl` lines of length n stored back to back (line stride
-// `ls` elements).  Thread `tid` of `nthr` handles butterflies tid, tid + nthr, ...  `tw` is the
-// twiddle table of length n (shared memory in the kernels).
+// `ls` elements).  Thread `tid` of `nthr` handles butterflies tid, tid + nthr, ... (a butterfly is
+// (line, block, j) with j < L), enumerated with carries.  `tw` is the length-n twiddle table.
 template <int R, bool FWD, typename V, typename T>
 HOM_HD void dit_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, int nthr) {
   const int B = L * R;
   const int nb = n / R;           // butterflies per line
   const int twstep = n / B;
-  const int total = nl * nb;
-  const float inv_nb = 1.0f / (float)nb, inv_L = 1.0f / (float)L;
-  for (int b = tid; b < total; b += nthr) {
-    const int line = fast_div(b, nb, inv_nb);
-    const int w = b - line * nb;
-    const int blk = fast_div(w, L, inv_L);
-    const int j = w - blk * L;
-    V* base = s + line * ls + blk * B + j;
+  Iter2 lw(tid, nthr, nb);        // (line, w)
+  Iter2 bj(lw.b, lw.db, L);       // (block, j) of w; advanced by the same step
+  const int nblk = n / B;
+  for (; lw.a < nl; ) {
+    V* base = s + lw.a * ls + bj.a * B + bj.b;
+    const int j = bj.b;
     V v[R];
     v[0] = base[0];
 #pragma unroll
@@ -221,7 +228,16 @@ HOM_HD void dit_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
     }
     dft_small<R, FWD, V, T>(v);
 #pragma unroll
-    for (int p = 0; p < R; ++p) base[p * L] = v[p];
+    for (int p = 0; p < R; ++p) base[p * L] = v[out_pos<R>(p)];
+    // advance (line, w) and (block, j) together
+    lw.b += lw.db;
+    lw.a += lw.da;
+    bj.next();
+    if (bj.a >= nblk) bj.a -= nblk;
+    if (lw.b >= nb) {
+      lw.b -= nb;
+      ++lw.a;
+    }
   }
 }
 
@@ -231,14 +247,12 @@ HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
   const int B = L * R;
   const int nb = n / R;
   const int twstep = n / B;
-  const int total = nl * nb;
-  const float inv_nb = 1.0f / (float)nb, inv_L = 1.0f / (float)L;
-  for (int b = tid; b < total; b += nthr) {
-    const int line = fast_div(b, nb, inv_nb);
-    const int w = b - line * nb;
-    const int blk = fast_div(w, L, inv_L);
-    const int j = w - blk * L;
-    V* base = s + line * ls + blk * B + j;
+  Iter2 lw(tid, nthr, nb);
+  Iter2 bj(lw.b, lw.db, L);
+  const int nblk = n / B;
+  for (; lw.a < nl; ) {
+    V* base = s + lw.a * ls + bj.a * B + bj.b;
+    const int j = bj.b;
     V v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = base[q * L];
@@ -246,12 +260,20 @@ HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
     base[0] = v[0];
 #pragma unroll
     for (int p = 1; p < R; ++p) {
-      V x = v[p];
+      V x = v[out_pos<R>(p)];
       if (L > 1) {
         V t = tw[j * p * twstep];
         x = FWD ? cmul(x, t) : cmulc(x, t);
       }
       base[p * L] = x;
+    }
+    lw.b += lw.db;
+    lw.a += lw.da;
+    bj.next();
+    if (bj.a >= nblk) bj.a -= nblk;
+    if (lw.b >= nb) {
+      lw.b -= nb;
+      ++lw.a;
     }
   }
 }

@@ -75,7 +75,8 @@ template <typename T> __device__ __forceinline__ const T* phase_tab(const SolveA
 template <> __device__ __forceinline__ const float* phase_tab<float>(const SolveArgs& A) { return A.phase_c32; }
 template <> __device__ __forceinline__ const double* phase_tab<double>(const SolveArgs& A) { return A.phase_c64; }
 
-// Kahan-compensated accumulation in the field precision (the cross-thread part is FP64).
+// Kahan-compensated accumulation in the field precision: the running sum s and the negated
+// lost low part c (the represented value is s - c).
 template <typename T> struct Acc {
   T s = T(0), c = T(0);
   __device__ __forceinline__ void add(T x) {
@@ -84,19 +85,29 @@ template <typename T> struct Acc {
     c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Sum K doubles over the block; thread 0 gets the totals in out[].  Every thread must call.
-template <int K>
-__device__ void block_sum(double (&v)[K], double (&out)[K]) {
+// Sum K compensated partials over the block; thread 0 gets FP64 totals in out[].  For FP32 the
+// warp stage adds (sum, error) pairs with the error-free TwoSum in FP32, so FP64 arithmetic (2
+// operations per SM and cycle on this GPU) is used only for the final per-warp combination.
+// Every thread must call.
+template <typename T, int K>
+__device__ void block_sum(const Acc<T> (&v)[K], double (&out)[K]) {
   __shared__ double red[kThreads / 32][K];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) red[w][k] = x;
+    T hi = v[k].s, lo = -v[k].c;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ohi = __shfl_down_sync(0xffffffffu, hi, o);
+      const T olo = __shfl_down_sync(0xffffffffu, lo, o);
+      const T t = hi + ohi;            // TwoSum(hi, ohi)
+      const T bp = t - hi;
+      const T err = (hi - (t - bp)) + (ohi - bp);
+      hi = t;
+      lo = lo + olo + err;
+    }
+    if (lane == 0) red[w][k] = (double)hi + (double)lo;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -162,28 +173,31 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   const int nlines = (nreal + 1) >> 1;
   const size_t load_stride = (size_t)c.nrows * Hp * NC;
   const V zero = mk(T(0), T(0));
-
-  auto gaddr = [&](int q, int kx, int& par) -> size_t {
+  // Real row q = (row, active load, component) -> element offset of its half spectrum at kx = 0;
+  // the top bit carries the eps buffer parity of its load.
+  long long* qbase = reinterpret_cast<long long*>(s + (size_t)nlines * n);
+  for (int q = threadIdx.x; q < nreal; q += kThreads) {
     const int per_row = nal * NC;
     const int rl = q / per_row;
     const int rem = q - rl * per_row;
     const int la = rem / NC;
     const int comp = rem - la * NC;
-    par = s_par[la];
-    return c.ws_off + (size_t)s_al[la] * load_stride + ((size_t)(t.row0 + rl) * Hp + kx) * NC + comp;
-  };
+    const long long off = (long long)(c.ws_off + (size_t)s_al[la] * load_stride + (size_t)(t.row0 + rl) * Hp * NC + comp);
+    qbase[q] = off | ((long long)s_par[la] << 62);
+  }
+  __syncthreads();
+  const long long kOffMask = (1LL << 62) - 1;
 
   // 1. two real rows per complex line, Hermitian-extended half spectra
-  for (int i = threadIdx.x; i < nlines * H; i += kThreads) {
-    const int line = i / H, kx = i - line * H;
+  for (Iter2 it(threadIdx.x, kThreads, H); it.a < nlines; it.next()) {
+    const int line = it.a, kx = it.b;
     const int q0 = 2 * line, q1 = q0 + 1;
-    int par;
-    size_t ad = gaddr(q0, kx, par);
-    V a = static_cast<const V*>(A.eps[par])[ad];
+    const long long b0 = qbase[q0];
+    V a = static_cast<const V*>(A.eps[b0 >> 62])[(b0 & kOffMask) + (size_t)kx * NC];
     V b = zero;
     if (q1 < nreal) {
-      ad = gaddr(q1, kx, par);
-      b = static_cast<const V*>(A.eps[par])[ad];
+      const long long b1 = qbase[q1];
+      b = static_cast<const V*>(A.eps[b1 >> 62])[(b1 & kOffMask) + (size_t)kx * NC];
     }
     V* z = s + (size_t)line * n;
     if (kx == 0) {
@@ -198,13 +212,12 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   fft_dif<false, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
 
   // 3. constitutive update at every grid point of the task's rows
-  const int npts = t.nrows * n;
   const T lam0 = (T)c.lam0, mu2 = (T)(2.0 * c.mu0);
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
     Acc<T> acc[NC];
-    for (int p = threadIdx.x; p < npts; p += kThreads) {
-      const int rl = p / n, x = p - rl * n;
+    for (Iter2 it(threadIdx.x, kThreads, n); it.a < t.nrows; it.next()) {
+      const int rl = it.a, x = it.b;
       const int pos = HOM_LDG(sp.perm + x);
       const size_t vox = (size_t)(t.row0 + rl) * n + x;
       const uint32_t lab = HOM_LDG(A.label + c.vox_off + vox);
@@ -254,10 +267,8 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
       }
     }
     if (!OUT) {
-      double v[NC], tot[NC];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) v[k] = acc[k].value();
-      block_sum<NC>(v, tot);
+      double tot[NC];
+      block_sum<T, NC>(acc, tot);
       if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) A.partR[((size_t)blockIdx.x * A.L + l) * NC + k] = tot[k];
@@ -276,17 +287,16 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   fft_dit<true, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
   // 5. split the two real rows of each line and store the half spectra of tau
   V* tau = static_cast<V*>(A.tau);
-  for (int i = threadIdx.x; i < nlines * H; i += kThreads) {
-    const int line = i / H, kx = i - line * H;
+  for (Iter2 it(threadIdx.x, kThreads, H); it.a < nlines; it.next()) {
+    const int line = it.a, kx = it.b;
     const V* z = s + (size_t)line * n;
     const V zk = z[kx];
     const V zm = z[kx == 0 ? 0 : n - kx];
     const V a = mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));   // (Z[k] + conj Z[n-k]) / 2
     const V b = mk(T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x));   // (Z[k] - conj Z[n-k]) / 2i
     const int q0 = 2 * line;
-    int par;
-    tau[gaddr(q0, kx, par)] = a;
-    if (q0 + 1 < nreal) tau[gaddr(q0 + 1, kx, par)] = b;
+    tau[(qbase[q0] & kOffMask) + (size_t)kx * NC] = a;
+    if (q0 + 1 < nreal) tau[(qbase[q0 + 1] & kOffMask) + (size_t)kx * NC] = b;
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_ROW,
@@ -317,8 +327,8 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const V* in = static_cast<const V*>(A.tau);
   V* out = DIM == 2 ? static_cast<V*>(A.eps[(it + 1) & 1]) : static_cast<V*>(A.tau);
 
-  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
-    const int j = i / nl, w = i - j * nl;
+  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+    const int j = it.a, w = it.b;
     s[(size_t)w * n + j] = in[base + (size_t)j * rowstride + w];
   }
   __syncthreads();
@@ -330,6 +340,12 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const T lpm = (T)(c.lam0 + c.mu0);
   const T ratio = (T)((c.lam0 + c.mu0) / (c.lam0 + 2.0 * c.mu0));
   const T inv_nv = (T)(1.0 / (double)c.nv);
+  const T inv_mu0 = (T)(1.0 / c.mu0);
+  // 2 pi a(k) of the transformed axis, one entry per bin (after the lines in shared memory)
+  T* xi_tab = reinterpret_cast<T*>(s + (size_t)nl * n);
+  for (int k = threadIdx.x; k < n; k += kThreads) xi_tab[k] = two_pi * (T)signed_freq(k, n);
+  const T xi_fixed = DIM == 3 ? two_pi * (T)signed_freq(t.fixed, n) : T(0);
+  __syncthreads();
   const T rs2 = T(0.707106781186547524400844362105);
   const double* Eld = A.E + ((size_t)t.cell * A.L + t.load) * NC;
   V* gbuf = static_cast<V*>(A.g);
@@ -337,8 +353,8 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const size_t grow_stride = DIM == 2 ? (size_t)Hp * DIM : (size_t)n * Hp * DIM;
   const size_t gfix = DIM == 3 ? (size_t)t.fixed * Hp * DIM : 0;
   Acc<T> r2acc, rnacc;
-  for (int i = threadIdx.x; i < ntk * n; i += kThreads) {
-    const int kk = i / ntk, kxl = i - kk * ntk;
+  for (Iter2 it(threadIdx.x, kThreads, ntk); it.a < n; it.next()) {
+    const int kk = it.a, kxl = it.b;
     const int kx = t.kx0 + kxl;
     const int pos = HOM_LDG(sp.perm + kk);
     V* tv[NC];
@@ -346,12 +362,12 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     for (int k = 0; k < NC; ++k) tv[k] = s + (size_t)(kxl * NC + k) * n + pos;
     V* gp = gbuf + gbase + gfix + (size_t)kk * grow_stride + (size_t)kxl * DIM;
     T xi[DIM];
-    xi[0] = two_pi * (T)kx;
+    xi[0] = xi_tab[kx];  // kx <= (n-1)/2: the table entry is 2 pi kx
     if (DIM == 2) {
-      xi[1] = two_pi * (T)signed_freq(kk, n);
+      xi[1] = xi_tab[kk];
     } else {
-      xi[1] = two_pi * (T)signed_freq(t.fixed, n);
-      xi[DIM - 1] = two_pi * (T)signed_freq(kk, n);
+      xi[1] = xi_fixed;
+      xi[DIM - 1] = xi_tab[kk];
     }
     const bool k0 = kx == 0 && kk == 0 && (DIM == 2 || t.fixed == 0);
     if (k0) {
@@ -400,11 +416,12 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       r2 += r.x * r.x + r.y * r.y;
     }
     const T wgt = kx == 0 ? T(1) : T(2);
+    const T inv_q2 = T(1) / q2;
     r2acc.add(wgt * r2);
-    rnacc.add(wgt * r2 / q2);
+    rnacc.add(wgt * r2 * inv_q2);
     // g' = K0^-1 (tau_hat xi);  eps_hat' = -sym(xi (x) g') / N_v
-    const T inv_mq = T(1) / (mu0 * q2);
-    const T rq = ratio / q2;
+    const T inv_mq = inv_mu0 * inv_q2;
+    const T rq = ratio * inv_q2;
     V w[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -425,16 +442,17 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     }
   }
   {
-    double vv[2] = {r2acc.value(), rnacc.value()}, tot[2];
-    block_sum<2>(vv, tot);  // contains the barrier before the inverse transform
+    const Acc<T> vv[2] = {r2acc, rnacc};
+    double tot[2];
+    block_sum<T, 2>(vv, tot);  // contains the barrier before the inverse transform
     if (threadIdx.x == 0) {
       A.partC[2 * (size_t)blockIdx.x] = tot[0];
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
     }
   }
   fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
-  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
-    const int j = i / nl, w = i - j * nl;
+  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+    const int j = it.a, w = it.b;
     out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + j];
   }
   if (threadIdx.x == 0)
@@ -463,16 +481,16 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
                       (size_t)t.kx0 * NC;
   const V* in = static_cast<const V*>(A.tau);
   V* out = FWD ? static_cast<V*>(A.tau) : static_cast<V*>(A.eps[(it + 1) & 1]);
-  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
-    const int j = i / nl, w = i - j * nl;
+  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+    const int j = it.a, w = it.b;
     const int pos = FWD ? j : HOM_LDG(sp.perm + j);
     s[(size_t)w * n + pos] = in[base + (size_t)j * rowstride + w];
   }
   __syncthreads();
   if (FWD) fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
   else fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
-  for (int i = threadIdx.x; i < n * nl; i += kThreads) {
-    const int j = i / nl, w = i - j * nl;
+  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+    const int j = it.a, w = it.b;
     const int pos = FWD ? HOM_LDG(sp.perm + j) : j;
     out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + pos];
   }
@@ -683,17 +701,18 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     const size_t line_bytes = (size_t)k.n * vsize;  // one line; the twiddle table is one more
     auto row_lines = [&](int rows) { return (size_t)((rows * L * nc + 1) / 2) + 1; };
     int r = 1;
-    while (r < c.nrows && row_lines(r + 1) * line_bytes <= budget) ++r;
-    const size_t need_r = row_lines(r) * line_bytes;
+    while (r < c.nrows && row_lines(r + 1) * line_bytes + (size_t)(r + 1) * L * nc * sizeof(long long) <= budget) ++r;
+    const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * sizeof(long long);
     if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
     lay.smem_row = std::max(lay.smem_row, need_r);
     c.rtask0 = (int)lay.tR.size();
     for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), 0});
     c.rtask1 = (int)lay.tR.size();
     // Green-pass and y-pass tiles of kx
-    int ntk = (int)std::max<size_t>(1, (budget - std::min(budget, line_bytes)) / ((size_t)nc * line_bytes));
+    // Green/y tiles: ntk kx columns x nc lines, plus the twiddle table and the wave-number table
+    int ntk = (int)std::max<size_t>(1, (budget - std::min(budget, 2 * line_bytes)) / ((size_t)nc * line_bytes));
     ntk = std::min(ntk, c.H);
-    const size_t need_l = ((size_t)ntk * nc + 1) * line_bytes;
+    const size_t need_l = ((size_t)ntk * nc + 2) * line_bytes;
     if (need_l > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "line of n = %d does not fit on chip", k.n);
     lay.smem_green = std::max(lay.smem_green, need_l);
     lay.smem_y = std::max(lay.smem_y, need_l);
