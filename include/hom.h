@@ -216,6 +216,33 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 
+/* hom_solve for callers that cannot allocate device memory.  The paper has no counterpart: this is
+ * a deployment variant of hom_solve, not part of the method.
+ *
+ * Who needs it: callers whose device memory is owned by another allocator (a framework that
+ * reserved the GPU's memory up front for its caching allocator, where a foreign cudaMalloc fails
+ * or fragments the pool), callers under a hard per-process memory budget, and latency-sensitive
+ * callers that cannot afford the device-wide synchronisation of cudaFree.
+ *
+ * Same arguments, results and kernels as hom_solve, but the call makes no device allocation: the
+ * FFT plan tables and all solver scratch (mixed-domain state, partial sums, bookkeeping) live in
+ * one fixed array of 64 MiB in the library's device memory (every device that loads the library
+ * holds it until the process exits).  A batch needing more scratch than that is rejected with
+ * HOM_ERR_UNSUPPORTED_SIZE and a message giving both sizes.  Roughly, 2D FP32 scratch per cell is
+ * 88 * L * n * Hp bytes with Hp = (n+1)/2 rounded up to a multiple of 8 (one 405^2 cell with 3
+ * loads takes 22 MB and fits, one 1215^2 cell with 3 loads takes 195 MB and does not); FP64
+ * needs twice that, 3D cells n times more.
+ *   - opts->use_graph must be 0 and out->stats must be NULL (both would allocate);
+ *     HOM_ERR_INVALID_ARG otherwise.  Outputs in host memory are staged through the same array.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ *     caches it; make that first call outside any stream capture.
+ *   - Every call reuses the same array and leaves its contents behind; each call re-initialises
+ *     what it needs.  Calls whose GPU work overlaps (several streams or host threads at once) race
+ *     on the array: serialise them.
+ * Synchronises the stream before returning, like hom_solve. */
+int hom_solve_noalloc(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
+                      const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
+
 /* Effective stiffness from mean stresses: <sigma^(l)> = C_eff E^(l) for the L = nc linearly
  * independent load cases of each cell, so C_eff = S^T (E^T)^-1 (with the nc unit Mandel strains
  * as loads, column l of C_eff is <sigma^(l)>).  Computed in FP64 on the host.

@@ -36,8 +36,8 @@ HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
 KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "init"]
 
-EXPORTED = ["hom_filter_build", "hom_solve", "hom_effective_stiffness", "hom_last_error", "hom_release",
-            "hom_version"]
+EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_effective_stiffness", "hom_last_error",
+            "hom_release", "hom_version"]
 
 
 class HomError(RuntimeError):
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         h.hom_solve.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(hom_solve_opts), ctypes.POINTER(hom_result), ctypes.c_void_p]
+        h.hom_solve_noalloc.argtypes = h.hom_solve.argtypes
         h.hom_effective_stiffness.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
         h.hom_last_error.restype = ctypes.c_char_p
@@ -240,10 +241,17 @@ def hom_filter_build(cells: Sequence, phases: Sequence[Tuple[float, float]], dev
     raise HomError(HOM_ERR_CAPACITY, "mixed table did not fit after resizing")
 
 
+def hom_solve_noalloc(material: Material, E, c0, **kw) -> dict:
+    """hom_solve through the no-allocation entry point (fixed 64 MiB device scratch inside the
+    library; no graphs, no kernel statistics).  The output tensors are still allocated here, by
+    the caller side."""
+    return hom_solve(material, E, c0, _entry="hom_solve_noalloc", **kw)
+
+
 def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: int = HOM_FP64,
               criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
-              stats: bool = False, stream=None, allow_not_converged: bool = True) -> dict:
+              stats: bool = False, stream=None, allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
     """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
 
     E: [ncells, L, nc] (or [L, nc], shared by every cell) Mandel macroscopic strains.
@@ -285,7 +293,7 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                           check_every=int(check_every), diverge_window=int(diverge_window),
                           use_graph=int(bool(use_graph)))
     with torch.cuda.device(device):
-        code = lib().hom_solve(material.marshalled.cells, ncells, ctypes.byref(material.struct),
+        code = getattr(lib(), _entry)(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L,
                                c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
                                ctypes.byref(res), _stream_handle(stream))

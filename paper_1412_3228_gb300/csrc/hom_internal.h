@@ -35,6 +35,21 @@ int get_workspace(size_t bytes, void** ptr);
 // ------------------------------------------------------------------ validation
 bool grid_supported(int n);
 
+// ------------------------------------------------------------------ solver body
+// Caller-provided device scratch.  With a non-null base the solver places the FFT plan tables and
+// all of its scratch arrays in [base, base + capacity) and makes no device allocation; a call
+// that needs more than `capacity` bytes fails with HOM_ERR_UNSUPPORTED_SIZE.
+struct ExternalWorkspace {
+  unsigned char* base;
+  size_t capacity;
+};
+
+// Validation and dispatch shared by the hom_solve entry points (ext = nullptr: library-owned
+// plans and workspace).
+int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
+                const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
+                const ExternalWorkspace* ext);
+
 // ------------------------------------------------------------------ kernel descriptors
 struct FCell {           // one cell of the filter build
   int dim, n, matrix_phase, rule, S, nprim, prim0;

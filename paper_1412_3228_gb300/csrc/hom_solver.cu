@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "hom_internal.h"
+#include "hom_plan.h"
 
 namespace hom {
 namespace {
@@ -646,6 +647,7 @@ int allow_smem(K kernel, size_t bytes) {
 struct Layout {
   std::vector<CellDev> cells;
   std::vector<Plan> plans;
+  std::vector<HostPlan> host_plans;  // external workspace only: tables to upload with the call
   std::vector<TaskR> tR;
   std::vector<TaskL> tC, tY;
   std::vector<PairDev> pairs;
@@ -660,7 +662,7 @@ size_t smem_budget() {
 }
 
 int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize, int max_radix, const double* c0,
-                 Layout& lay) {
+                 bool external, Layout& lay) {
   const int nc = nc_of(dim);
   const size_t budget = smem_budget();
   const size_t kMaxSmem = 227 * 1024;
@@ -678,9 +680,22 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     c.nv = (long long)c.nrows * k.n;
     auto itp = std::find(plan_n.begin(), plan_n.end(), k.n);
     if (itp == plan_n.end()) {
-      Plan p;
-      int rc = get_plan(k.n, max_radix, &p);
-      if (rc != HOM_OK) return rc;
+      Plan p{};
+      if (external) {
+        HostPlan hp;
+        if (!build_host_plan(k.n, hp, max_radix) || (int)hp.radix.size() > kMaxStages)
+          return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7", k.n);
+        p.n = k.n;
+        p.nstage = (int)hp.radix.size();
+        for (int s2 = 0; s2 < p.nstage; ++s2) {
+          p.radix[s2] = hp.radix[s2];
+          p.span[s2] = hp.span[s2];
+        }
+        lay.host_plans.push_back(hp);  // table pointers are set once the scratch is carved
+      } else {
+        int rc = get_plan(k.n, max_radix, &p);
+        if (rc != HOM_OK) return rc;
+      }
       plan_n.push_back(k.n);
       lay.plans.push_back(p);
       c.plan = (int)lay.plans.size() - 1;
@@ -775,11 +790,11 @@ bool is_device_ptr(const void* p) {
 
 template <typename T, int DIM, int MAXR>
 int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L, const double* c0,
-              const hom_solve_opts* opts, hom_result* out, cudaStream_t st) {
+              const hom_solve_opts* opts, hom_result* out, cudaStream_t st, const ExternalWorkspace* ext) {
   using V = typename Cx<T>::V;
   const int nc = nc_of(DIM);
   Layout lay;
-  int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, lay);
+  int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
   const bool want_fields = out->eps || out->sigma;
@@ -808,10 +823,47 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
+  // external workspace: the plan tables (permutation, FP32 and FP64 twiddles) follow the scratch
+  std::vector<size_t> o_plan_tab(lay.host_plans.size());
+  for (size_t i = 0; i < lay.host_plans.size(); ++i) {
+    const size_t n = (size_t)lay.host_plans[i].n;
+    o_plan_tab[i] = take(n * sizeof(uint16_t));
+    take(n * sizeof(float2));
+    take(n * sizeof(double2));
+  }
   void* wsv = nullptr;
-  rc = get_workspace(off, &wsv);
-  if (rc != HOM_OK) return rc;
+  if (ext) {
+    if (off > ext->capacity)
+      return set_error(HOM_ERR_UNSUPPORTED_SIZE,
+                       "this batch needs %zu bytes of solver scratch; the fixed scratch array holds %zu bytes", off,
+                       ext->capacity);
+    wsv = ext->base;
+  } else {
+    rc = get_workspace(off, &wsv);
+    if (rc != HOM_OK) return rc;
+  }
   unsigned char* ws = static_cast<unsigned char*>(wsv);
+  for (size_t i = 0; i < lay.host_plans.size(); ++i) {
+    const HostPlan& hp = lay.host_plans[i];
+    const size_t n = (size_t)hp.n;
+    const size_t o_perm = o_plan_tab[i];
+    const size_t o_t32 = o_perm + (n * sizeof(uint16_t) + 255) / 256 * 256;
+    const size_t o_t64 = o_t32 + (n * sizeof(float2) + 255) / 256 * 256;
+    std::vector<float2> t32(n);
+    std::vector<double2> t64(n);
+    for (size_t t2 = 0; t2 < n; ++t2) {
+      t32[t2] = make_float2((float)hp.tw[2 * t2], (float)hp.tw[2 * t2 + 1]);
+      t64[t2] = make_double2(hp.tw[2 * t2], hp.tw[2 * t2 + 1]);
+    }
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_perm, hp.perm.data(), n * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_t32, t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_t64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st));
+    Plan& p = lay.plans[i];
+    p.perm = reinterpret_cast<const uint16_t*>(ws + o_perm);
+    p.tw32 = reinterpret_cast<const float2*>(ws + o_t32);
+    p.tw64 = reinterpret_cast<const double2*>(ws + o_t64);
+  }
+  if (ext) HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging vectors above go out of scope
   {
     std::vector<unsigned char> h(host_hi - host_lo, 0);
     auto put = [&](size_t o, const void* src, size_t b) {
@@ -1001,8 +1053,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
 using namespace hom;
 
-extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
-                         const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
+namespace hom {
+
+int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
+                const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
+                const ExternalWorkspace* ext) {
   if (!cells || ncells <= 0 || !mat || !E || !c0 || !opts || !out || !out->mean_sigma)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: null or empty argument");
   if (L < 1 || L > kMaxLoads) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: L must be in [1, %d]", kMaxLoads);
@@ -1032,11 +1087,18 @@ extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_materi
   const int r32 = env ? std::atoi(env) : 27;
   if (opts->precision == HOM_FP32) {
     if (r32 >= 45)
-      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st)
-                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st);
-    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st)
-                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st);
+      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
+                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
+    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
+                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
   }
-  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st)
-                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st);
+  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
+                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
+}
+
+}  // namespace hom
+
+extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
+                         const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
+  return solve_entry(cells, ncells, mat, E, L, c0, opts, out, stream, nullptr);
 }
