@@ -216,6 +216,34 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 
+/* Reverse-mode derivative of a loss L(C_eff, sigma) through the fixed point (section 2, eqs. 1-a,
+ * 1-b, 2) and the filter rules (eqs. 3, 4, 5-a, 5-b).  The paper does not differentiate its method;
+ * this is the implicit (adjoint) derivative of the discrete problem it solves.
+ *   cells, ncells, mat, c0, opts  as given to the forward hom_solve (opts->precision selects the
+ *                   field type; tol / max_iter / criterion apply to the adjoint solve, whose error
+ *                   is measured relative to its first residual)
+ *   L               load cases per cell of the forward solve
+ *   eps             device, forward strain fields [cell][load][nc][voxels] (hom_result.eps)
+ *   dL_dC           host [ncells][nc][nc] dL/dC_eff, or NULL.  Needs the nc unit Mandel loads in
+ *                   order (L == nc): then dC_ij/dc~(x) = eps^(i)(x) eps^(j)(x) / N_v exactly.
+ *   dL_dsigma       device [cell][load][nc][voxels] dL/dsigma(x) for every voxel, or NULL.  The
+ *                   adjoint field w (compatible, zero mean) solves w = -Gamma0 * ((c~-c0):w - c~:S)
+ *                   and contributes (S - w) (x) eps to dL/dc~(x).
+ *   dL_dctilde      device [sum voxels][ns] or NULL: dL/dc~(x), packed; entry (p <= q) is the
+ *                   derivative for c~_pq and c~_qp moving together (A_pq + A_qp for p < q).
+ *   dL_dphase       host [nphase][2]: dL/dlambda, dL/dmu of every phase, through the rule of every
+ *                   voxel (pure voxels: c = lambda 1(x)1 + 2 mu I; mixed voxels: the rule's
+ *                   forward-mode derivative).  Balls holding more than two phases are not supported.
+ *   dL_dfrac        device [mat->mixed_count] or NULL: dL/df of each mixed entry (f = fraction of
+ *                   its second phase, the first one taking 1 - f).
+ *   adjoint_info    optional: iterations / status / err / err_n of the adjoint solves
+ * Returns HOM_OK, or HOM_ERR_NOT_CONVERGED if an adjoint solve reached max_iter (outputs written).
+ * Synchronises the stream. */
+int hom_solve_backward(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* c0, int32_t L,
+                       const hom_solve_opts* opts, const void* eps, const double* dL_dC, const void* dL_dsigma,
+                       void* dL_dctilde, double* dL_dphase, double* dL_dfrac, hom_result* adjoint_info,
+                       void* stream);
+
 /* hom_solve for callers that cannot allocate device memory.  The paper has no counterpart: this is
  * a deployment variant of hom_solve, not part of the method.
  *

@@ -36,8 +36,8 @@ HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
 KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "init"]
 
-EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_effective_stiffness", "hom_last_error",
-            "hom_release", "hom_version"]
+EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_solve_backward", "hom_effective_stiffness",
+            "hom_last_error", "hom_release", "hom_version"]
 
 
 class HomError(RuntimeError):
@@ -103,6 +103,11 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(hom_solve_opts), ctypes.POINTER(hom_result), ctypes.c_void_p]
         h.hom_solve_noalloc.argtypes = h.hom_solve.argtypes
+        h.hom_solve_backward.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                         ctypes.POINTER(hom_solve_opts), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(hom_result), ctypes.c_void_p]
         h.hom_effective_stiffness.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
         h.hom_last_error.restype = ctypes.c_char_p
@@ -306,6 +311,90 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                                               bytes=float(st.bytes[k])) for k in range(HOM_NKERNEL)}
         out["voxel_iterations"] = float(st.voxel_iterations)
     return out
+
+
+def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_dsigma: Optional[torch.Tensor] = None,
+                       want_ctilde: bool = True, want_frac: bool = True, precision: int = HOM_FP64,
+                       criterion: int = HOM_CRIT_E, tol: float = 1e-10, max_iter: int = 2000, stream=None) -> dict:
+    """Adjoint derivative of L(C_eff, sigma) (see include/hom.h).  `forward` is the dict returned by
+    hom_solve (with device fields); dL_dC is [ncells, nc, nc] (host), dL_dsigma a device tensor laid
+    out like forward['sigma'].  Returns dctilde [sum voxels, ns] (device), dphase [nphase, 2],
+    dfrac [mixed_count] (device) and the adjoint solve's iterations / status."""
+    cells = material.cells
+    ncells = len(cells)
+    dim = material.dim
+    nc = nc_of(dim)
+    L = forward["L"]
+    c0 = np.ascontiguousarray(np.broadcast_to(np.asarray(c0, dtype=np.float64), (ncells, 2)))
+    device = material.label.device
+    ftype = torch.float32 if precision == HOM_FP32 else torch.float64
+    eps = forward["eps"]
+    if eps is None or not eps.is_cuda or eps.dtype != ftype:
+        raise ValueError("forward eps fields must be device tensors of the solve precision")
+    nvox = sum(c.n ** c.dim for c in cells)
+    dct = torch.empty(nvox * ns_of(dim), dtype=ftype, device=device) if want_ctilde else None
+    dfr = torch.zeros(max(1, material.mixed_count), dtype=torch.float64, device=device) if want_frac else None
+    dph = np.zeros((material.struct.nphase, 2))
+    G = None
+    if dL_dC is not None:
+        G = np.ascontiguousarray(np.asarray(dL_dC, dtype=np.float64).reshape(ncells, nc, nc))
+    if dL_dsigma is not None and (not dL_dsigma.is_cuda or dL_dsigma.dtype != ftype):
+        raise ValueError("dL_dsigma must be a device tensor of the solve precision")
+    iters = np.zeros((ncells, L), dtype=np.int32)
+    status = np.zeros((ncells, L), dtype=np.int32)
+    err = np.zeros((ncells, L))
+    err_n = np.zeros((ncells, L))
+    info = hom_result(iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
+                      err_n=err_n.ctypes.data)
+    opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
+                          check_every=0, diverge_window=0, use_graph=0)
+    with torch.cuda.device(device):
+        code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
+                                        c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),
+                                        ctypes.c_void_p(eps.data_ptr()),
+                                        None if G is None else ctypes.c_void_p(G.ctypes.data),
+                                        None if dL_dsigma is None else ctypes.c_void_p(dL_dsigma.data_ptr()),
+                                        None if dct is None else ctypes.c_void_p(dct.data_ptr()),
+                                        ctypes.c_void_p(dph.ctypes.data),
+                                        None if dfr is None else ctypes.c_void_p(dfr.data_ptr()),
+                                        ctypes.byref(info), _stream_handle(stream))
+    _check(code, (HOM_OK, HOM_ERR_NOT_CONVERGED))
+    return dict(dctilde=dct, dphase=dph, dfrac=None if dfr is None else dfr[:material.mixed_count],
+                adjoint_iterations=iters, adjoint_status=status, adjoint_err=err, adjoint_err_n=err_n, code=code)
+
+
+class HomSolve(torch.autograd.Function):
+    """C_eff (and the local stress fields) of a batch of cells as a differentiable function of the
+    phase Lame constants.  Forward: hom_filter_build + hom_solve with the nc unit Mandel loads +
+    hom_effective_stiffness.  Backward: hom_solve_backward (adjoint solve, no iterate history).
+
+        C, sigma = HomSolve.apply(phase_lame, cells, c0, settings)
+    phase_lame: float64 tensor [nphase, 2] (lambda, mu); c0: [ncells, 2] reference media (held fixed:
+    the converged discrete solution does not depend on c0); settings: dict of hom_solve keywords.
+    Returns C [ncells, nc, nc] (float64, CPU) and sigma (device, layout of hom_solve's fields)."""
+
+    @staticmethod
+    def forward(ctx, phase_lame, cells, c0, settings):
+        ctx.set_materialize_grads(False)
+        phases = [tuple(map(float, row)) for row in phase_lame.detach().cpu().tolist()]
+        mat = hom_filter_build(cells, phases)
+        dim = mat.dim
+        E = np.eye(nc_of(dim))
+        res = hom_solve(mat, E, c0, fields=True, **settings)
+        C = hom_effective_stiffness(E, res["mean_sigma"], dim)
+        ctx.mat, ctx.res, ctx.c0, ctx.settings = mat, res, c0, settings
+        return torch.from_numpy(C), res["sigma"]
+
+    @staticmethod
+    def backward(ctx, gC, gsigma):
+        st = ctx.settings
+        g = hom_solve_backward(ctx.mat, ctx.res, ctx.c0,
+                               dL_dC=None if gC is None else gC.detach().cpu().numpy(),
+                               dL_dsigma=None if gsigma is None else gsigma.detach().contiguous(),
+                               want_ctilde=False, want_frac=False, precision=st.get("precision", HOM_FP64),
+                               criterion=st.get("criterion", HOM_CRIT_E), tol=st.get("tol", 1e-10),
+                               max_iter=st.get("max_iter", 2000))
+        return torch.from_numpy(g["dphase"]), None, None, None
 
 
 def hom_effective_stiffness(E, mean_sigma, dim: int) -> np.ndarray:

@@ -138,6 +138,7 @@ extern "C" void hom_release(void) {
     if (kv.second.ws) cudaFree(kv.second.ws);
   }
   g_cache.clear();
+  release_backward_buffers();
   cudaSetDevice(cur);
 }
 

@@ -346,48 +346,4 @@ HOM_HD int packed_index(int nc, int I, int J) {
   return I * nc - I * (I - 1) / 2 + (J - I);
 }
 
-// ------------------------------------------------------------------ small dense FP64 algebra
-// In-place inverse of an m x m matrix (row-major, m <= 6) by Gauss-Jordan with partial pivoting.
-// Returns false if a pivot vanishes.
-HOM_HD bool inv_small(double* A, int m) {
-  double Ainv[36];
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) Ainv[i * m + j] = (i == j) ? 1.0 : 0.0;
-  for (int c = 0; c < m; ++c) {
-    int piv = c;
-    double best = A[c * m + c] < 0 ? -A[c * m + c] : A[c * m + c];
-    for (int r = c + 1; r < m; ++r) {
-      double v = A[r * m + c] < 0 ? -A[r * m + c] : A[r * m + c];
-      if (v > best) { best = v; piv = r; }
-    }
-    if (!(best > 0.0)) return false;
-    if (piv != c) {
-      for (int j = 0; j < m; ++j) {
-        double t = A[c * m + j]; A[c * m + j] = A[piv * m + j]; A[piv * m + j] = t;
-        t = Ainv[c * m + j]; Ainv[c * m + j] = Ainv[piv * m + j]; Ainv[piv * m + j] = t;
-      }
-    }
-    const double d = 1.0 / A[c * m + c];
-    for (int j = 0; j < m; ++j) { A[c * m + j] *= d; Ainv[c * m + j] *= d; }
-    for (int r = 0; r < m; ++r) {
-      if (r == c) continue;
-      const double f = A[r * m + c];
-      if (f == 0.0) continue;
-      for (int j = 0; j < m; ++j) { A[r * m + j] -= f * A[c * m + j]; Ainv[r * m + j] -= f * Ainv[c * m + j]; }
-    }
-  }
-  for (int i = 0; i < m * m; ++i) A[i] = Ainv[i];
-  return true;
-}
-
-// C = A * B (m x k) * (k x p), row-major
-HOM_HD void matmul(const double* A, const double* B, double* C, int m, int k, int p) {
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < p; ++j) {
-      double s = 0.0;
-      for (int t = 0; t < k; ++t) s += A[i * k + t] * B[t * p + j];
-      C[i * p + j] = s;
-    }
-}
-
 }  // namespace hom

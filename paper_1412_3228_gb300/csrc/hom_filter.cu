@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "hom_internal.h"
+#include "hom_rules.cuh"
 
 namespace hom {
 namespace {
@@ -48,118 +49,6 @@ __device__ bool inside_exact(const FPrim& p, const double* su, int dim, double P
     q = dadd(q, dmul(w, w));
   }
   return q <= Ru2;
-}
-
-// Packed isotropic Mandel stiffness (plane strain in 2D).
-__device__ void iso_full(double lam, double mu, int dim, double* C) {
-  const int nc = nc_of(dim);
-  for (int i = 0; i < nc * nc; ++i) C[i] = 0.0;
-  for (int i = 0; i < nc; ++i) C[i * nc + i] = 2.0 * mu;
-  for (int i = 0; i < dim; ++i)
-    for (int j = 0; j < dim; ++j) C[i * nc + j] += lam;
-}
-
-// Mandel rotation Q (eps' = Q eps) for the orthonormal rows R (local axes).
-__device__ void mandel_rotation(const double* R, int dim, double* Q) {
-  const int nc = nc_of(dim);
-  const double s2 = 1.4142135623730950488;
-  for (int I = 0; I < nc; ++I) {
-    int i, j;
-    mandel_pair(dim, I, i, j);
-    const double wI = (i == j) ? 1.0 : s2;
-    for (int J = 0; J < nc; ++J) {
-      int p, q;
-      mandel_pair(dim, J, p, q);
-      const double wJ = (p == q) ? 1.0 : s2;
-      double v = R[i * dim + p] * R[j * dim + q];
-      if (p != q) v += R[i * dim + q] * R[j * dim + p];
-      Q[I * nc + J] = wI / wJ * v;
-    }
-  }
-}
-
-// 2-layer laminate (eqs. 5-a, 5-b) by the block formula in the interface frame:
-//   A = <C_OO^-1>, B = <C_OO^-1 C_OP>, D = <C_PP - C_PO C_OO^-1 C_OP>
-//   C~_OO = A^-1, C~_OP = A^-1 B, C~_PP = D + B^T A^-1 B.
-__device__ bool two_layer(const double* Ca, const double* Cb, double fa, double fb, const double* nrm, int dim,
-                          double* Cout) {
-  const int nc = nc_of(dim);
-  double R[9];
-  if (dim == 2) {
-    R[0] = nrm[1]; R[1] = -nrm[0];
-    R[2] = nrm[0]; R[3] = nrm[1];
-  } else {
-    int m = 0;
-    double am = fabs(nrm[0]);
-    for (int k = 1; k < 3; ++k)
-      if (fabs(nrm[k]) < am) { am = fabs(nrm[k]); m = k; }
-    double e[3] = {0, 0, 0};
-    e[m] = 1.0;
-    double t1[3] = {nrm[1] * e[2] - nrm[2] * e[1], nrm[2] * e[0] - nrm[0] * e[2], nrm[0] * e[1] - nrm[1] * e[0]};
-    double l = sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
-    for (int k = 0; k < 3; ++k) t1[k] /= l;
-    double t2[3] = {nrm[1] * t1[2] - nrm[2] * t1[1], nrm[2] * t1[0] - nrm[0] * t1[2], nrm[0] * t1[1] - nrm[1] * t1[0]};
-    for (int k = 0; k < 3; ++k) { R[k] = t1[k]; R[3 + k] = t2[k]; R[6 + k] = nrm[k]; }
-  }
-  double Q[36], QT[36], tmp[36], La[36], Lb[36];
-  mandel_rotation(R, dim, Q);
-  for (int i = 0; i < nc; ++i)
-    for (int j = 0; j < nc; ++j) QT[i * nc + j] = Q[j * nc + i];
-  matmul(Q, Ca, tmp, nc, nc, nc); matmul(tmp, QT, La, nc, nc, nc);
-  matmul(Q, Cb, tmp, nc, nc, nc); matmul(tmp, QT, Lb, nc, nc, nc);
-  // in-plane (P) and out-of-plane (O) local components
-  int Pi[3], Oi[3], nP = 0, nO = 0;
-  for (int I = 0; I < nc; ++I) {
-    int i, j;
-    mandel_pair(dim, I, i, j);
-    if (i == dim - 1 || j == dim - 1) Oi[nO++] = I; else Pi[nP++] = I;
-  }
-  double A[9] = {0}, B[9] = {0}, D[9] = {0};
-  const double* Ls[2] = {La, Lb};
-  const double fs[2] = {fa, fb};
-  for (int k = 0; k < 2; ++k) {
-    const double* L = Ls[k];
-    double OO[9], OP[9], PP[9];
-    for (int a = 0; a < nO; ++a)
-      for (int b = 0; b < nO; ++b) OO[a * nO + b] = L[Oi[a] * nc + Oi[b]];
-    for (int a = 0; a < nO; ++a)
-      for (int b = 0; b < nP; ++b) OP[a * nP + b] = L[Oi[a] * nc + Pi[b]];
-    for (int a = 0; a < nP; ++a)
-      for (int b = 0; b < nP; ++b) PP[a * nP + b] = L[Pi[a] * nc + Pi[b]];
-    if (!inv_small(OO, nO)) return false;
-    double OiOP[9];
-    matmul(OO, OP, OiOP, nO, nO, nP);
-    for (int a = 0; a < nO * nO; ++a) A[a] += fs[k] * OO[a];
-    for (int a = 0; a < nO * nP; ++a) B[a] += fs[k] * OiOP[a];
-    // C_PO C_OO^-1 C_OP = OP^T (OO^-1 OP)
-    for (int a = 0; a < nP; ++a)
-      for (int b = 0; b < nP; ++b) {
-        double s = 0.0;
-        for (int t = 0; t < nO; ++t) s += OP[t * nP + a] * OiOP[t * nP + b];
-        D[a * nP + b] += fs[k] * (PP[a * nP + b] - s);
-      }
-  }
-  if (!inv_small(A, nO)) return false;  // A now holds A^-1 = C~_OO
-  double AB[9];
-  matmul(A, B, AB, nO, nO, nP);  // C~_OP
-  double loc[36];
-  for (int a = 0; a < nO; ++a)
-    for (int b = 0; b < nO; ++b) loc[Oi[a] * nc + Oi[b]] = A[a * nO + b];
-  for (int a = 0; a < nO; ++a)
-    for (int b = 0; b < nP; ++b) {
-      loc[Oi[a] * nc + Pi[b]] = AB[a * nP + b];
-      loc[Pi[b] * nc + Oi[a]] = AB[a * nP + b];
-    }
-  for (int a = 0; a < nP; ++a)
-    for (int b = 0; b < nP; ++b) {
-      double s = 0.0;
-      for (int t = 0; t < nO; ++t) s += B[t * nP + a] * AB[t * nP + b];
-      loc[Pi[a] * nc + Pi[b]] = D[a * nP + b] + s;
-    }
-  // back to the global frame: C = Q^T C' Q
-  matmul(QT, loc, tmp, nc, nc, nc);
-  matmul(tmp, Q, Cout, nc, nc, nc);
-  return true;
 }
 
 struct FilterArgs {
@@ -309,33 +198,12 @@ __global__ void __launch_bounds__(kThreads) k_filter(FilterArgs A) {
   double Cs[kMaxPhases][36];
   double fs[kMaxPhases];
   for (int k = 0; k < nph; ++k) {
-    iso_full(A.phase_lame[2 * ph_id[k]], A.phase_lame[2 * ph_id[k] + 1], dim, Cs[k]);
+    iso_full_t<double>(A.phase_lame[2 * ph_id[k]], A.phase_lame[2 * ph_id[k] + 1], dim, Cs[k]);
     fs[k] = (double)ph_cnt[k] / (double)M;
   }
   double Ct[36];
-  int rule = cell.rule;
-  if (rule == HOM_RULE_TWO_LAYER) {
-    if (nph != 2) { atomicExch(A.err_flag, 1); return; }
-    if (!nrm_ok || !two_layer(Cs[0], Cs[1], fs[0], fs[1], nrm, dim, Ct)) rule = HOM_RULE_VOIGT;
-  }
-  if (rule == HOM_RULE_VOIGT) {
-    for (int i = 0; i < nc * nc; ++i) {
-      double s = 0.0;
-      for (int k = 0; k < nph; ++k) s += fs[k] * Cs[k][i];
-      Ct[i] = s;
-    }
-  } else if (rule == HOM_RULE_REUSS) {
-    double acc[36];
-    for (int i = 0; i < nc * nc; ++i) acc[i] = 0.0;
-    for (int k = 0; k < nph; ++k) {
-      double inv[36];
-      for (int i = 0; i < nc * nc; ++i) inv[i] = Cs[k][i];
-      inv_small(inv, nc);
-      for (int i = 0; i < nc * nc; ++i) acc[i] += fs[k] * inv[i];
-    }
-    inv_small(acc, nc);
-    for (int i = 0; i < nc * nc; ++i) Ct[i] = acc[i];
-  }
+  const int rule = apply_rule_t<double>(cell.rule, nph, Cs, fs, nrm_ok, nrm, dim, Ct);
+  if (rule < 0) { atomicExch(A.err_flag, 1); return; }
   const unsigned long long m = atomicAdd(A.mixed_counter, 1ull);
   if ((long long)m >= A.mat.mixed_capacity) {
     *label = HOM_MIXED_BIT;  // placeholder: the caller must grow the table and rebuild

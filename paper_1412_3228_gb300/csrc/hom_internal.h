@@ -31,6 +31,7 @@ int get_plan(int n, int max_radix, Plan* out);
 
 // Device scratch owned by the library (grown on demand, freed by hom_release).
 int get_workspace(size_t bytes, void** ptr);
+void release_backward_buffers();
 
 // ------------------------------------------------------------------ validation
 bool grid_supported(int n);
@@ -44,11 +45,19 @@ struct ExternalWorkspace {
   size_t capacity;
 };
 
+// Adjoint Lippmann-Schwinger solve (used by hom_solve_backward): the same fixed point driven by a
+// stress-sensitivity source S (real field, layout of the solver output fields) with zero mean
+// strain.  The constitutive step becomes sigma' = c~ : (w - S), tau' = sigma' - c0 : w, and the
+// stopping rule is relative to the residual of the first iterate (w = 0).
+struct AdjointSpec {
+  const void* source;  // device, [cell][load][nc][voxels] in the solve precision
+};
+
 // Validation and dispatch shared by the hom_solve entry points (ext = nullptr: library-owned
-// plans and workspace).
+// plans and workspace; adj = nullptr: forward solve).
 int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
                 const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
-                const ExternalWorkspace* ext);
+                const ExternalWorkspace* ext, const AdjointSpec* adj = nullptr);
 
 // ------------------------------------------------------------------ kernel descriptors
 struct FCell {           // one cell of the filter build

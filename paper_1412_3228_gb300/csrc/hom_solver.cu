@@ -67,6 +67,8 @@ struct SolveArgs {
   double tol;
   void* out_eps;
   void* out_sig;
+  const void* src;  // adjoint source S (nullptr for the forward solve)
+  double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
 };
 
 template <typename T> __device__ __forceinline__ const T* mixed_tab(const SolveArgs& A);
@@ -235,12 +237,20 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         const V zz = s[(size_t)(q >> 1) * n + pos];
         e[k] = (q & 1) ? zz.y : zz.x;
       }
+      T ee[NC];  // strain the stiffness acts on: eps, or w - S in the adjoint solve
+#pragma unroll
+      for (int k = 0; k < NC; ++k) ee[k] = e[k];
+      if (A.src) {
+        const T* S = static_cast<const T*>(A.src) + c.fld_off + (size_t)l * NC * c.nv + vox;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) ee[k] -= S[(size_t)k * c.nv];
+      }
       T sg[NC];
 #pragma unroll
       for (int I = 0; I < NC; ++I) {
         T acc_i = T(0);
 #pragma unroll
-        for (int J = 0; J < NC; ++J) acc_i += C[packed_index(NC, I, J)] * e[J];
+        for (int J = 0; J < NC; ++J) acc_i += C[packed_index(NC, I, J)] * ee[J];
         sg[I] = acc_i;
       }
       if (OUT) {
@@ -545,8 +555,20 @@ __global__ void __launch_bounds__(kThreads) k_control(SolveArgs A, int nc) {
         A.mean_sigma[(size_t)warp * nc + k] = tot / (double)c.nv;
         den2 += tot * tot;
       }
-      const double den = sqrt(den2);
-      const double e = sqrt(r2) / den, en = sqrt(rn2) / den;
+      double e, en;
+      if (A.res0) {  // adjoint: relative to the first iterate's residual
+        if (it == 0) {
+          A.res0[2 * warp] = r2;
+          A.res0[2 * warp + 1] = rn2;
+        }
+        const double d0 = A.res0[2 * warp], d1 = A.res0[2 * warp + 1];
+        e = d0 > 0.0 ? sqrt(r2 / d0) : 0.0;
+        en = d1 > 0.0 ? sqrt(rn2 / d1) : 0.0;
+      } else {
+        const double den = sqrt(den2);
+        e = sqrt(r2) / den;
+        en = sqrt(rn2) / den;
+      }
       A.err[warp] = e;
       A.errn[warp] = en;
       const double crit = A.criterion == HOM_CRIT_E ? e : en;
@@ -790,7 +812,8 @@ bool is_device_ptr(const void* p) {
 
 template <typename T, int DIM, int MAXR>
 int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L, const double* c0,
-              const hom_solve_opts* opts, hom_result* out, cudaStream_t st, const ExternalWorkspace* ext) {
+              const hom_solve_opts* opts, hom_result* out, cudaStream_t st, const ExternalWorkspace* ext,
+              const AdjointSpec* adj) {
   using V = typename Cx<T>::V;
   const int nc = nc_of(DIM);
   Layout lay;
@@ -820,6 +843,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_int = take((size_t)npairs * 4 * sizeof(int) + 64);
   const size_t o_dbl = take((size_t)npairs * (3 + nc) * sizeof(double));
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
+  const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
@@ -923,6 +947,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.tol = opts->tol;
   A.out_eps = out->eps ? (eps_dev ? out->eps : (void*)(ws + o_stage_e)) : nullptr;
   A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
+  A.src = adj ? adj->source : nullptr;
+  A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
 
   if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
   if ((rc = allow_smem(k_row<T, DIM, true, MAXR>, lay.smem_row)) != HOM_OK) return rc;
@@ -1057,7 +1083,7 @@ namespace hom {
 
 int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
                 const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
-                const ExternalWorkspace* ext) {
+                const ExternalWorkspace* ext, const AdjointSpec* adj) {
   if (!cells || ncells <= 0 || !mat || !E || !c0 || !opts || !out || !out->mean_sigma)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: null or empty argument");
   if (L < 1 || L > kMaxLoads) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: L must be in [1, %d]", kMaxLoads);
@@ -1087,13 +1113,13 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   const int r32 = env ? std::atoi(env) : 27;
   if (opts->precision == HOM_FP32) {
     if (r32 >= 45)
-      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
-                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
-    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
-                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
+      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
+                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
+    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
+                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
   }
-  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext)
-                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext);
+  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
+                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
 }
 
 }  // namespace hom
