@@ -125,35 +125,44 @@ def _periodic_dist(a: np.ndarray, b: np.ndarray) -> float:
 
 def rsa_spheres_cell(n: int, seed: int, vf: float = 0.3, rmin: float = 0.05, rmax: float = 0.1,
                      rule: int = RULE_TWO_LAYER, radius_px: float = 1.0, subgrid: int = 8,
-                     gap_voxels: float = 2.0, max_tries: int = 200000) -> Cell:
+                     gap_voxels: float = 2.0, batches: int = 400) -> Cell:
     """3D random sequential addition of non-overlapping spheres (periodic minimum image).
 
-    Radii are drawn uniformly in [rmin, rmax]; spheres are added until the total volume
-    reaches vf, and the last radius is shrunk so that the total is exactly vf.  Two spheres
-    keep a surface gap of at least gap_voxels / n.
-    """
+    Radii are drawn uniformly in [rmin, rmax]; spheres are added until the total volume reaches
+    vf, and the last radius is shrunk so that the total is exactly vf.  Two spheres keep a surface
+    gap of at least gap_voxels / n.  Candidate centres are tried in seeded batches of 256; a
+    sphere that finds no room after `batches` // 8 batches is shrunk by 5 % (not below rmin)."""
     rng = np.random.default_rng(seed)
     gap = gap_voxels / n
-    centres: List[np.ndarray] = []
-    radii: List[float] = []
+    centres = np.zeros((0, 3))
+    radii = np.zeros(0)
     vol = 0.0
-    tries = 0
-    while vol < vf:
+    while vol < vf - 1e-15:
         r = float(rng.uniform(rmin, rmax))
         rem = vf - vol
         if 4.0 / 3.0 * math.pi * r ** 3 >= rem:
             r = (rem * 3.0 / (4.0 * math.pi)) ** (1.0 / 3.0)
-        while True:
-            tries += 1
-            if tries > max_tries:
-                raise RuntimeError("sphere packing failed; lower vf or the gap")
-            c = rng.uniform(0.0, 1.0, size=3)
-            if all(_periodic_dist(c, cj) >= r + rj + gap for cj, rj in zip(centres, radii)):
+        placed = None
+        for b in range(batches):
+            if b > 0 and b % max(1, batches // 8) == 0:
+                r = max(rmin, 0.95 * r) if r > rmin else r
+            cand = rng.uniform(0.0, 1.0, size=(256, 3))
+            if centres.shape[0] == 0:
+                placed = cand[0]
                 break
-        centres.append(c)
-        radii.append(r)
+            d = np.abs(cand[:, None, :] - centres[None, :, :])
+            d = np.minimum(d, 1.0 - d)
+            dist = np.sqrt(np.sum(d * d, axis=-1))
+            ok = np.all(dist >= r + radii[None, :] + gap, axis=1)
+            if np.any(ok):
+                placed = cand[int(np.argmax(ok))]
+                break
+        if placed is None:
+            raise RuntimeError("sphere packing failed; lower vf or the gap")
+        centres = np.vstack([centres, placed[None, :]])
+        radii = np.append(radii, r)
         vol += 4.0 / 3.0 * math.pi * r ** 3
-    prims = [Primitive(PRIM_SPHERE, 1, (float(c[0]), float(c[1]), float(c[2])), r)
+    prims = [Primitive(PRIM_SPHERE, 1, (float(c[0]), float(c[1]), float(c[2])), float(r))
              for c, r in zip(centres, radii)]
     return Cell(3, n, 0, prims, rule, radius_px, subgrid)
 

@@ -179,6 +179,9 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   // Real row q = (row, active load, component) -> element offset of its half spectrum at kx = 0;
   // the top bit carries the eps buffer parity of its load.
   long long* qbase = reinterpret_cast<long long*>(s + (size_t)nlines * n);
+  // per real row: kx = 0 entry of the stored eps (the row mean) and of the transformed tau (the row sum)
+  T* dc_eps = reinterpret_cast<T*>(qbase + nreal);
+  T* dc_tau = dc_eps + nreal;
   for (int q = threadIdx.x; q < nreal; q += kThreads) {
     const int per_row = nal * NC;
     const int rl = q / per_row;
@@ -205,6 +208,8 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
     V* z = s + (size_t)line * n;
     if (kx == 0) {
       z[0] = mk(a.x, b.x);
+      dc_eps[q0] = a.x;
+      if (q1 < nreal) dc_eps[q1] = b.x;
     } else {
       z[kx] = mk(a.x - b.y, a.y + b.x);      // A + iB
       z[n - kx] = mk(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
@@ -214,21 +219,28 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   // 2. inverse x-DFT (natural -> digit-reversed positions)
   fft_dif<false, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
 
-  // 3. constitutive update at every grid point of the task's rows
-  const T lam0 = (T)c.lam0, mu2 = (T)(2.0 * c.mu0);
-  for (int la = 0; la < nal; ++la) {
-    const int l = s_al[la];
-    Acc<T> acc[NC];
-    for (Iter2 it(threadIdx.x, kThreads, n); it.a < t.nrows; it.next()) {
-      const int rl = it.a, x = it.b;
-      const int pos = HOM_LDG(sp.perm + x);
-      const size_t vox = (size_t)(t.row0 + rl) * n + x;
-      const uint32_t lab = HOM_LDG(A.label + c.vox_off + vox);
-      const T* src = (lab & HOM_MIXED_BIT) ? mixed_tab<T>(A) + (size_t)(lab & ~HOM_MIXED_BIT) * NS
-                                           : phase_tab<T>(A) + (size_t)lab * NS;
-      T C[NS];
+  // 3. constitutive update at every grid point of the task's rows: the material is read once per
+  // voxel for all loads; pure voxels use sigma = lam tr(eps) I + 2 mu eps, mixed ones the packed c~.
+  const T lam0 = (T)c.lam0, mu2_0 = (T)(2.0 * c.mu0);
+  for (Iter2 it(threadIdx.x, kThreads, n); it.a < t.nrows; it.next()) {
+    const int rl = it.a, x = it.b;
+    const int pos = HOM_LDG(sp.perm + x);
+    const size_t vox = (size_t)(t.row0 + rl) * n + x;
+    const uint32_t lab = HOM_LDG(A.label + c.vox_off + vox);
+    const bool mixed = (lab & HOM_MIXED_BIT) != 0;
+    T C[NS];
+    T lam = T(0), mu2 = T(0);
+    if (mixed) {
+      const T* src = mixed_tab<T>(A) + (size_t)(lab & ~HOM_MIXED_BIT) * NS;
 #pragma unroll
       for (int k = 0; k < NS; ++k) C[k] = HOM_LDG(src + k);
+    } else {
+      const T* src = phase_tab<T>(A) + (size_t)lab * NS;
+      lam = HOM_LDG(src + 1);                 // c_01 = lambda
+      mu2 = HOM_LDG(src) - lam;               // c_00 - c_01 = 2 mu
+    }
+    for (int la = 0; la < nal; ++la) {
+      const int l = s_al[la];
       T e[NC];
       const int q0 = (rl * nal + la) * NC;
 #pragma unroll
@@ -246,12 +258,21 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         for (int k = 0; k < NC; ++k) ee[k] -= S[(size_t)k * c.nv];
       }
       T sg[NC];
+      if (mixed) {
 #pragma unroll
-      for (int I = 0; I < NC; ++I) {
-        T acc_i = T(0);
+        for (int I = 0; I < NC; ++I) {
+          T acc_i = T(0);
 #pragma unroll
-        for (int J = 0; J < NC; ++J) acc_i += C[packed_index(NC, I, J)] * ee[J];
-        sg[I] = acc_i;
+          for (int J = 0; J < NC; ++J) acc_i += C[packed_index(NC, I, J)] * ee[J];
+          sg[I] = acc_i;
+        }
+      } else {
+        T tr = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) tr += ee[k];
+        const T ltr = lam * tr;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) sg[k] = mu2 * ee[k] + (k < DIM ? ltr : T(0));
       }
       if (OUT) {
         const size_t base = c.fld_off + (size_t)l * NC * c.nv + vox;
@@ -266,23 +287,14 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         T tr = T(0);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) tr += e[k];
+        const T ltr0 = lam0 * tr;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          const T c0e = mu2 * e[k] + (k < DIM ? lam0 * tr : T(0));
-          const T tau = sg[k] - c0e;
+          const T tau = sg[k] - (mu2_0 * e[k] + (k < DIM ? ltr0 : T(0)));
           const int q = q0 + k;
           V* zz = s + (size_t)(q >> 1) * n + pos;
           if (q & 1) zz->y = tau; else zz->x = tau;
-          acc[k].add(sg[k]);
         }
-      }
-    }
-    if (!OUT) {
-      double tot[NC];
-      block_sum<T, NC>(acc, tot);
-      if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) A.partR[((size_t)blockIdx.x * A.L + l) * NC + k] = tot[k];
       }
     }
   }
@@ -308,6 +320,27 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
     const int q0 = 2 * line;
     tau[(qbase[q0] & kOffMask) + (size_t)kx * NC] = a;
     if (q0 + 1 < nreal) tau[(qbase[q0 + 1] & kOffMask) + (size_t)kx * NC] = b;
+    if (kx == 0) {
+      dc_tau[q0] = a.x;
+      if (q0 + 1 < nreal) dc_tau[q0 + 1] = b.x;
+    }
+  }
+  __syncthreads();
+  // Sum of sigma over the task's rows, per load and component, from the kx = 0 bins:
+  //   sum_x sigma = sum_x tau + c0 : sum_x eps, with sum_x tau the (tree-summed) DFT bin of tau and
+  //   sum_x eps = n times the stored row mean.  Rows are combined in FP64.
+  if (threadIdx.x < nal * NC) {
+    const int la = threadIdx.x / NC, k = threadIdx.x - la * NC;
+    double acc = 0.0;
+    for (int rl = 0; rl < t.nrows; ++rl) {
+      const int q0 = (rl * nal + la) * NC;
+      double tr = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) tr += (double)dc_eps[q0 + j];
+      const double se = (double)n * (2.0 * c.mu0 * (double)dc_eps[q0 + k] + (k < DIM ? c.lam0 * tr : 0.0));
+      acc += (double)dc_tau[q0 + k] + se;
+    }
+    A.partR[((size_t)blockIdx.x * A.L + s_al[la]) * NC + k] = acc;
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_ROW,
@@ -738,8 +771,10 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     const size_t line_bytes = (size_t)k.n * vsize;  // one line; the twiddle table is one more
     auto row_lines = [&](int rows) { return (size_t)((rows * L * nc + 1) / 2) + 1; };
     int r = 1;
-    while (r < c.nrows && row_lines(r + 1) * line_bytes + (size_t)(r + 1) * L * nc * sizeof(long long) <= budget) ++r;
-    const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * sizeof(long long);
+    while (r < c.nrows &&
+           row_lines(r + 1) * line_bytes + (size_t)(r + 1) * L * nc * (sizeof(long long) + vsize) <= budget)
+      ++r;
+    const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * (sizeof(long long) + 2 * vsize / 2);
     if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
     lay.smem_row = std::max(lay.smem_row, need_r);
     c.rtask0 = (int)lay.tR.size();
@@ -1107,14 +1142,17 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   if (mat->dim != dim) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material built for another dimension");
   cudaGetLastError();  // do not report an error left behind by an unrelated earlier call
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Largest register radix of the FFT stages: FP32 kernels are compiled for 27 and 45, FP64 ones
-  // for 15 (HOM_MAX_RADIX32 selects the FP32 variant).
+  // Largest register radix of the FFT stages: FP32 kernels are compiled for 15, 27 and 45, FP64
+  // ones for 15 (HOM_MAX_RADIX32 selects the FP32 variant).
   const char* env = std::getenv("HOM_MAX_RADIX32");
   const int r32 = env ? std::atoi(env) : 27;
   if (opts->precision == HOM_FP32) {
     if (r32 >= 45)
       return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
                       : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
+    if (r32 <= 15)
+      return dim == 2 ? run_solve<float, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
+                      : run_solve<float, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
     return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
                     : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
   }
