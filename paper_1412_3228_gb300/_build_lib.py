@@ -48,6 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH
     if os.environ.get("HOM_PTXAS_VERBOSE"):
         common += ["-Xptxas", "-v"]
+    if os.environ.get("HOM_THREADS"):  # threads per CTA of the solver passes (tuning)
+        common += ["-DHOM_THREADS=%d" % int(os.environ["HOM_THREADS"])]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -62,17 +62,8 @@ int get_plan(int n, int max_radix, Plan* out) {
   HostPlan hp;
   if (!build_host_plan(n, hp, max_radix) || (int)hp.radix.size() > kMaxStages)
     return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7", n);
-  const size_t perm_bytes = ((size_t)n * sizeof(uint16_t) + 255) / 256 * 256;
-  const size_t tw32_bytes = ((size_t)n * sizeof(float2) + 255) / 256 * 256;
-  const size_t tw64_bytes = (size_t)n * sizeof(double2);
-  std::vector<unsigned char> host(perm_bytes + tw32_bytes + tw64_bytes, 0);
-  std::memcpy(host.data(), hp.perm.data(), (size_t)n * sizeof(uint16_t));
-  float2* t32 = reinterpret_cast<float2*>(host.data() + perm_bytes);
-  double2* t64 = reinterpret_cast<double2*>(host.data() + perm_bytes + tw32_bytes);
-  for (int t = 0; t < n; ++t) {
-    t32[t] = make_float2((float)hp.tw[2 * t], (float)hp.tw[2 * t + 1]);
-    t64[t] = make_double2(hp.tw[2 * t], hp.tw[2 * t + 1]);
-  }
+  std::vector<unsigned char> host(plan_table_bytes(n), 0);
+  fill_plan_tables(hp, host.data());
   DevicePlan dp;
   cudaError_t e = cudaMalloc(&dp.mem, host.size());
   if (e != cudaSuccess) return set_error(HOM_ERR_OOM, "plan allocation failed: %s", cudaGetErrorString(e));
@@ -88,10 +79,8 @@ int get_plan(int n, int max_radix, Plan* out) {
     p.radix[s] = hp.radix[s];
     p.span[s] = hp.span[s];
   }
-  unsigned char* base = static_cast<unsigned char*>(dp.mem);
-  p.perm = reinterpret_cast<const uint16_t*>(base);
-  p.tw32 = reinterpret_cast<const float2*>(base + perm_bytes);
-  p.tw64 = reinterpret_cast<const double2*>(base + perm_bytes + tw32_bytes);
+  plan_dividers(p);
+  set_plan_pointers(p, static_cast<unsigned char*>(dp.mem));
   dc.plans[std::make_pair(n, max_radix)] = dp;
   *out = p;
   return HOM_OK;

@@ -168,14 +168,36 @@ HOM_HD void dft_small(V* v) {
   else dft_composite<split_a<R>(), R / split_a<R>(), FWD, V, T>(v);
 }
 
+// Exact division by a divisor fixed on the host: q = umulhi(a, m) with m = ceil(2^32 / d) is exact
+// whenever a * d < 2^32 (all index ranges here are far below).  Integer division compiled for the
+// device goes through int <-> float conversions, which share the slow FP64 pipe on this GPU.
+struct FastDiv {
+  unsigned m;
+  int d;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.d = d;
+  f.m = d <= 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + (unsigned)d - 1) / (unsigned)d);
+  return f;
+}
+HOM_HD int fdiv(int a, const FastDiv& f) {
+  if (f.d <= 1) return a;
+#if defined(__CUDA_ARCH__)
+  return (int)__umulhi((unsigned)a, f.m);
+#else
+  return (int)(((unsigned long long)(unsigned)a * f.m) >> 32);
+#endif
+}
+
 // Enumerates the flat indices f = tid, tid + step, ... < total as pairs (a, b) with f = a * nb + b,
 // updating the pair with carries instead of dividing.
 struct Iter2 {
   int a, b, da, db, nb;
-  HOM_HD Iter2(int f0, int step, int nb_) : nb(nb_) {
-    a = f0 / nb;
+  HOM_HD Iter2(int f0, int step, const FastDiv& div) : nb(div.d) {
+    a = fdiv(f0, div);
     b = f0 - a * nb;
-    da = step / nb;
+    da = fdiv(step, div);
     db = step - da * nb;
   }
   HOM_HD void next() {
@@ -192,10 +214,25 @@ struct Plan {
   int nstage;
   int radix[kMaxStages];  // DIT order
   int span[kMaxStages];   // L_s = radix[0] * ... * radix[s-1]
+  FastDiv div_nb[kMaxStages];  // n / radix[s] (butterflies per line)
+  FastDiv div_L[kMaxStages];   // span[s]
+  FastDiv div_n, div_h;        // n and (n + 1) / 2
   const uint16_t* perm;   // perm[k] = position of index k in the digit-reversed layout
   const float2* tw32;     // exp(-2 pi i t / n), t < n
   const double2* tw64;
+  const float* xi32;      // 2 pi a(k): signed DFT frequency of bin k times 2 pi
+  const double* xi64;
 };
+
+// Fills the dividers of a plan whose n, nstage, radix and span are set.
+inline void plan_dividers(Plan& p) {
+  for (int s = 0; s < p.nstage; ++s) {
+    p.div_nb[s] = make_fastdiv(p.n / p.radix[s]);
+    p.div_L[s] = make_fastdiv(p.span[s]);
+  }
+  p.div_n = make_fastdiv(p.n);
+  p.div_h = make_fastdiv((p.n + 1) / 2);
+}
 
 template <typename V> HOM_HD const V* twiddles(const Plan& p);
 template <> HOM_HD const float2* twiddles<float2>(const Plan& p) { return p.tw32; }
@@ -205,13 +242,14 @@ template <> HOM_HD const double2* twiddles<double2>(const Plan& p) { return p.tw
 // `ls` elements).  Thread `tid` of `nthr` handles butterflies tid, tid + nthr, ... (a butterfly is
 // (line, block, j) with j < L), enumerated with carries.  `tw` is the length-n twiddle table.
 template <int R, bool FWD, typename V, typename T>
-HOM_HD void dit_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, int nthr) {
+HOM_HD void dit_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, int nthr, const FastDiv& dnb,
+                      const FastDiv& dL) {
   const int B = L * R;
   const int nb = n / R;           // butterflies per line
-  const int twstep = n / B;
-  Iter2 lw(tid, nthr, nb);        // (line, w)
-  Iter2 bj(lw.b, lw.db, L);       // (block, j) of w; advanced by the same step
-  const int nblk = n / B;
+  const int nblk = fdiv(nb, dL);  // n / B blocks per line, also the twiddle stride
+  const int twstep = nblk;
+  Iter2 lw(tid, nthr, dnb);       // (line, w)
+  Iter2 bj(lw.b, lw.db, dL);      // (block, j) of w; advanced by the same step
   for (; lw.a < nl; ) {
     V* base = s + lw.a * ls + bj.a * B + bj.b;
     const int j = bj.b;
@@ -243,13 +281,14 @@ HOM_HD void dit_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
 
 // One DIF stage (radix R, span L): DFT_r of the inputs, then the twiddles, written in place.
 template <int R, bool FWD, typename V, typename T>
-HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, int nthr) {
+HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, int nthr, const FastDiv& dnb,
+                      const FastDiv& dL) {
   const int B = L * R;
   const int nb = n / R;
-  const int twstep = n / B;
-  Iter2 lw(tid, nthr, nb);
-  Iter2 bj(lw.b, lw.db, L);
-  const int nblk = n / B;
+  const int nblk = fdiv(nb, dL);
+  const int twstep = nblk;
+  Iter2 lw(tid, nthr, dnb);
+  Iter2 bj(lw.b, lw.db, dL);
   for (; lw.a < nl; ) {
     V* base = s + lw.a * ls + bj.a * B + bj.b;
     const int j = bj.b;
@@ -309,7 +348,7 @@ template <bool FWD, int MAXR, typename V, typename T>
 HOM_HD void fft_dit(V* s, int nl, int ls, const Plan& p, const V* tw, int tid, int nthr) {
   for (int st = 0; st < p.nstage; ++st) {
     const int r = p.radix[st], L = p.span[st];
-#define HOM_DIT(R) dit_stage<R, FWD, V, T>(s, nl, ls, p.n, L, tw, tid, nthr)
+#define HOM_DIT(R) dit_stage<R, FWD, V, T>(s, nl, ls, p.n, L, tw, tid, nthr, p.div_nb[st], p.div_L[st])
     HOM_RADIX_CASES(HOM_DIT)
 #undef HOM_DIT
     HOM_SYNC();
@@ -320,7 +359,7 @@ template <bool FWD, int MAXR, typename V, typename T>
 HOM_HD void fft_dif(V* s, int nl, int ls, const Plan& p, const V* tw, int tid, int nthr) {
   for (int st = p.nstage - 1; st >= 0; --st) {
     const int r = p.radix[st], L = p.span[st];
-#define HOM_DIF(R) dif_stage<R, FWD, V, T>(s, nl, ls, p.n, L, tw, tid, nthr)
+#define HOM_DIF(R) dif_stage<R, FWD, V, T>(s, nl, ls, p.n, L, tw, tid, nthr, p.div_nb[st], p.div_L[st])
     HOM_RADIX_CASES(HOM_DIF)
 #undef HOM_DIF
     HOM_SYNC();

@@ -29,6 +29,21 @@ int set_error(int code, const char* fmt, ...);
 // and uploaded on first use), or an error.
 int get_plan(int n, int max_radix, Plan* out);
 
+// Points a plan's table pointers into device memory laid out by fill_plan_tables.
+inline void set_plan_pointers(Plan& p, unsigned char* base) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t n = (size_t)p.n;
+  p.perm = reinterpret_cast<const uint16_t*>(base);
+  base += up(n * 2);
+  p.tw32 = reinterpret_cast<const float2*>(base);
+  base += up(n * 8);
+  p.tw64 = reinterpret_cast<const double2*>(base);
+  base += up(n * 16);
+  p.xi32 = reinterpret_cast<const float*>(base);
+  base += up(n * 4);
+  p.xi64 = reinterpret_cast<const double*>(base);
+}
+
 // Device scratch owned by the library (grown on demand, freed by hom_release).
 int get_workspace(size_t bytes, void** ptr);
 void release_backward_buffers();
@@ -81,10 +96,16 @@ struct CellDev {         // one cell of the solver
   long long g_off;       // complex-element offset of the cell in the displacement-like array
   double lam0, mu0;
   int rtask0, rtask1;    // row-pass task range
+  // per-cell constants, computed on the host (FP64 arithmetic is slow on the device)
+  float f_lam0, f_mu2, f_lpm, f_ratio, f_inv_mu0, f_inv_nv;
+  double d_lam0, d_mu2, d_lpm, d_ratio, d_inv_mu0, d_inv_nv;
 };
 
 struct TaskR { int cell, row0, nrows, pad; };              // rows [row0, row0+nrows) x all loads
-struct TaskL { int cell, load, kx0, ntk, fixed, pad; };    // lines along one axis, kx tile
+struct TaskL {  // lines along one axis for a tile of kx: ntk columns x nc components
+  int cell, load, kx0, ntk, fixed, pad;
+  FastDiv d_ntk, d_nl, d_ng;  // dividers by ntk, ntk * nc and ntk * dim
+};
 
 // Per (cell, load) pair
 struct PairDev { int cell, load, ctask0, ctask1; };

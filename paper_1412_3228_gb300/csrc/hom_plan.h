@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <functional>
 #include <utility>
 #include <vector>
@@ -17,6 +18,7 @@ struct HostPlan {
   std::vector<int> span;        // product of the radices before each stage
   std::vector<uint16_t> perm;   // position of index k in the digit-reversed layout
   std::vector<double> tw;       // interleaved (re, im) of exp(-2 pi i t / n)
+  std::vector<double> xi;       // 2 pi a(k), a(k) the signed frequency of DFT bin k
 };
 
 // Factor n into the register radices {3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49} (each at most
@@ -73,6 +75,8 @@ inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
     }
     p.perm[k] = (uint16_t)pos;
   }
+  p.xi.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) p.xi[k] = 6.28318530717958647692528676656 * (double)(k <= (n - 1) / 2 ? k : k - n);
   p.tw.assign(2 * (size_t)n, 0.0);
   const double two_pi = 6.28318530717958647692528676656;
   for (int t = 0; t < n; ++t) {
@@ -82,6 +86,30 @@ inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
     p.tw[2 * t + 1] = -std::sin(a);
   }
   return true;
+}
+
+// Device layout of a plan's tables (each block 256-byte aligned): permutation (uint16),
+// FP32 twiddles, FP64 twiddles, FP32 wave numbers, FP64 wave numbers.
+inline size_t plan_table_bytes(int n) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up((size_t)n * 2) + up((size_t)n * 8) + up((size_t)n * 16) + up((size_t)n * 4) + up((size_t)n * 8);
+}
+
+inline void fill_plan_tables(const HostPlan& hp, unsigned char* dst) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t n = (size_t)hp.n;
+  unsigned char* q = dst;
+  std::memcpy(q, hp.perm.data(), n * sizeof(uint16_t));
+  q += up(n * 2);
+  float* t32 = reinterpret_cast<float*>(q);
+  for (size_t t = 0; t < n; ++t) { t32[2 * t] = (float)hp.tw[2 * t]; t32[2 * t + 1] = (float)hp.tw[2 * t + 1]; }
+  q += up(n * 8);
+  std::memcpy(q, hp.tw.data(), n * 16);
+  q += up(n * 16);
+  float* x32 = reinterpret_cast<float*>(q);
+  for (size_t k = 0; k < n; ++k) x32[k] = (float)hp.xi[k];
+  q += up(n * 4);
+  std::memcpy(q, hp.xi.data(), n * 8);
 }
 
 }  // namespace hom

@@ -29,7 +29,10 @@
 namespace hom {
 namespace {
 
-constexpr int kThreads = 256;
+#ifndef HOM_THREADS
+#define HOM_THREADS 256
+#endif
+constexpr int kThreads = HOM_THREADS;  // threads per CTA of the pass kernels (a build-time tunable)
 constexpr int kMaxLoads = 8;
 
 struct SolveArgs {
@@ -138,7 +141,25 @@ __device__ __forceinline__ V* stage_twiddles(unsigned char* smem, const Plan& sp
   return tw;
 }
 
-__device__ __forceinline__ int signed_freq(int k, int n) { return k <= (n - 1) / 2 ? k : k - n; }
+// 1/x for |x| >= 4 pi^2 (no special values): the fast FP32 reciprocal (a few ulp) avoids the
+// IEEE division sequence; FP64 keeps the correctly rounded division.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <typename T> __device__ __forceinline__ const T* xi_table(const Plan& p);
+template <> __device__ __forceinline__ const float* xi_table<float>(const Plan& p) { return p.xi32; }
+template <> __device__ __forceinline__ const double* xi_table<double>(const Plan& p) { return p.xi64; }
+
+// Per-cell constants of the reference medium in the field precision (precomputed on the host).
+template <typename T> struct CellConst {
+  T lam0, mu2, lpm, ratio, inv_mu0, inv_nv;
+};
+__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<float>& k) {
+  k = {c.f_lam0, c.f_mu2, c.f_lpm, c.f_ratio, c.f_inv_mu0, c.f_inv_nv};
+}
+__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<double>& k) {
+  k = {c.d_lam0, c.d_mu2, c.d_lpm, c.d_ratio, c.d_inv_mu0, c.d_inv_nv};
+}
 
 // ------------------------------------------------------------------ row pass
 // OUT = false: one iteration's row pass (eps -> tau).  OUT = true: final fields of the returned
@@ -194,25 +215,44 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   __syncthreads();
   const long long kOffMask = (1LL << 62) - 1;
 
-  // 1. two real rows per complex line, Hermitian-extended half spectra
-  for (Iter2 it(threadIdx.x, kThreads, H); it.a < nlines; it.next()) {
-    const int line = it.a, kx = it.b;
-    const int q0 = 2 * line, q1 = q0 + 1;
-    const long long b0 = qbase[q0];
-    V a = static_cast<const V*>(A.eps[b0 >> 62])[(b0 & kOffMask) + (size_t)kx * NC];
-    V b = zero;
-    if (q1 < nreal) {
-      const long long b1 = qbase[q1];
-      b = static_cast<const V*>(A.eps[b1 >> 62])[(b1 & kOffMask) + (size_t)kx * NC];
-    }
-    V* z = s + (size_t)line * n;
-    if (kx == 0) {
-      z[0] = mk(a.x, b.x);
-      dc_eps[q0] = a.x;
-      if (q1 < nreal) dc_eps[q1] = b.x;
-    } else {
-      z[kx] = mk(a.x - b.y, a.y + b.x);      // A + iB
-      z[n - kx] = mk(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
+  // 1. two real rows per complex line, Hermitian-extended half spectra (four items per round so
+  // that eight global loads are in flight per thread)
+  {
+    constexpr int U = 4;
+    Iter2 it(threadIdx.x, kThreads, sp.div_h);
+    while (it.a < nlines) {
+      int line[U], kx[U];
+      V a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        line[u] = it.a;
+        kx[u] = it.b;
+        a[u] = b[u] = zero;
+        if (it.a < nlines) {
+          const int q0 = 2 * it.a, q1 = q0 + 1;
+          const long long b0 = qbase[q0];
+          a[u] = static_cast<const V*>(A.eps[b0 >> 62])[(b0 & kOffMask) + (size_t)it.b * NC];
+          if (q1 < nreal) {
+            const long long b1 = qbase[q1];
+            b[u] = static_cast<const V*>(A.eps[b1 >> 62])[(b1 & kOffMask) + (size_t)it.b * NC];
+          }
+        }
+        it.next();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (line[u] >= nlines) break;
+        const int q0 = 2 * line[u], q1 = q0 + 1;
+        V* z = s + (size_t)line[u] * n;
+        if (kx[u] == 0) {
+          z[0] = mk(a[u].x, b[u].x);
+          dc_eps[q0] = a[u].x;
+          if (q1 < nreal) dc_eps[q1] = b[u].x;
+        } else {
+          z[kx[u]] = mk(a[u].x - b[u].y, a[u].y + b[u].x);      // A + iB
+          z[n - kx[u]] = mk(a[u].x + b[u].y, b[u].x - a[u].y);  // conj(A) + i conj(B)
+        }
+      }
     }
   }
   __syncthreads();
@@ -221,8 +261,10 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
 
   // 3. constitutive update at every grid point of the task's rows: the material is read once per
   // voxel for all loads; pure voxels use sigma = lam tr(eps) I + 2 mu eps, mixed ones the packed c~.
-  const T lam0 = (T)c.lam0, mu2_0 = (T)(2.0 * c.mu0);
-  for (Iter2 it(threadIdx.x, kThreads, n); it.a < t.nrows; it.next()) {
+  CellConst<T> cc;
+  cell_const(c, cc);
+  const T lam0 = cc.lam0, mu2_0 = cc.mu2;
+  for (Iter2 it(threadIdx.x, kThreads, sp.div_n); it.a < t.nrows; it.next()) {
     const int rl = it.a, x = it.b;
     const int pos = HOM_LDG(sp.perm + x);
     const size_t vox = (size_t)(t.row0 + rl) * n + x;
@@ -310,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   fft_dit<true, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
   // 5. split the two real rows of each line and store the half spectra of tau
   V* tau = static_cast<V*>(A.tau);
-  for (Iter2 it(threadIdx.x, kThreads, H); it.a < nlines; it.next()) {
+  for (Iter2 it(threadIdx.x, kThreads, sp.div_h); it.a < nlines; it.next()) {
     const int line = it.a, kx = it.b;
     const V* z = s + (size_t)line * n;
     const V zk = z[kx];
@@ -371,24 +413,40 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const V* in = static_cast<const V*>(A.tau);
   V* out = DIM == 2 ? static_cast<V*>(A.eps[(it + 1) & 1]) : static_cast<V*>(A.tau);
 
-  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
-    const int j = it.a, w = it.b;
-    s[(size_t)w * n + j] = in[base + (size_t)j * rowstride + w];
+  {
+    constexpr int U = 4;
+    Iter2 it(threadIdx.x, kThreads, t.d_nl);
+    while (it.a < n) {
+      int jj[U], ww[U];
+      V v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        jj[u] = it.a;
+        ww[u] = it.b;
+        if (it.a < n) v[u] = in[base + (size_t)it.a * rowstride + it.b];
+        it.next();
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (jj[u] < n) s[(size_t)ww[u] * n + jj[u]] = v[u];
+    }
   }
   __syncthreads();
   fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
 
   // Green operator at every wave vector of the tile (spectrum at digit-reversed positions)
-  const T two_pi = T(6.28318530717958647692528676656);
-  const T mu0 = (T)c.mu0;
-  const T lpm = (T)(c.lam0 + c.mu0);
-  const T ratio = (T)((c.lam0 + c.mu0) / (c.lam0 + 2.0 * c.mu0));
-  const T inv_nv = (T)(1.0 / (double)c.nv);
-  const T inv_mu0 = (T)(1.0 / c.mu0);
+  CellConst<T> cc;
+  cell_const(c, cc);
+  const T mu0 = T(0.5) * cc.mu2;
+  const T lpm = cc.lpm;
+  const T ratio = cc.ratio;
+  const T inv_nv = cc.inv_nv;
+  const T inv_mu0 = cc.inv_mu0;
   // 2 pi a(k) of the transformed axis, one entry per bin (after the lines in shared memory)
   T* xi_tab = reinterpret_cast<T*>(s + (size_t)nl * n);
-  for (int k = threadIdx.x; k < n; k += kThreads) xi_tab[k] = two_pi * (T)signed_freq(k, n);
-  const T xi_fixed = DIM == 3 ? two_pi * (T)signed_freq(t.fixed, n) : T(0);
+  const T* xi_src = xi_table<T>(sp);
+  for (int k = threadIdx.x; k < n; k += kThreads) xi_tab[k] = xi_src[k];
+  const T xi_fixed = DIM == 3 ? xi_src[t.fixed] : T(0);
   __syncthreads();
   const T rs2 = T(0.707106781186547524400844362105);
   const double* Eld = A.E + ((size_t)t.cell * A.L + t.load) * NC;
@@ -397,8 +455,25 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const size_t grow_stride = DIM == 2 ? (size_t)Hp * DIM : (size_t)n * Hp * DIM;
   const size_t gfix = DIM == 3 ? (size_t)t.fixed * Hp * DIM : 0;
   Acc<T> r2acc, rnacc;
-  for (Iter2 it(threadIdx.x, kThreads, ntk); it.a < n; it.next()) {
-    const int kk = it.a, kxl = it.b;
+  // g of the next point is loaded while the current one is processed
+  Iter2 gi(threadIdx.x, kThreads, t.d_ntk);
+  V gnext[DIM];
+  if (gi.a < n) {
+    const V* gp0 = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * DIM;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) gnext[d] = gp0[d];
+  }
+  for (; gi.a < n;) {
+    const int kk = gi.a, kxl = gi.b;
+    V gv[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) gv[d] = gnext[d];
+    gi.next();
+    if (gi.a < n) {
+      const V* gpn = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * DIM;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) gnext[d] = gpn[d];
+    }
     const int kx = t.kx0 + kxl;
     const int pos = HOM_LDG(sp.perm + kk);
     V* tv[NC];
@@ -435,7 +510,7 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       tt[0][DIM - 1] = tt[DIM - 1][0] = rs2 * *tv[4];
       tt[0][1] = tt[1][0] = rs2 * *tv[5];
     }
-    V v[DIM], gv[DIM];
+    V v[DIM];
     T q2 = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -444,7 +519,6 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
 #pragma unroll
       for (int b = 0; b < DIM; ++b) acc = acc + xi[b] * tt[a][b];
       v[a] = acc;
-      gv[a] = gp[a];
     }
     V xg = mk(T(0), T(0)), xv = mk(T(0), T(0));
 #pragma unroll
@@ -460,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       r2 += r.x * r.x + r.y * r.y;
     }
     const T wgt = kx == 0 ? T(1) : T(2);
-    const T inv_q2 = T(1) / q2;
+    const T inv_q2 = recip(q2);
     r2acc.add(wgt * r2);
     rnacc.add(wgt * r2 * inv_q2);
     // g' = K0^-1 (tau_hat xi);  eps_hat' = -sym(xi (x) g') / N_v
@@ -495,7 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     }
   }
   fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
-  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+  for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + j];
   }
@@ -525,7 +599,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
                       (size_t)t.kx0 * NC;
   const V* in = static_cast<const V*>(A.tau);
   V* out = FWD ? static_cast<V*>(A.tau) : static_cast<V*>(A.eps[(it + 1) & 1]);
-  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+  for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     const int pos = FWD ? j : HOM_LDG(sp.perm + j);
     s[(size_t)w * n + pos] = in[base + (size_t)j * rowstride + w];
@@ -533,7 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
   __syncthreads();
   if (FWD) fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
   else fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
-  for (Iter2 it(threadIdx.x, kThreads, nl); it.a < n; it.next()) {
+  for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     const int pos = FWD ? HOM_LDG(sp.perm + j) : j;
     out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + pos];
@@ -710,9 +784,31 @@ struct Layout {
   size_t smem_row = 0, smem_green = 0, smem_y = 0;
 };
 
+
+TaskL make_task(int cell, int load, int kx0, int ntk, int fixed, int nc, int dim) {
+  TaskL t{};
+  t.cell = cell;
+  t.load = load;
+  t.kx0 = kx0;
+  t.ntk = ntk;
+  t.fixed = fixed;
+  t.d_ntk = make_fastdiv(ntk);
+  t.d_nl = make_fastdiv(ntk * nc);
+  t.d_ng = make_fastdiv(ntk * dim);
+  return t;
+}
+
+// Per-CTA shared-memory budget of the Green and y passes: three kx columns of a 1215 line in FP32
+// (nine lines, two CTAs per SM); HOM_GREEN_BUDGET overrides it.
+size_t green_budget() {
+  const char* e = std::getenv("HOM_GREEN_BUDGET");
+  size_t b = e ? (size_t)std::atoll(e) : (size_t)110 * 1024;
+  return std::min<size_t>(std::max<size_t>(b, 8 * 1024), 227 * 1024);
+}
+
 size_t smem_budget() {
   const char* e = std::getenv("HOM_SMEM_BUDGET");
-  size_t b = e ? (size_t)std::atoll(e) : (size_t)64 * 1024;
+  size_t b = e ? (size_t)std::atoll(e) : (size_t)96 * 1024;  // two CTAs per SM (measured best)
   return std::min<size_t>(std::max<size_t>(b, 8 * 1024), 227 * 1024);
 }
 
@@ -746,6 +842,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
           p.radix[s2] = hp.radix[s2];
           p.span[s2] = hp.span[s2];
         }
+        plan_dividers(p);
         lay.host_plans.push_back(hp);  // table pointers are set once the scratch is carved
       } else {
         int rc = get_plan(k.n, max_radix, &p);
@@ -763,6 +860,18 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     c.g_off = (long long)lay.g_elems;
     c.lam0 = c0[2 * ci];
     c.mu0 = c0[2 * ci + 1];
+    c.d_lam0 = c.lam0;
+    c.d_mu2 = 2.0 * c.mu0;
+    c.d_lpm = c.lam0 + c.mu0;
+    c.d_ratio = (c.lam0 + c.mu0) / (c.lam0 + 2.0 * c.mu0);
+    c.d_inv_mu0 = 1.0 / c.mu0;
+    c.d_inv_nv = 1.0 / (double)((long long)(dim == 2 ? k.n : k.n * k.n) * k.n);
+    c.f_lam0 = (float)c.d_lam0;
+    c.f_mu2 = (float)c.d_mu2;
+    c.f_lpm = (float)c.d_lpm;
+    c.f_ratio = (float)c.d_ratio;
+    c.f_inv_mu0 = (float)c.d_inv_mu0;
+    c.f_inv_nv = (float)c.d_inv_nv;
     vox += c.nv;
     lay.fld_elems += (size_t)L * nc * c.nv;
     lay.ws_elems += (size_t)L * c.nrows * c.Hp * nc;
@@ -782,56 +891,77 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     c.rtask1 = (int)lay.tR.size();
     // Green-pass and y-pass tiles of kx
     // Green/y tiles: ntk kx columns x nc lines, plus the twiddle table and the wave-number table
-    int ntk = (int)std::max<size_t>(1, (budget - std::min(budget, 2 * line_bytes)) / ((size_t)nc * line_bytes));
+    const size_t gbudget = green_budget();
+    int ntk = (int)std::max<size_t>(1, (gbudget - std::min(gbudget, 2 * line_bytes)) / ((size_t)nc * line_bytes));
     ntk = std::min(ntk, c.H);
     const size_t need_l = ((size_t)ntk * nc + 2) * line_bytes;
-    if (need_l > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "line of n = %d does not fit on chip", k.n);
     lay.smem_green = std::max(lay.smem_green, need_l);
     lay.smem_y = std::max(lay.smem_y, need_l);
     for (int l = 0; l < L; ++l) {
       PairDev pd{ci, l, (int)lay.tC.size(), 0};
       const int nfix = dim == 2 ? 1 : k.n;
       for (int f = 0; f < nfix; ++f)
-        for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tC.push_back(TaskL{ci, l, kx0, std::min(ntk, c.H - kx0), f, 0});
+        for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tC.push_back(make_task(ci, l, kx0, std::min(ntk, c.H - kx0), f, nc, dim));
       pd.ctask1 = (int)lay.tC.size();
       lay.pairs.push_back(pd);
       if (dim == 3)
         for (int z = 0; z < k.n; ++z)
-          for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tY.push_back(TaskL{ci, l, kx0, std::min(ntk, c.H - kx0), z, 0});
+          for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tY.push_back(make_task(ci, l, kx0, std::min(ntk, c.H - kx0), z, nc, dim));
     }
     lay.cells.push_back(c);
   }
   return HOM_OK;
 }
 
+// CUDA events around every launch when statistics are requested.  Events come from a pool kept
+// per device and reused across calls, so recording them costs no event creation on the timed path.
+struct EventPool {
+  std::vector<cudaEvent_t> ev;
+  size_t next = 0;
+};
+EventPool g_event_pool[64];
+
 struct Timer {
   hom_kernel_stats* stats;
   cudaStream_t st;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> marks;  // kernel kind, event indices
+  EventPool* pool = nullptr;
+  cudaEvent_t take() {
+    if (!pool) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      pool = &g_event_pool[dev & 63];
+      pool->next = 0;
+    }
+    if (pool->next == pool->ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool->ev.push_back(e);
+    }
+    return pool->ev[pool->next++];
+  }
   void begin(int kind) {
     if (!stats) return;
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, st);
-    ev.push_back({kind, {a, b}});
+    const size_t a = pool ? pool->next : 0;
+    cudaEventRecord(take(), st);
+    marks.push_back({kind, {a, 0}});
   }
   void end() {
     if (!stats) return;
-    cudaEventRecord(ev.back().second.second, st);
+    marks.back().second.second = pool->next;
+    cudaEventRecord(take(), st);
   }
   void collect() {
     if (!stats) return;
-    for (auto& e : ev) {
+    for (auto& m : marks) {
       float ms = 0.f;
-      cudaEventSynchronize(e.second.second);
-      cudaEventElapsedTime(&ms, e.second.first, e.second.second);
-      stats->ms[e.first] += ms;
-      stats->launches[e.first] += 1;
-      cudaEventDestroy(e.second.first);
-      cudaEventDestroy(e.second.second);
+      cudaEventSynchronize(pool->ev[m.second.second]);
+      cudaEventElapsedTime(&ms, pool->ev[m.second.first], pool->ev[m.second.second]);
+      stats->ms[m.first] += ms;
+      stats->launches[m.first] += 1;
     }
-    ev.clear();
+    marks.clear();
+    pool->next = 0;
   }
 };
 
@@ -882,14 +1012,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
-  // external workspace: the plan tables (permutation, FP32 and FP64 twiddles) follow the scratch
+  // external workspace: the plan tables follow the scratch
   std::vector<size_t> o_plan_tab(lay.host_plans.size());
-  for (size_t i = 0; i < lay.host_plans.size(); ++i) {
-    const size_t n = (size_t)lay.host_plans[i].n;
-    o_plan_tab[i] = take(n * sizeof(uint16_t));
-    take(n * sizeof(float2));
-    take(n * sizeof(double2));
-  }
+  for (size_t i = 0; i < lay.host_plans.size(); ++i) o_plan_tab[i] = take(plan_table_bytes(lay.host_plans[i].n));
   void* wsv = nullptr;
   if (ext) {
     if (off > ext->capacity)
@@ -902,25 +1027,14 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     if (rc != HOM_OK) return rc;
   }
   unsigned char* ws = static_cast<unsigned char*>(wsv);
+  std::vector<unsigned char> plan_host;
   for (size_t i = 0; i < lay.host_plans.size(); ++i) {
     const HostPlan& hp = lay.host_plans[i];
-    const size_t n = (size_t)hp.n;
-    const size_t o_perm = o_plan_tab[i];
-    const size_t o_t32 = o_perm + (n * sizeof(uint16_t) + 255) / 256 * 256;
-    const size_t o_t64 = o_t32 + (n * sizeof(float2) + 255) / 256 * 256;
-    std::vector<float2> t32(n);
-    std::vector<double2> t64(n);
-    for (size_t t2 = 0; t2 < n; ++t2) {
-      t32[t2] = make_float2((float)hp.tw[2 * t2], (float)hp.tw[2 * t2 + 1]);
-      t64[t2] = make_double2(hp.tw[2 * t2], hp.tw[2 * t2 + 1]);
-    }
-    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_perm, hp.perm.data(), n * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_t32, t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice, st));
-    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_t64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, st));
-    Plan& p = lay.plans[i];
-    p.perm = reinterpret_cast<const uint16_t*>(ws + o_perm);
-    p.tw32 = reinterpret_cast<const float2*>(ws + o_t32);
-    p.tw64 = reinterpret_cast<const double2*>(ws + o_t64);
+    plan_host.assign(plan_table_bytes(hp.n), 0);
+    fill_plan_tables(hp, plan_host.data());
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_plan_tab[i], plan_host.data(), plan_host.size(), cudaMemcpyHostToDevice, st));
+    if (ext) HOM_CUDA_TRY(cudaStreamSynchronize(st));  // plan_host is reused for the next table
+    set_plan_pointers(lay.plans[i], ws + o_plan_tab[i]);
   }
   if (ext) HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging vectors above go out of scope
   {

@@ -1,0 +1,142 @@
+"""Full-size GPU parity: the bench workloads in the launch configuration bench.py times, against
+values the FP64 oracle stored in tests/golden (written by tests/golden/make_golden.py, which calls
+only the oracle) and against per-voxel oracle computations on sampled voxels."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import hom_inputs as H
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+hom = pytest.importorskip("paper_1412_3228_gb300")
+from gpu_helpers import dense_ctilde, unpack  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    torch.cuda.set_device(0)
+
+
+def _sweep():
+    cells, phases = H.resolution_sweep_cells((45, 135, 405, 1215), (10.0, 0.1))
+    c0 = np.array([H.mean_lame(phases[c.matrix_phase:c.matrix_phase + 2]) for c in cells])
+    gold = {(e["n"], e["contrast"], e["rule"]): np.array(e["ceff"])
+            for e in json.load(open(os.path.join(GOLDEN, "sweep2d_ceff.json")))["cells"]}
+    keys = []
+    for c in cells:
+        contrast = round(phases[c.matrix_phase + 1][1] / phases[c.matrix_phase][1], 6)
+        keys.append((c.n, contrast, H.RULE_NAMES[c.rule]))
+    return cells, phases, c0, gold, keys
+
+
+@pytest.mark.parametrize("precision,crit,tol,bar", [(1, 0, 1e-10, 1e-9), (0, 1, 1e-6, 1e-5)], ids=["fp64", "fp32"])
+def test_resolution_sweep_ceff_matches_oracle(precision, crit, tol, bar):
+    """All 32 cells x 3 loads of the 2D sweep in one batched call (FP32) or one call (FP64)."""
+    cells, phases, c0, gold, keys = _sweep()
+    mat = hom.hom_filter_build(cells, phases)
+    r = hom.hom_solve(mat, np.eye(3), c0, precision=precision, criterion=crit, tol=tol, max_iter=3000, fields=False)
+    assert (r["status"] == 0).all()
+    C = hom.hom_effective_stiffness(np.eye(3), r["mean_sigma"], 2)
+    worst = 0.0
+    for i, k in enumerate(keys):
+        g = gold[k]
+        worst = max(worst, float(np.abs(C[i] - g).max() / np.abs(g).max()))
+    assert worst < bar, worst
+
+
+def _oracle_voxel_ctilde(cell, phases, a):
+    """c~ of one voxel (index a = (ax, ay[, az])) by the oracle's definitions, computed alone."""
+    dim, S = cell.dim, cell.subgrid
+    offs = O.sample_offsets(dim, cell.radius_px, S)
+    j = np.asarray(a)[None, :] * S + offs
+    ph = O.phase_at(cell, (2 * j + 1).astype(np.float64), S)
+    present, counts = np.unique(ph, return_counts=True)
+    Cs = [O.isotropic_mandel(*phases[p], dim) for p in present]
+    if present.size == 1:
+        return Cs[0], False
+    fs = counts / offs.shape[0]
+    if cell.rule == H.RULE_VOIGT:
+        return O.hr_voigt(Cs, fs), True
+    if cell.rule == H.RULE_REUSS:
+        return O.hr_reuss(Cs, fs), True
+    x = (np.asarray(a) + 0.5) / cell.n
+    best, nrm = np.inf, None
+    for prim in cell.prims:
+        d, v = O.surface_distance(prim, x[None, :], dim)
+        if d[0] < best:
+            best, nrm = d[0], v[0]
+    return O.hr_two_layer(Cs[0], Cs[1], fs[0], fs[1], nrm, dim), True
+
+
+@pytest.mark.parametrize("rule", [H.RULE_VOIGT, H.RULE_REUSS, H.RULE_TWO_LAYER])
+def test_filter_build_1215_sampled_voxels(rule):
+    cell = H.centred_disk_cell(1215, rule=rule)
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build([cell], phases)
+    got, mixed = dense_ctilde(mat, 0)
+    rng = np.random.default_rng(1215 + rule)
+    mixed_idx = np.nonzero(mixed)[0]
+    assert mixed_idx.size > 1000
+    pick = np.concatenate([rng.choice(mixed_idx, 40, replace=False), rng.integers(0, 1215 ** 2, 40)])
+    for v in pick:
+        a = (v % 1215, v // 1215)
+        C, is_mixed = _oracle_voxel_ctilde(cell, phases, a)
+        assert bool(mixed[v]) == is_mixed, v
+        np.testing.assert_allclose(unpack(got[v], 3), C, rtol=0, atol=1e-12 * np.abs(C).max())
+
+
+def _spheres81():
+    p = os.path.join(GOLDEN, "spheres3d_ceff.json")
+    if not os.path.exists(p):
+        pytest.skip("3D golden values not generated")
+    gold = {e["contrast"]: np.array(e["ceff"]) for e in json.load(open(p))["cells"]}
+    cell = H.rsa_spheres_cell(81, seed=1081, vf=0.3, rmin=0.05, rmax=0.1, rule=H.RULE_TWO_LAYER, radius_px=1.0,
+                              subgrid=8, gap_voxels=81 / 243.0)
+    return cell, gold
+
+
+@pytest.mark.parametrize("precision,crit,tol,bar", [(1, 0, 1e-9, 1e-8), (0, 1, 1e-6, 1e-5)], ids=["fp64", "fp32"])
+def test_spheres_81_ceff_matches_oracle(precision, crit, tol, bar):
+    """81^3 random-sphere cells, 2-layer filter, all 6 loads in one launch, both contrasts."""
+    base, gold = _spheres81()
+    phases, cells = [], []
+    for contrast in (10.0, 0.1):
+        cells.append(H.remap_phases(base, len(phases)))
+        phases.extend(H.two_phases(contrast))
+    c0 = [H.mean_lame(phases[0:2]), H.mean_lame(phases[2:4])]
+    mat = hom.hom_filter_build(cells, phases)
+    r = hom.hom_solve(mat, np.eye(6), c0, precision=precision, criterion=crit, tol=tol, max_iter=3000, fields=False)
+    assert (r["status"] == 0).all()
+    C = hom.hom_effective_stiffness(np.eye(6), r["mean_sigma"], 3)
+    for i, contrast in enumerate((10.0, 0.1)):
+        g = gold[contrast]
+        assert float(np.abs(C[i] - g).max() / np.abs(g).max()) < bar
+        # major symmetry of the computed tensor (to the solver tolerance)
+        assert float(np.abs(C[i] - C[i].T).max() / np.abs(C[i]).max()) < 10 * bar
+
+
+def test_spheres_81_filter_sampled_voxels():
+    base, _ = _spheres81()
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build([base], phases)
+    got, mixed = dense_ctilde(mat, 0)
+    rng = np.random.default_rng(81)
+    n = 81
+    pick = np.concatenate([rng.choice(np.nonzero(mixed)[0], 25, replace=False), rng.integers(0, n ** 3, 25)])
+    for v in pick:
+        a = (v % n, (v // n) % n, v // (n * n))
+        C, is_mixed = _oracle_voxel_ctilde(base, phases, a)
+        assert bool(mixed[v]) == is_mixed, v
+        np.testing.assert_allclose(unpack(got[v], 6), C, rtol=0, atol=1e-12 * np.abs(C).max())
