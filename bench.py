@@ -207,6 +207,16 @@ def run_ours(args, rank, world):
     fp32_err, ncmp = ceff_errors(cells, phases, r["mean_sigma"], golden_ceff())
     iters = r["iterations"]
 
+    # ---- the filter build alone (part of every step above)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(3):
+        hom.hom_filter_build(cells, phases)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    filter_ms = f0.elapsed_time(f1) / 3
+
     # ---- end to end: the public API with host outputs (fields and C_eff back on the host)
     e2e_ms, e2e_vi, d2h = 0.0, 0.0, 0
     torch.cuda.synchronize()
@@ -261,6 +271,7 @@ def run_ours(args, rank, world):
             "iterations": {"max": int(iters.max()), "min": int(iters.min()),
                            "per_rule": {H.RULE_NAMES[rr]: int(np.mean([iters[i].mean() for i, c in enumerate(cells)
                                                                         if c.rule == rr])) for rr in RULES}},
+            "filter_build_ms": round(filter_ms, 3),
             "ceff_max_rel_err_vs_oracle": fp32_err, "ceff_cells_compared": ncmp,
             "fp64_plain": fp64}
     if rank == 0 and not args.skip_cpu:

@@ -80,11 +80,18 @@ struct FCell {           // one cell of the filter build
   double radius_px;
   long long vox_off;
   long long block0;      // first thread block of this cell
+  float inv_n;           // 1 / n rounded to FP32
+  float reach32;         // filter radius in cell units (r / n) rounded to FP32
+  int R2i;               // (2 S r)^2 rounded down: a fine point is in the ball iff sum D^2 <= R2i
+  int tlo, thi;          // range of the fine-point offsets t that can fall in a ball
+  int M;                 // fine points per ball
+  FastDiv dn, dnt;       // dividers by n and by thi - tlo + 1
 };
 struct FPrim {
   int kind, phase, axis, pad;
   double c[3];
   double radius;
+  float c32[3], r32;     // centre and radius (slab: thickness) rounded to FP32
 };
 
 struct CellDev {         // one cell of the solver

@@ -42,6 +42,18 @@ FILTER_CASES = [
     ("sph15-2layer", lambda: H.rsa_spheres_cell(15, seed=1015, vf=0.15, rmin=0.1, rmax=0.15, subgrid=6, gap_voxels=1.0), 10.0),
     ("sph9-reuss", lambda: H.rsa_spheres_cell(9, seed=9, vf=0.15, rmin=0.12, rmax=0.18, rule=H.RULE_REUSS,
                                               subgrid=4, gap_voxels=1.0), 0.1),
+    # disk across the periodic boundary (wrapped offsets)
+    ("wrap-disk-2layer", lambda: H.Cell(2, 45, 0, [H.Primitive(H.PRIM_DISK, 1, (0.02, 0.97, 0.0), 0.3)],
+                                        H.RULE_TWO_LAYER, 1.0, 16), 10.0),
+    # overlapping disks of one phase: the owner of a sample is the first primitive containing it,
+    # the 2-layer normal comes from the nearest surface, whichever primitive holds it
+    ("overlap-2layer", lambda: H.Cell(2, 45, 0, [H.Primitive(H.PRIM_DISK, 1, (0.45, 0.5, 0.0), 0.2),
+                                                 H.Primitive(H.PRIM_DISK, 1, (0.62, 0.52, 0.0), 0.15)],
+                                      H.RULE_TWO_LAYER, 1.5, 8), 10.0),
+    # many disks, larger filter radius and a coarse subgrid
+    ("rdisks-voigt", lambda: H.random_disk_cell(7, sizes=(75,), kmin=30, kmax=30, radius_px=1.3, subgrid=7)[0], 0.1),
+    ("sph21-voigt", lambda: H.rsa_spheres_cell(21, seed=21, vf=0.3, rmin=0.12, rmax=0.16, rule=H.RULE_VOIGT,
+                                               subgrid=6, gap_voxels=0.1), 10.0),
 ]
 
 
@@ -71,6 +83,21 @@ def test_filter_build_parity(name, make, contrast):
     # FP32 copy is the rounded FP64 value
     got32, _ = dense_ctilde(mat, 0, fp64=False)
     np.testing.assert_array_equal(got32, got.astype(np.float32))
+
+
+def test_filter_build_three_phases():
+    """Overlapping disks of two inclusion phases: counts per phase and the Voigt/Reuss averages of
+    three phases match the oracle."""
+    cell = H.Cell(2, 35, 0, [H.Primitive(H.PRIM_DISK, 1, (0.45, 0.5, 0.0), 0.2),
+                             H.Primitive(H.PRIM_DISK, 2, (0.6, 0.55, 0.0), 0.15)], H.RULE_REUSS, 1.2, 12)
+    phases = H.two_phases(10.0) + [H.lame_from_young(0.3, 0.3)]
+    for rule in (H.RULE_VOIGT, H.RULE_REUSS):
+        cell.rule = rule
+        mat = hom.hom_filter_build([cell], phases)
+        fb = O.filter_build(cell, phases)
+        got, mixed = dense_ctilde(mat, 0)
+        np.testing.assert_array_equal(mixed, fb["mixed"].ravel())
+        assert _rel(unpack(got, 3), fb["ctilde"].reshape(-1, 3, 3)) < 1e-12
 
 
 def _solve_both(cells, phases, E, precision, criterion, tol, max_iter=2000, c0=None):
