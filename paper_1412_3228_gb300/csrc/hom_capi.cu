@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "hom_internal.h"
+#include "hom_fast2d.h"
 #include "hom_plan.h"
 
 namespace hom {
@@ -128,6 +129,7 @@ extern "C" void hom_release(void) {
   }
   g_cache.clear();
   release_backward_buffers();
+  fast2d_release();
   cudaSetDevice(cur);
 }
 

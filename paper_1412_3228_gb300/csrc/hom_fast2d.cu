@@ -1,0 +1,676 @@
+// Specialised FP32 row and Green passes of the 2D fixed-point scheme (section 2, eqs. 1-a, 1-b,
+// 2) for grid sizes n with a radix plan fixed at compile time.
+//
+// Lane pairs.  Shared memory holds one float4 per (position, pair): (re_A, re_B, im_A, im_B), the
+// same position of two complex lines A and B.  Every butterfly, the Green operator and the
+// constitutive update then act on both lines with packed FP32x2 instructions (add/sub/mul/fma
+// .f32x2), one instruction per pair of values.
+//   row pass  : pair c = Mandel component c; line A = real rows y0 + i*(y0+1), line B = rows
+//               y0+2 + i*(y0+3).  One CTA handles 4 rows and loops over the active loads.
+//   Green pass: pair c = component c; line A = column kx0, line B = column kx0 + 1.
+// With the three components side by side, the element stride is 48 bytes, so consecutive
+// positions fall on distinct bank quads: the stage accesses are free of bank conflicts.
+//
+// Transforms are the in-place mixed-radix DIF (natural -> digit-reversed) and DIT (digit-reversed
+// -> natural) of hom_common.cuh with the radices as template parameters: every index division is
+// by a compile-time constant.  The row pass works on x samples at digit-reversed positions and
+// reads labels permuted the same way (label_perm); the Green pass reads the wave number of each
+// position from a table, and keeps its displacement-like state g in its own layout
+// [load][column pair][position][4 complex], private to this pass.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hom_fast2d.h"
+#include "hom_plan.h"
+#include "hom_solve_args.cuh"
+
+namespace hom {
+namespace {
+
+constexpr int kT = 256;  // threads per CTA
+constexpr int NP = 3;    // lane pairs per position (2D Mandel components)
+
+// ------------------------------------------------------------------ packed FP32x2 arithmetic
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  memcpy(&ra, &a, 8);
+  memcpy(&rb, &b, 8);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  memcpy(&d, &rd, 8);
+  return d;
+}
+
+// Two complex numbers, one per line: re = (re_A, re_B), im = (im_A, im_B).
+struct P2 {
+  float2 re, im;
+};
+__device__ __forceinline__ P2 ldp(const float4& v) { return P2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 stp(const P2& p) { return make_float4(p.re.x, p.re.y, p.im.x, p.im.y); }
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+__device__ __forceinline__ P2 scale(float s, P2 a) { return P2{mul2(f2(s), a.re), mul2(f2(s), a.im)}; }
+// a * (c + i s) with scalar c, s (the same for both lines)
+__device__ __forceinline__ P2 cmul_s(P2 a, float c, float s) {
+  return P2{fma2(a.im, f2(-s), mul2(a.re, f2(c))), fma2(a.im, f2(c), mul2(a.re, f2(s)))};
+}
+// a * w (FWD) or a * conj(w) with w4 = (wr, wr, wi, wi)
+template <bool FWD>
+__device__ __forceinline__ P2 twmul(P2 a, float4 w4) {
+  const float2 wr = make_float2(w4.x, w4.y), wi = make_float2(w4.z, w4.w);
+  if (FWD) return P2{sub2(mul2(a.re, wr), mul2(a.im, wi)), fma2(a.re, wi, mul2(a.im, wr))};
+  return P2{fma2(a.im, wi, mul2(a.re, wr)), sub2(mul2(a.im, wr), mul2(a.re, wi))};
+}
+
+// ------------------------------------------------------------------ register DFTs on lane pairs
+// Forward transforms use w = exp(-2 pi i / r), inverse ones conj(w); no scaling.  Composite sizes
+// leave X[k] in v[out_pos<R>(k)] (hom_common.cuh).
+template <bool FWD>
+__device__ __forceinline__ void dft3p(P2* v) {
+  const float h = 0.866025403784438646763723170753f;  // sin(2 pi / 3)
+  const P2 s = v[1] + v[2];
+  const P2 d = v[1] - v[2];
+  const P2 m{fma2(s.re, f2(-0.5f), v[0].re), fma2(s.im, f2(-0.5f), v[0].im)};
+  v[0] = v[0] + s;
+  const float hf = FWD ? h : -h;  // v1 = m - i hf d, v2 = m + i hf d
+  v[1] = P2{fma2(d.im, f2(hf), m.re), fma2(d.re, f2(-hf), m.im)};
+  v[2] = P2{fma2(d.im, f2(-hf), m.re), fma2(d.re, f2(hf), m.im)};
+}
+
+template <bool FWD>
+__device__ __forceinline__ void dft5p(P2* v) {
+  const float c1 = 0.309016994374947424102293417183f, c2 = -0.809016994374947424102293417183f;
+  const float s1 = 0.951056516295153572116439333379f, s2 = 0.587785252292473129168705954639f;
+  const P2 a1 = v[1] + v[4], b1 = v[1] - v[4];
+  const P2 a2 = v[2] + v[3], b2 = v[2] - v[3];
+  const P2 r1{fma2(a2.re, f2(c2), fma2(a1.re, f2(c1), v[0].re)), fma2(a2.im, f2(c2), fma2(a1.im, f2(c1), v[0].im))};
+  const P2 r2{fma2(a2.re, f2(c1), fma2(a1.re, f2(c2), v[0].re)), fma2(a2.im, f2(c1), fma2(a1.im, f2(c2), v[0].im))};
+  const float t1 = FWD ? s1 : -s1, t2 = FWD ? s2 : -s2;
+  // i1 = t1 b1 + t2 b2, i2 = t2 b1 - t1 b2; X1 = r1 - i i1, X4 = r1 + i i1, X2 = r2 - i i2, X3 = r2 + i i2
+  const P2 i1{fma2(b2.re, f2(t2), mul2(b1.re, f2(t1))), fma2(b2.im, f2(t2), mul2(b1.im, f2(t1)))};
+  const P2 i2{fma2(b2.re, f2(-t1), mul2(b1.re, f2(t2))), fma2(b2.im, f2(-t1), mul2(b1.im, f2(t2)))};
+  v[0] = v[0] + a1 + a2;
+  v[1] = P2{add2(r1.re, i1.im), sub2(r1.im, i1.re)};
+  v[4] = P2{sub2(r1.re, i1.im), add2(r1.im, i1.re)};
+  v[2] = P2{add2(r2.re, i2.im), sub2(r2.im, i2.re)};
+  v[3] = P2{sub2(r2.re, i2.im), add2(r2.im, i2.re)};
+}
+
+template <int R, bool FWD> __device__ __forceinline__ void dftp(P2* v);
+
+// R = A * B inside the registers: X[ka + A kb] = sum_nb w_B^(nb kb) [w_R^(nb ka) sum_na x[B na + nb] w_A^(na ka)]
+template <int A, int B, bool FWD>
+__device__ __forceinline__ void dft_compositep(P2* v) {
+  constexpr int R = A * B;
+#pragma unroll
+  for (int nb = 0; nb < B; ++nb) {
+    P2 t[A];
+#pragma unroll
+    for (int na = 0; na < A; ++na) t[na] = v[B * na + nb];
+    dftp<A, FWD>(t);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) {
+      const P2 x = t[out_pos<A>(ka)];
+      const int m = (nb * ka) % R;
+      if (m == 0) {
+        v[B * ka + nb] = x;
+      } else {
+        const float c = (float)tw_cos(R, m), sn = FWD ? (float)(-tw_sin(R, m)) : (float)tw_sin(R, m);
+        v[B * ka + nb] = cmul_s(x, c, sn);
+      }
+    }
+  }
+#pragma unroll
+  for (int ka = 0; ka < A; ++ka) dftp<B, FWD>(v + B * ka);
+}
+
+template <int R, bool FWD>
+__device__ __forceinline__ void dftp(P2* v) {
+  if constexpr (R == 3) dft3p<FWD>(v);
+  else if constexpr (R == 5) dft5p<FWD>(v);
+  else dft_compositep<split_a<R>(), R / split_a<R>(), FWD>(v);
+}
+
+// ------------------------------------------------------------------ compile-time plans
+// Radices in DIT order; registers bound the radix at 15 (15 lane pairs = 60 floats).
+template <int N> struct Radix;
+template <> struct Radix<45> { static constexpr int m = 2, r0 = 5, r1 = 9, r2 = 1; };
+template <> struct Radix<75> { static constexpr int m = 2, r0 = 5, r1 = 15, r2 = 1; };
+template <> struct Radix<135> { static constexpr int m = 2, r0 = 15, r1 = 9, r2 = 1; };
+template <> struct Radix<225> { static constexpr int m = 2, r0 = 15, r1 = 15, r2 = 1; };
+template <> struct Radix<405> { static constexpr int m = 3, r0 = 5, r1 = 9, r2 = 9; };
+template <> struct Radix<1215> { static constexpr int m = 3, r0 = 15, r1 = 9, r2 = 9; };
+constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};
+
+// One stage over the NP pairs of every position; thread t takes the butterflies t, t + kT, ...
+// (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
+template <int N, int R, int L, bool FWD, bool DIT>
+__device__ __forceinline__ void stage_p(float4* s, const float4* __restrict__ tw) {
+  constexpr int NB = N / R, B = L * R, TS = N / B;
+  for (int t = threadIdx.x; t < NB * NP; t += kT) {
+    const int cc = t / NB;
+    const int b = t - cc * NB;
+    const int blk = b / L;
+    const int j = b - blk * L;
+    float4* base = s + (blk * B + j) * NP + cc;
+    P2 v[R];
+    if (DIT) {
+      v[0] = ldp(base[0]);
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        P2 x = ldp(base[q * L * NP]);
+        if (L > 1) x = twmul<FWD>(x, __ldg(tw + j * q * TS));
+        v[q] = x;
+      }
+      dftp<R, FWD>(v);
+#pragma unroll
+      for (int p = 0; p < R; ++p) base[p * L * NP] = stp(v[out_pos<R>(p)]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) v[q] = ldp(base[q * L * NP]);
+      dftp<R, FWD>(v);
+      base[0] = stp(v[0]);
+#pragma unroll
+      for (int p = 1; p < R; ++p) {
+        P2 x = v[out_pos<R>(p)];
+        if (L > 1) x = twmul<FWD>(x, __ldg(tw + j * p * TS));
+        base[p * L * NP] = stp(x);
+      }
+    }
+  }
+}
+
+template <int N, bool FWD>
+__device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
+  using P = Radix<N>;
+  stage_p<N, P::r0, 1, FWD, true>(s, tw);
+  __syncthreads();
+  if constexpr (P::m > 1) {
+    stage_p<N, P::r1, P::r0, FWD, true>(s, tw);
+    __syncthreads();
+  }
+  if constexpr (P::m > 2) {
+    stage_p<N, P::r2, P::r0 * P::r1, FWD, true>(s, tw);
+    __syncthreads();
+  }
+}
+
+template <int N, bool FWD>
+__device__ __forceinline__ void fft_dif_p(float4* s, const float4* tw) {
+  using P = Radix<N>;
+  if constexpr (P::m > 2) {
+    stage_p<N, P::r2, P::r0 * P::r1, FWD, false>(s, tw);
+    __syncthreads();
+  }
+  if constexpr (P::m > 1) {
+    stage_p<N, P::r1, P::r0, FWD, false>(s, tw);
+    __syncthreads();
+  }
+  stage_p<N, P::r0, 1, FWD, false>(s, tw);
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ row pass
+// eps (stored x half-spectra) -> inverse x-DFT -> tau = sigma - c0 : eps -> forward x-DFT -> tau.
+struct RowShared {
+  int al[kMaxLoads], nal;                    // active loads
+  float dc[kMaxLoads][2][kFastRows][NP];     // [load][eps row mean, tau row sum][row][comp]
+};
+
+template <int N>
+__device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, const CellDev& c,
+                                         const FastPlanDev& fp, float4* s, RowShared& sh) {
+  constexpr int H = (N + 1) / 2;
+  int* s_al = sh.al;
+  int& s_nal = sh.nal;
+  auto& s_dc = sh.dc;
+  const int it = *A.it_dev;
+  if (threadIdx.x == 0) {
+    int nal = 0;
+    for (int l = 0; l < A.L; ++l)
+      if (A.active[t.cell * A.L + l]) s_al[nal++] = l;
+    s_nal = nal;
+  }
+  __syncthreads();
+  const int nal = s_nal;
+  if (nal == 0) return;
+  const int Hp = c.Hp, y0 = t.row0, nr = t.nrows;
+  const size_t rs = (size_t)Hp * NP;  // complex elements per stored row
+  const size_t load_stride = (size_t)N * rs;
+  CellConst<float> cc;
+  cell_const(c, cc);
+  const float lam0 = cc.lam0, mu2_0 = cc.mu2;
+  const float2* epsb = static_cast<const float2*>(A.eps[it & 1]);
+  float2* taub = static_cast<float2*>(A.tau);
+  const uint32_t* lab0 = A.label_perm + c.vox_off + (size_t)y0 * N;
+  const float2 z2 = make_float2(0.f, 0.f);
+
+  for (int la = 0; la < nal; ++la) {
+    const int l = s_al[la];
+    const float2* ein = epsb + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
+    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component
+    for (int f = threadIdx.x; f < H * NP; f += kT) {
+      const int kx = f / NP, k = f - kx * NP;
+      float2 a[kFastRows];
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r) a[r] = r < nr ? ein[(size_t)r * rs + (size_t)kx * NP + k] : z2;
+      // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
+      s[kx * NP + k] = make_float4(a[0].x - a[1].y, a[2].x - a[3].y, a[0].y + a[1].x, a[2].y + a[3].x);
+      if (kx > 0) {
+        s[(N - kx) * NP + k] = make_float4(a[0].x + a[1].y, a[2].x + a[3].y, a[1].x - a[0].y, a[3].x - a[2].y);
+      } else {
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) s_dc[la][0][r][k] = a[r].x;
+      }
+    }
+    __syncthreads();
+    fft_dif_p<N, false>(s, fp.tw4);  // inverse: eps at digit-reversed positions
+
+    // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3)
+    for (int pos = threadIdx.x; pos < N; pos += kT) {
+      uint32_t lab[kFastRows];
+      bool mixed = false;
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r) {
+        lab[r] = r < nr ? __ldg(lab0 + (size_t)r * N + pos) : 0u;
+        mixed |= (lab[r] & HOM_MIXED_BIT) != 0;
+      }
+      float4 e[NP];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) e[k] = s[pos * NP + k];
+      if (!mixed) {
+        // pure voxels: tau = (lam - lam0) tr(eps) I + (2 mu - 2 mu0) eps
+        float dl[kFastRows], dm[kFastRows];
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          const float* pc = A.phase_c32 + (size_t)lab[r] * 6;
+          const float lam = __ldg(pc + 1);
+          dl[r] = lam - lam0;
+          dm[r] = (__ldg(pc) - lam) - mu2_0;
+        }
+        const float2 dl_lo = make_float2(dl[0], dl[2]), dl_hi = make_float2(dl[1], dl[3]);
+        const float2 dm_lo = make_float2(dm[0], dm[2]), dm_hi = make_float2(dm[1], dm[3]);
+        const float2 tr_lo = add2(make_float2(e[0].x, e[0].y), make_float2(e[1].x, e[1].y));
+        const float2 tr_hi = add2(make_float2(e[0].z, e[0].w), make_float2(e[1].z, e[1].w));
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          float2 lo = mul2(dm_lo, make_float2(e[k].x, e[k].y));
+          float2 hi = mul2(dm_hi, make_float2(e[k].z, e[k].w));
+          if (k < 2) {
+            lo = fma2(dl_lo, tr_lo, lo);
+            hi = fma2(dl_hi, tr_hi, hi);
+          }
+          s[pos * NP + k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+      } else {
+        float out[NP][kFastRows];
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          float ev[NP];
+#pragma unroll
+          for (int k = 0; k < NP; ++k) ev[k] = r == 0 ? e[k].x : r == 1 ? e[k].z : r == 2 ? e[k].y : e[k].w;
+          float C[6];
+          const float* src = (lab[r] & HOM_MIXED_BIT) ? A.mixed_c32 + (size_t)(lab[r] & ~HOM_MIXED_BIT) * 6
+                                                      : A.phase_c32 + (size_t)lab[r] * 6;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) C[q] = __ldg(src + q);
+          const float tr0 = ev[0] + ev[1];
+          // packed upper triangle of the 3x3 Mandel matrix: (00, 01, 02, 11, 12, 22)
+          const float sg0 = C[0] * ev[0] + C[1] * ev[1] + C[2] * ev[2];
+          const float sg1 = C[1] * ev[0] + C[3] * ev[1] + C[4] * ev[2];
+          const float sg2 = C[2] * ev[0] + C[4] * ev[1] + C[5] * ev[2];
+          out[0][r] = sg0 - (mu2_0 * ev[0] + lam0 * tr0);
+          out[1][r] = sg1 - (mu2_0 * ev[1] + lam0 * tr0);
+          out[2][r] = sg2 - mu2_0 * ev[2];
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) s[pos * NP + k] = make_float4(out[k][0], out[k][2], out[k][1], out[k][3]);
+      }
+    }
+    __syncthreads();
+    fft_dit_p<N, true>(s, fp.tw4);  // forward: natural order
+
+    // 3. split the two real rows of each line; store the half spectra of tau
+    float2* tout = taub + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
+    for (int f = threadIdx.x; f < H * NP; f += kT) {
+      const int kx = f / NP, k = f - kx * NP;
+      const float4 Z = s[kx * NP + k];
+      const float4 Zm = s[(kx == 0 ? 0 : N - kx) * NP + k];
+      // (Z[k] + conj Z[n-k]) / 2 -> first row of a line, (Z[k] - conj Z[n-k]) / 2i -> second row
+      float2 o[kFastRows];
+      o[0] = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.z - Zm.z));
+      o[1] = make_float2(0.5f * (Z.z + Zm.z), 0.5f * (Zm.x - Z.x));
+      o[2] = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Z.w - Zm.w));
+      o[3] = make_float2(0.5f * (Z.w + Zm.w), 0.5f * (Zm.y - Z.y));
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r)
+        if (r < nr) tout[(size_t)r * rs + (size_t)kx * NP + k] = o[r];
+      if (kx == 0) {
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) s_dc[la][1][r][k] = o[r].x;
+      }
+    }
+    __syncthreads();
+  }
+  // sum of sigma over the task's rows per load and component (see the generic row pass):
+  //   sum_x sigma = sum_x tau + c0 : (n * row mean of eps), rows combined in FP64
+  if (threadIdx.x < nal * NP) {
+    const int la = threadIdx.x / NP, k = threadIdx.x - la * NP;
+    double acc = 0.0;
+    for (int r = 0; r < nr; ++r) {
+      const double tr = (double)s_dc[la][0][r][0] + (double)s_dc[la][0][r][1];
+      const double se = (double)N * (2.0 * c.mu0 * (double)s_dc[la][0][r][k] + (k < 2 ? c.lam0 * tr : 0.0));
+      acc += (double)s_dc[la][1][r][k] + se;
+    }
+    A.partR[((size_t)blockIdx.x * A.L + s_al[la]) * NP + k] = acc;
+  }
+  if (threadIdx.x == 0)
+    atomicAdd(A.bytes + HOM_K_ROW,
+              (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N * 4));
+}
+
+__global__ void __launch_bounds__(kT, 2) k_row_f2d(SolveArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RowShared sh;
+  float4* s = reinterpret_cast<float4*>(smem_raw);
+  const TaskR t = A.tR[blockIdx.x];
+  const CellDev c = A.cells[t.cell];
+  const FastPlanDev fp = A.fplans[c.fplan];
+  switch (c.n) {
+    case 45: row_body<45>(A, t, c, fp, s, sh); break;
+    case 75: row_body<75>(A, t, c, fp, s, sh); break;
+    case 135: row_body<135>(A, t, c, fp, s, sh); break;
+    case 225: row_body<225>(A, t, c, fp, s, sh); break;
+    case 405: row_body<405>(A, t, c, fp, s, sh); break;
+    case 1215: row_body<1215>(A, t, c, fp, s, sh); break;
+    default: break;
+  }
+}
+
+// ------------------------------------------------------------------ Green pass
+// tau (mixed domain) -> forward y-DFT -> Gamma0 and the residual on J (eq. 2) -> inverse y-DFT -> eps.
+template <int N>
+__device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, const CellDev& c,
+                                           const FastPlanDev& fp, float4* s) {
+  constexpr int H = (N + 1) / 2;
+  const int cl = t.cell * A.L + t.load;
+  if (!A.active[cl]) return;
+  const int it = *A.it_dev;
+  const int Hp = c.Hp, kx0 = t.kx0;
+  const bool hasB = kx0 + 1 < H;
+  const size_t rs = (size_t)Hp * NP;
+  const size_t base = c.ws_off + (size_t)t.load * N * rs + (size_t)kx0 * NP;
+  const float2* in = static_cast<const float2*>(A.tau) + base;
+  float2* out = static_cast<float2*>(A.eps[(it + 1) & 1]) + base;
+  const float2 z2 = make_float2(0.f, 0.f);
+
+  for (int f = threadIdx.x; f < N * NP; f += kT) {
+    const int y = f / NP, k = f - y * NP;
+    const float2 a = in[(size_t)y * rs + k];
+    const float2 b = hasB ? in[(size_t)y * rs + NP + k] : z2;
+    s[f] = make_float4(a.x, b.x, a.y, b.y);
+  }
+  __syncthreads();
+  fft_dif_p<N, true>(s, fp.tw4);  // forward: bin ky at position perm(ky)
+
+  CellConst<float> cc;
+  cell_const(c, cc);
+  const float2 mu0 = f2(0.5f * cc.mu2), lpm = f2(cc.lpm), ratio = f2(cc.ratio), inv_mu0 = f2(cc.inv_mu0);
+  const float inv_nv = cc.inv_nv;
+  const float rs2 = 0.707106781186547524400844362105f;
+  const float2 X = make_float2(__ldg(fp.xinat + kx0), hasB ? __ldg(fp.xinat + kx0 + 1) : 0.f);
+  const float2 X2 = mul2(X, X);
+  const float2 wgt = make_float2(kx0 == 0 ? 1.f : 2.f, hasB ? 2.f : 0.f);
+  // g of this column pair: [position][4 complex] = (kx0 d0, kx0 d1, kx0+1 d0, kx0+1 d1)
+  float4* gb = static_cast<float4*>(A.g) +
+               (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 4) / 2;
+  const double* Eld = A.E + (size_t)cl * NP;
+  float2 r2s = z2, r2c = z2, rns = z2, rnc = z2;  // Kahan sums (value, lost low part) per lane
+  for (int pos = threadIdx.x; pos < N; pos += kT) {
+    const float Yv = __ldg(fp.xipos + pos);
+    const float2 Y = f2(Yv);
+    const P2 T0 = ldp(s[pos * NP]), T1 = ldp(s[pos * NP + 1]), T2 = ldp(s[pos * NP + 2]);
+    const float4 ga = gb[2 * pos], gbv = gb[2 * pos + 1];
+    const P2 G0{make_float2(ga.x, gbv.x), make_float2(ga.y, gbv.y)};
+    const P2 G1{make_float2(ga.z, gbv.z), make_float2(ga.w, gbv.w)};
+    // v = tau_hat . xi (tau_01 = T2 / sqrt 2)
+    const P2 T01 = scale(rs2, T2);
+    const P2 V0{fma2(Y, T01.re, mul2(X, T0.re)), fma2(Y, T01.im, mul2(X, T0.im))};
+    const P2 V1{fma2(Y, T1.re, mul2(X, T01.re)), fma2(Y, T1.im, mul2(X, T01.im))};
+    const float2 q2 = fma2(Y, Y, X2);
+    const P2 XG{fma2(Y, G1.re, mul2(X, G0.re)), fma2(Y, G1.im, mul2(X, G0.im))};
+    const P2 XV{fma2(Y, V1.re, mul2(X, V0.re)), fma2(Y, V1.im, mul2(X, V0.im))};
+    // residual of the current iterate: r = tau_hat xi - K0 g, K0 g = mu0 q2 g + (lam0 + mu0) xi (xi . g)
+    const float2 mq = mul2(mu0, q2);
+    const float2 lx = mul2(lpm, X), ly = mul2(lpm, Y);
+    const P2 R0{sub2(sub2(V0.re, mul2(mq, G0.re)), mul2(lx, XG.re)), sub2(sub2(V0.im, mul2(mq, G0.im)), mul2(lx, XG.im))};
+    const P2 R1{sub2(sub2(V1.re, mul2(mq, G1.re)), mul2(ly, XG.re)), sub2(sub2(V1.im, mul2(mq, G1.im)), mul2(ly, XG.im))};
+    float2 r2 = mul2(R0.re, R0.re);
+    r2 = fma2(R0.im, R0.im, r2);
+    r2 = fma2(R1.re, R1.re, r2);
+    r2 = fma2(R1.im, R1.im, r2);
+    const bool k0 = kx0 == 0 && pos == 0;  // k = 0: eps_hat(0) = E, g = 0, no residual
+    const float2 iq = make_float2(k0 ? 0.f : __fdividef(1.f, q2.x), hasB ? __fdividef(1.f, q2.y) : 0.f);
+    // g' = K0^-1 (tau_hat xi), eps_hat' = -sym(xi (x) g') / N_v
+    const float2 imq = mul2(inv_mu0, iq);
+    const float2 rq = mul2(ratio, iq);
+    const float2 rx = mul2(rq, X), ry = mul2(rq, Y);
+    const P2 W0{mul2(imq, sub2(V0.re, mul2(rx, XV.re))), mul2(imq, sub2(V0.im, mul2(rx, XV.im)))};
+    const P2 W1{mul2(imq, sub2(V1.re, mul2(ry, XV.re))), mul2(imq, sub2(V1.im, mul2(ry, XV.im)))};
+    const float2 nx = mul2(X, f2(-inv_nv)), ny = mul2(Y, f2(-inv_nv));
+    const float2 ns = f2(-rs2 * inv_nv);
+    P2 E0{mul2(nx, W0.re), mul2(nx, W0.im)};
+    P2 E1{mul2(ny, W1.re), mul2(ny, W1.im)};
+    P2 E2{mul2(ns, fma2(X, W1.re, mul2(Y, W0.re))), mul2(ns, fma2(X, W1.im, mul2(Y, W0.im)))};
+    float4 gna = make_float4(W0.re.x, W0.im.x, W1.re.x, W1.im.x);
+    const float4 gnb = make_float4(W0.re.y, W0.im.y, W1.re.y, W1.im.y);
+    float2 wr = wgt;
+    if (k0) {
+      E0.re.x = (float)Eld[0]; E0.im.x = 0.f;
+      E1.re.x = (float)Eld[1]; E1.im.x = 0.f;
+      E2.re.x = (float)Eld[2]; E2.im.x = 0.f;
+      gna = make_float4(0.f, 0.f, 0.f, 0.f);
+      wr.x = 0.f;
+    }
+    s[pos * NP] = stp(E0);
+    s[pos * NP + 1] = stp(E1);
+    s[pos * NP + 2] = stp(E2);
+    gb[2 * pos] = gna;
+    gb[2 * pos + 1] = gnb;
+    // Kahan accumulation of wgt * r2 and wgt * r2 / q2, lane by lane
+    const float2 a1 = mul2(wr, r2), a2 = mul2(a1, iq);
+    {
+      const float2 yv = sub2(a1, r2c), tv = add2(r2s, yv);
+      r2c = sub2(sub2(tv, r2s), yv);
+      r2s = tv;
+    }
+    {
+      const float2 yv = sub2(a2, rnc), tv = add2(rns, yv);
+      rnc = sub2(sub2(tv, rns), yv);
+      rns = tv;
+    }
+  }
+  {
+    Acc<float> vv[2];
+    // combine the two lanes (each a compensated pair) into one compensated pair per sum
+    vv[0].s = r2s.x;
+    vv[0].c = r2c.x;
+    vv[0].add(r2s.y);
+    vv[0].add(-r2c.y);
+    vv[1].s = rns.x;
+    vv[1].c = rnc.x;
+    vv[1].add(rns.y);
+    vv[1].add(-rnc.y);
+    double tot[2];
+    block_sum<float, 2>(vv, tot);  // contains the barrier before the inverse transform
+    if (threadIdx.x == 0) {
+      A.partC[2 * (size_t)blockIdx.x] = tot[0];
+      A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
+    }
+  }
+  fft_dit_p<N, false>(s, fp.tw4);  // inverse: natural order
+  for (int f = threadIdx.x; f < N * NP; f += kT) {
+    const int y = f / NP, k = f - y * NP;
+    const float4 v = s[f];
+    out[(size_t)y * rs + k] = make_float2(v.x, v.z);
+    if (hasB) out[(size_t)y * rs + NP + k] = make_float2(v.y, v.w);
+  }
+  if (threadIdx.x == 0) {
+    const int ntk = hasB ? 2 : 1;
+    atomicAdd(A.bytes + HOM_K_GREEN,
+              (unsigned long long)(2 * (size_t)N * ntk * NP * sizeof(float2) + 2 * (size_t)N * ntk * 2 * sizeof(float2)));
+  }
+}
+
+__global__ void __launch_bounds__(kT, 2) k_green_f2d(SolveArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* s = reinterpret_cast<float4*>(smem_raw);
+  const TaskL t = A.tC[blockIdx.x];
+  const CellDev c = A.cells[t.cell];
+  const FastPlanDev fp = A.fplans[c.fplan];
+  switch (c.n) {
+    case 45: green_body<45>(A, t, c, fp, s); break;
+    case 75: green_body<75>(A, t, c, fp, s); break;
+    case 135: green_body<135>(A, t, c, fp, s); break;
+    case 225: green_body<225>(A, t, c, fp, s); break;
+    case 405: green_body<405>(A, t, c, fp, s); break;
+    case 1215: green_body<1215>(A, t, c, fp, s); break;
+    default: break;
+  }
+}
+
+// ------------------------------------------------------------------ labels in transform order
+__global__ void k_permute_labels(SolveArgs A, int ncells) {
+  const int ci = blockIdx.y;
+  if (ci >= ncells) return;
+  const CellDev c = A.cells[ci];
+  if (c.fplan < 0) return;
+  const FastPlanDev fp = A.fplans[c.fplan];
+  const long long nv = (long long)c.n * c.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / c.n;
+    const int pos = (int)(i - y * c.n);
+    const_cast<uint32_t*>(A.label_perm)[c.vox_off + i] = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct FastCacheEntry {
+  int dev, n;
+  FastPlanDev p;
+  void* mem;
+};
+std::mutex g_fast_mu;
+std::vector<FastCacheEntry> g_fast_cache;
+
+std::vector<int> radices_of(int n) {
+  switch (n) {
+    case 45: return {Radix<45>::r0, Radix<45>::r1};
+    case 75: return {Radix<75>::r0, Radix<75>::r1};
+    case 135: return {Radix<135>::r0, Radix<135>::r1};
+    case 225: return {Radix<225>::r0, Radix<225>::r1};
+    case 405: return {Radix<405>::r0, Radix<405>::r1, Radix<405>::r2};
+    case 1215: return {Radix<1215>::r0, Radix<1215>::r1, Radix<1215>::r2};
+    default: return {};
+  }
+}
+
+}  // namespace
+
+bool fast2d_size(int n) {
+  for (int k : kFastSizes)
+    if (k == n) return true;
+  return false;
+}
+
+int fast2d_plan(int n, FastPlanDev* out) {
+  int dev = 0;
+  HOM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_fast_mu);
+  for (const auto& e : g_fast_cache)
+    if (e.dev == dev && e.n == n) {
+      *out = e.p;
+      return HOM_OK;
+    }
+  HostPlan hp;
+  if (!fast2d_size(n) || !build_host_plan_radices(n, radices_of(n), hp))
+    return set_error(HOM_ERR_UNSUPPORTED_SIZE, "no specialised plan for n = %d", n);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4);
+  std::vector<unsigned char> h(b_tw + b_ip + b_xp + b_xn, 0);
+  float* tw = reinterpret_cast<float*>(h.data());
+  for (int t = 0; t < n; ++t) {
+    tw[4 * t] = tw[4 * t + 1] = (float)hp.tw[2 * t];
+    tw[4 * t + 2] = tw[4 * t + 3] = (float)hp.tw[2 * t + 1];
+  }
+  uint16_t* ip = reinterpret_cast<uint16_t*>(h.data() + b_tw);
+  for (int k = 0; k < n; ++k) ip[hp.perm[k]] = (uint16_t)k;
+  float* xp = reinterpret_cast<float*>(h.data() + b_tw + b_ip);
+  float* xn = reinterpret_cast<float*>(h.data() + b_tw + b_ip + b_xp);
+  for (int p = 0; p < n; ++p) xp[p] = (float)hp.xi[ip[p]];
+  for (int k = 0; k < n; ++k) xn[k] = (float)hp.xi[k];
+  void* mem = nullptr;
+  HOM_CUDA_TRY(cudaMalloc(&mem, h.size()));
+  HOM_CUDA_TRY(cudaMemcpy(mem, h.data(), h.size(), cudaMemcpyHostToDevice));
+  unsigned char* m = static_cast<unsigned char*>(mem);
+  FastPlanDev p{};
+  p.tw4 = reinterpret_cast<const float4*>(m);
+  p.iperm = reinterpret_cast<const uint16_t*>(m + b_tw);
+  p.xipos = reinterpret_cast<const float*>(m + b_tw + b_ip);
+  p.xinat = reinterpret_cast<const float*>(m + b_tw + b_ip + b_xp);
+  p.n = n;
+  g_fast_cache.push_back({dev, n, p, mem});
+  *out = p;
+  return HOM_OK;
+}
+
+void fast2d_release() {
+  std::lock_guard<std::mutex> lk(g_fast_mu);
+  for (auto& e : g_fast_cache) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(e.dev);
+    cudaFree(e.mem);
+    cudaSetDevice(cur);
+  }
+  g_fast_cache.clear();
+}
+
+size_t fast2d_smem(int nmax) { return (size_t)nmax * NP * sizeof(float4); }
+
+namespace {
+template <typename K>
+int opt_in(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) HOM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return HOM_OK;
+}
+}  // namespace
+
+int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
+  int rc = opt_in(k_row_f2d, smem);
+  if (rc != HOM_OK) return rc;
+  k_row_f2d<<<ntasks, kT, smem, st>>>(A);
+  return HOM_OK;
+}
+
+int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
+  int rc = opt_in(k_green_f2d, smem);
+  if (rc != HOM_OK) return rc;
+  k_green_f2d<<<ntasks, kT, smem, st>>>(A);
+  return HOM_OK;
+}
+
+int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st) {
+  if (ncells > 65535) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "too many cells for the label permutation");
+  const unsigned gx = (unsigned)std::min<long long>((max_nv + 255) / 256, 1024);
+  k_permute_labels<<<dim3(gx, (unsigned)ncells), 256, 0, st>>>(A, ncells);
+  HOM_CUDA_TRY(cudaGetLastError());
+  return HOM_OK;
+}
+
+}  // namespace hom

@@ -1,0 +1,40 @@
+// Specialised FP32 passes of the 2D fixed-point scheme (section 2, eqs. 1-a, 1-b, 2) for grid
+// sizes with a compile-time radix plan.  They compute what the generic row and Green passes of
+// hom_solver.cu compute, on the same mixed-domain state, task lists and partial sums; see
+// hom_fast2d.cu for the data layout in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hom {
+
+struct SolveArgs;
+
+// Device tables of one grid size n (plan with the radices compiled into the specialised passes).
+struct FastPlanDev {
+  const float4* tw4;      // (cos, cos, -sin, -sin)(2 pi t / n), t < n: twiddles duplicated per lane
+  const uint16_t* iperm;  // iperm[pos]: index held at position pos after a DIF transform
+  const float* xipos;     // 2 pi a(iperm[pos]): wave number of the bin at position pos
+  const float* xinat;     // 2 pi a(k) in natural order
+  int n, pad;
+};
+
+constexpr int kFastRows = 4;  // real rows per row-pass task (two complex lines, one lane pair)
+constexpr int kFastCols = 2;  // kx columns per Green-pass task (one lane pair)
+
+// True if n has a specialised plan.
+bool fast2d_size(int n);
+// Device tables of size n (built and uploaded on first use, kept until hom_release).
+int fast2d_plan(int n, FastPlanDev* out);
+// Dynamic shared memory of the passes for the largest grid size n of a call.
+size_t fast2d_smem(int nmax);
+// Launches (one CTA per task); `smem` from fast2d_smem.
+int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
+int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
+// label_perm[vox_off + y n + pos] = label[vox_off + y n + iperm[pos]] for every specialised cell.
+int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
+void fast2d_release();
+
+}  // namespace hom

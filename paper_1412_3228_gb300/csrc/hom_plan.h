@@ -57,9 +57,13 @@ inline bool factorize(int n, std::vector<int>& radix, int max_radix = 45) {
   return !radix.empty();
 }
 
-inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
+// Plan tables for a given radix list (DIT order); the product of the radices must be n.
+inline bool build_host_plan_radices(int n, const std::vector<int>& radix, HostPlan& p) {
   p.n = n;
-  if (!factorize(n, p.radix, max_radix)) return false;
+  p.radix = radix;
+  int prod = 1;
+  for (int r : radix) prod *= r;
+  if (prod != n || radix.empty()) return false;
   const int m = (int)p.radix.size();
   p.span.assign(m, 1);
   for (int s = 1; s < m; ++s) p.span[s] = p.span[s - 1] * p.radix[s - 1];
@@ -86,6 +90,12 @@ inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
     p.tw[2 * t + 1] = -std::sin(a);
   }
   return true;
+}
+
+inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
+  std::vector<int> radix;
+  if (!factorize(n, radix, max_radix)) return false;
+  return build_host_plan_radices(n, radix, p);
 }
 
 // Device layout of a plan's tables (each block 256-byte aligned): permutation (uint16),

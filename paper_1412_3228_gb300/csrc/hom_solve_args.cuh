@@ -1,0 +1,116 @@
+// Device-side arguments and reductions shared by the solver's pass kernels (generic passes in
+// hom_solver.cu, the specialised 2D FP32 passes in hom_fast2d.cu).
+#pragma once
+
+#include "hom_internal.h"
+
+namespace hom {
+
+struct FastPlanDev;
+
+#ifndef HOM_THREADS
+#define HOM_THREADS 256
+#endif
+constexpr int kThreads = HOM_THREADS;  // threads per CTA of the pass kernels (a build-time tunable)
+constexpr int kMaxLoads = 8;
+
+struct SolveArgs {
+  const CellDev* cells;
+  const Plan* plans;
+  const uint32_t* label;
+  const float* mixed_c32;
+  const double* mixed_c64;
+  const float* phase_c32;
+  const double* phase_c64;
+  const double* E;  // [ncells][L][nc]
+  void* eps[2];
+  void* tau;
+  void* g;
+  double* partR;    // [ntaskR][L][nc]
+  double* partC;    // [ntaskC][2]
+  const TaskR* tR;
+  const TaskL* tC;
+  const TaskL* tY;
+  const PairDev* pairs;
+  int npairs;
+  int* active;
+  int* iters;
+  int* status;
+  double* err;
+  double* errn;
+  double* mean_sigma;  // [npairs][nc]
+  double* last_err;
+  int* grow;
+  int* it_dev;
+  int* nactive;
+  unsigned int* done;
+  unsigned long long* bytes;  // [HOM_NKERNEL]
+  int L, criterion, max_iter, diverge_window;
+  double tol;
+  void* out_eps;
+  void* out_sig;
+  const void* src;  // adjoint source S (nullptr for the forward solve)
+  double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
+  const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
+  const uint32_t* label_perm; // specialised row pass: labels with x in transform order
+};
+
+// Kahan-compensated accumulation in the field precision: the running sum s and the negated
+// lost low part c (the represented value is s - c).
+template <typename T> struct Acc {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T x) {
+    T y = x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Sum K compensated partials over the block; thread 0 gets FP64 totals in out[].  For FP32 the
+// warp stage adds (sum, error) pairs with the error-free TwoSum in FP32, so FP64 arithmetic (2
+// operations per SM and cycle on this GPU) is used only for the final per-warp combination.
+// Every thread must call.
+template <typename T, int K>
+__device__ __forceinline__ void block_sum(const Acc<T> (&v)[K], double (&out)[K]) {
+  __shared__ double red[kThreads / 32][K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T hi = v[k].s, lo = -v[k].c;
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ohi = __shfl_down_sync(0xffffffffu, hi, o);
+      const T olo = __shfl_down_sync(0xffffffffu, lo, o);
+      const T t = hi + ohi;            // TwoSum(hi, ohi)
+      const T bp = t - hi;
+      const T err = (hi - (t - bp)) + (ohi - bp);
+      hi = t;
+      lo = lo + olo + err;
+    }
+    if (lane == 0) red[w][k] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < kThreads / 32; ++i) s += red[i][k];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+
+// Per-cell constants of the reference medium in the field precision (precomputed on the host).
+template <typename T> struct CellConst {
+  T lam0, mu2, lpm, ratio, inv_mu0, inv_nv;
+};
+__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<float>& k) {
+  k = {c.f_lam0, c.f_mu2, c.f_lpm, c.f_ratio, c.f_inv_mu0, c.f_inv_nv};
+}
+__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<double>& k) {
+  k = {c.d_lam0, c.d_mu2, c.d_lpm, c.d_ratio, c.d_inv_mu0, c.d_inv_nv};
+}
+
+}  // namespace hom

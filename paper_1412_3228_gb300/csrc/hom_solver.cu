@@ -21,58 +21,16 @@
 #include <cstring>
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "hom_internal.h"
 #include "hom_plan.h"
+#include "hom_solve_args.cuh"
+#include "hom_fast2d.h"
 
 namespace hom {
 namespace {
-
-#ifndef HOM_THREADS
-#define HOM_THREADS 256
-#endif
-constexpr int kThreads = HOM_THREADS;  // threads per CTA of the pass kernels (a build-time tunable)
-constexpr int kMaxLoads = 8;
-
-struct SolveArgs {
-  const CellDev* cells;
-  const Plan* plans;
-  const uint32_t* label;
-  const float* mixed_c32;
-  const double* mixed_c64;
-  const float* phase_c32;
-  const double* phase_c64;
-  const double* E;  // [ncells][L][nc]
-  void* eps[2];
-  void* tau;
-  void* g;
-  double* partR;    // [ntaskR][L][nc]
-  double* partC;    // [ntaskC][2]
-  const TaskR* tR;
-  const TaskL* tC;
-  const TaskL* tY;
-  const PairDev* pairs;
-  int npairs;
-  int* active;
-  int* iters;
-  int* status;
-  double* err;
-  double* errn;
-  double* mean_sigma;  // [npairs][nc]
-  double* last_err;
-  int* grow;
-  int* it_dev;
-  int* nactive;
-  unsigned int* done;
-  unsigned long long* bytes;  // [HOM_NKERNEL]
-  int L, criterion, max_iter, diverge_window;
-  double tol;
-  void* out_eps;
-  void* out_sig;
-  const void* src;  // adjoint source S (nullptr for the forward solve)
-  double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
-};
 
 template <typename T> __device__ __forceinline__ const T* mixed_tab(const SolveArgs& A);
 template <> __device__ __forceinline__ const float* mixed_tab<float>(const SolveArgs& A) { return A.mixed_c32; }
@@ -80,52 +38,6 @@ template <> __device__ __forceinline__ const double* mixed_tab<double>(const Sol
 template <typename T> __device__ __forceinline__ const T* phase_tab(const SolveArgs& A);
 template <> __device__ __forceinline__ const float* phase_tab<float>(const SolveArgs& A) { return A.phase_c32; }
 template <> __device__ __forceinline__ const double* phase_tab<double>(const SolveArgs& A) { return A.phase_c64; }
-
-// Kahan-compensated accumulation in the field precision: the running sum s and the negated
-// lost low part c (the represented value is s - c).
-template <typename T> struct Acc {
-  T s = T(0), c = T(0);
-  __device__ __forceinline__ void add(T x) {
-    T y = x - c;
-    T t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-};
-
-// Sum K compensated partials over the block; thread 0 gets FP64 totals in out[].  For FP32 the
-// warp stage adds (sum, error) pairs with the error-free TwoSum in FP32, so FP64 arithmetic (2
-// operations per SM and cycle on this GPU) is used only for the final per-warp combination.
-// Every thread must call.
-template <typename T, int K>
-__device__ void block_sum(const Acc<T> (&v)[K], double (&out)[K]) {
-  __shared__ double red[kThreads / 32][K];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T hi = v[k].s, lo = -v[k].c;
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ohi = __shfl_down_sync(0xffffffffu, hi, o);
-      const T olo = __shfl_down_sync(0xffffffffu, lo, o);
-      const T t = hi + ohi;            // TwoSum(hi, ohi)
-      const T bp = t - hi;
-      const T err = (hi - (t - bp)) + (ohi - bp);
-      hi = t;
-      lo = lo + olo + err;
-    }
-    if (lane == 0) red[w][k] = (double)hi + (double)lo;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < kThreads / 32; ++i) s += red[i][k];
-      out[k] = s;
-    }
-  }
-  __syncthreads();
-}
 
 __device__ __forceinline__ void load_plan(const SolveArgs& A, int idx, Plan& sp) {
   if (threadIdx.x == 0) sp = A.plans[idx];
@@ -149,17 +61,6 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <typename T> __device__ __forceinline__ const T* xi_table(const Plan& p);
 template <> __device__ __forceinline__ const float* xi_table<float>(const Plan& p) { return p.xi32; }
 template <> __device__ __forceinline__ const double* xi_table<double>(const Plan& p) { return p.xi64; }
-
-// Per-cell constants of the reference medium in the field precision (precomputed on the host).
-template <typename T> struct CellConst {
-  T lam0, mu2, lpm, ratio, inv_mu0, inv_nv;
-};
-__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<float>& k) {
-  k = {c.f_lam0, c.f_mu2, c.f_lpm, c.f_ratio, c.f_inv_mu0, c.f_inv_nv};
-}
-__device__ __forceinline__ void cell_const(const CellDev& c, CellConst<double>& k) {
-  k = {c.d_lam0, c.d_mu2, c.d_lpm, c.d_ratio, c.d_inv_mu0, c.d_inv_nv};
-}
 
 // ------------------------------------------------------------------ row pass
 // OUT = false: one iteration's row pass (eps -> tau).  OUT = true: final fields of the returned
@@ -780,6 +681,9 @@ struct Layout {
   std::vector<TaskR> tR;
   std::vector<TaskL> tC, tY;
   std::vector<PairDev> pairs;
+  std::vector<FastPlanDev> fplans;  // specialised 2D FP32 passes: per-size tables
+  bool fast = false;
+  int fast_nmax = 0;
   size_t ws_elems = 0, g_elems = 0, fld_elems = 0;
   size_t smem_row = 0, smem_green = 0, smem_y = 0;
 };
@@ -817,6 +721,16 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
   const int nc = nc_of(dim);
   const size_t budget = smem_budget();
   const size_t kMaxSmem = 227 * 1024;
+  // The specialised passes take 4-row and 2-column tasks; the output pass (generic row kernel)
+  // then needs 4 rows of every load on chip.
+  if (lay.fast) {
+    for (int ci = 0; ci < ncells; ++ci) {
+      const size_t lines = (size_t)((kFastRows * L * nc + 1) / 2) + 1;
+      if (!fast2d_size(cells[ci].n) ||
+          lines * cells[ci].n * vsize + (size_t)kFastRows * L * nc * (sizeof(long long) + vsize) > kMaxSmem)
+        lay.fast = false;
+    }
+  }
   long long vox = 0;
   std::vector<int> plan_n;
   for (int ci = 0; ci < ncells; ++ci) {
@@ -854,6 +768,21 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     } else {
       c.plan = (int)(itp - plan_n.begin());
     }
+    c.fplan = -1;
+    if (lay.fast) {
+      FastPlanDev fp{};
+      int rc = fast2d_plan(k.n, &fp);
+      if (rc != HOM_OK) return rc;
+      int idx = -1;
+      for (size_t i = 0; i < lay.fplans.size(); ++i)
+        if (lay.fplans[i].n == k.n) idx = (int)i;
+      if (idx < 0) {
+        lay.fplans.push_back(fp);
+        idx = (int)lay.fplans.size() - 1;
+      }
+      c.fplan = idx;
+      lay.fast_nmax = std::max(lay.fast_nmax, k.n);
+    }
     c.vox_off = vox;
     c.fld_off = (long long)lay.fld_elems;
     c.ws_off = (long long)lay.ws_elems;
@@ -883,6 +812,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     while (r < c.nrows &&
            row_lines(r + 1) * line_bytes + (size_t)(r + 1) * L * nc * (sizeof(long long) + vsize) <= budget)
       ++r;
+    if (lay.fast) r = std::min(kFastRows, c.nrows);
     const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * (sizeof(long long) + 2 * vsize / 2);
     if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
     lay.smem_row = std::max(lay.smem_row, need_r);
@@ -893,6 +823,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     // Green/y tiles: ntk kx columns x nc lines, plus the twiddle table and the wave-number table
     const size_t gbudget = green_budget();
     int ntk = (int)std::max<size_t>(1, (gbudget - std::min(gbudget, 2 * line_bytes)) / ((size_t)nc * line_bytes));
+    if (lay.fast) ntk = kFastCols;
     ntk = std::min(ntk, c.H);
     const size_t need_l = ((size_t)ntk * nc + 2) * line_bytes;
     lay.smem_green = std::max(lay.smem_green, need_l);
@@ -982,6 +913,10 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   using V = typename Cx<T>::V;
   const int nc = nc_of(DIM);
   Layout lay;
+  {
+    const char* fe = std::getenv("HOM_FAST2D");
+    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && !(fe && fe[0] == '0');
+  }
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1009,6 +944,13 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_dbl = take((size_t)npairs * (3 + nc) * sizeof(double));
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
+  long long nv_all = 0, nv_max = 0;
+  for (const CellDev& c : lay.cells) {
+    nv_all += c.nv;
+    nv_max = std::max(nv_max, c.nv);
+  }
+  const size_t o_lperm = lay.fast ? take((size_t)nv_all * sizeof(uint32_t)) : 0;
+  const size_t o_fplans = lay.fast ? take(lay.fplans.size() * sizeof(FastPlanDev)) : 0;
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
@@ -1050,6 +992,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     put(o_pairs, lay.pairs.data(), lay.pairs.size() * sizeof(PairDev));
     put(o_E, E, (size_t)npairs * nc * sizeof(double));
     HOM_CUDA_TRY(cudaMemcpyAsync(ws + host_lo, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+    if (lay.fast) {
+      HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_fplans, lay.fplans.data(), lay.fplans.size() * sizeof(FastPlanDev),
+                                   cudaMemcpyHostToDevice, st));
+      HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the staging vector goes out of scope
+    }
   }
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_eps0, 0, lay.ws_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_g, 0, lay.g_elems * sizeof(V), st));
@@ -1098,6 +1045,10 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
   A.src = adj ? adj->source : nullptr;
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
+  A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
+  A.label_perm = lay.fast ? reinterpret_cast<const uint32_t*>(ws + o_lperm) : nullptr;
+  const size_t smem_fast = lay.fast ? fast2d_smem(lay.fast_nmax) : 0;
+  if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
   if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
   if ((rc = allow_smem(k_row<T, DIM, true, MAXR>, lay.smem_row)) != HOM_OK) return rc;
@@ -1124,7 +1075,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   int launched = 0;
   auto one_iteration = [&]() {
     tm.begin(HOM_K_ROW);
-    k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
+    if (lay.fast) fast2d_row(A, nR, smem_fast, st);
+    else k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     if (DIM == 3) {
       tm.begin(HOM_K_YFWD);
@@ -1132,7 +1084,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
       tm.end();
     }
     tm.begin(HOM_K_GREEN);
-    k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
+    if (lay.fast) fast2d_green(A, nC, smem_fast, st);
+    else k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
     tm.end();
     if (DIM == 3) {
       tm.begin(HOM_K_YINV);
