@@ -46,6 +46,14 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return d;
 }
 
+// 16-byte asynchronous global -> shared copies (completed by cp_wait_all + a barrier).
+__device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Two complex numbers, one per line: re = (re_A, re_B), im = (im_A, im_B).
 struct P2 {
   float2 re, im;
@@ -150,7 +158,7 @@ constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};
 // One stage over the NP pairs of every position; thread t takes the butterflies t, t + kT, ...
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
 template <int N, int R, int L, bool FWD, bool DIT>
-__device__ __forceinline__ void stage_p(float4* s, const float4* __restrict__ tw) {
+__device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
   constexpr int NB = N / R, B = L * R, TS = N / B;
   for (int t = threadIdx.x; t < NB * NP; t += kT) {
     const int cc = t / NB;
@@ -164,7 +172,7 @@ __device__ __forceinline__ void stage_p(float4* s, const float4* __restrict__ tw
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         P2 x = ldp(base[q * L * NP]);
-        if (L > 1) x = twmul<FWD>(x, __ldg(tw + j * q * TS));
+        if (L > 1) x = twmul<FWD>(x, tw[j * q * TS]);
         v[q] = x;
       }
       dftp<R, FWD>(v);
@@ -178,7 +186,7 @@ __device__ __forceinline__ void stage_p(float4* s, const float4* __restrict__ tw
 #pragma unroll
       for (int p = 1; p < R; ++p) {
         P2 x = v[out_pos<R>(p)];
-        if (L > 1) x = twmul<FWD>(x, __ldg(tw + j * p * TS));
+        if (L > 1) x = twmul<FWD>(x, tw[j * p * TS]);
         base[p * L * NP] = stp(x);
       }
     }
@@ -247,29 +255,54 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
   const float lam0 = cc.lam0, mu2_0 = cc.mu2;
   const float2* epsb = static_cast<const float2*>(A.eps[it & 1]);
   float2* taub = static_cast<float2*>(A.tau);
-  const uint32_t* lab0 = A.label_perm + c.vox_off + (size_t)y0 * N;
   const float2 z2 = make_float2(0.f, 0.f);
+  // labels of the task's rows (transform order) and the twiddle table -> shared memory, behind
+  // the first loads
+  uint32_t* slab = reinterpret_cast<uint32_t*>(s + N * NP);
+  float4* tws = s + N * NP + (kFastRows * N + 3) / 4;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.label_perm + c.lp_off + (size_t)y0 * N);
+    const int nchunk = (nr * N + 3) / 4;
+    for (int i = threadIdx.x; i < nchunk; i += kT) cp16(slab + 4 * i, src + i);
+    for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
+    cp_commit();
+  }
 
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
     const float2* ein = epsb + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
-    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component
-    for (int f = threadIdx.x; f < H * NP; f += kT) {
-      const int kx = f / NP, k = f - kx * NP;
-      float2 a[kFastRows];
+    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component (U items
+    // per round: 4 U loads in flight per thread)
+    constexpr int U = 4;
+    for (int f0 = threadIdx.x; f0 < H * NP; f0 += U * kT) {
+      float2 a[U][kFastRows];
 #pragma unroll
-      for (int r = 0; r < kFastRows; ++r) a[r] = r < nr ? ein[(size_t)r * rs + (size_t)kx * NP + k] : z2;
-      // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
-      s[kx * NP + k] = make_float4(a[0].x - a[1].y, a[2].x - a[3].y, a[0].y + a[1].x, a[2].y + a[3].x);
-      if (kx > 0) {
-        s[(N - kx) * NP + k] = make_float4(a[0].x + a[1].y, a[2].x + a[3].y, a[1].x - a[0].y, a[3].x - a[2].y);
-      } else {
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
 #pragma unroll
-        for (int r = 0; r < kFastRows; ++r) s_dc[la][0][r][k] = a[r].x;
+        for (int r = 0; r < kFastRows; ++r) a[u][r] = (f < H * NP && r < nr) ? ein[(size_t)r * rs + f] : z2;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
+        if (f >= H * NP) continue;
+        const int kx = f / NP, k = f - kx * NP;
+        // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
+        const float2 q0 = a[u][0], q1 = a[u][1], q2 = a[u][2], q3 = a[u][3];
+        s[f] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
+        if (kx > 0) {
+          s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
+        } else {
+          s_dc[la][0][0][k] = q0.x;
+          s_dc[la][0][1][k] = q1.x;
+          s_dc[la][0][2][k] = q2.x;
+          s_dc[la][0][3][k] = q3.x;
+        }
       }
     }
+    cp_wait_all();
     __syncthreads();
-    fft_dif_p<N, false>(s, fp.tw4);  // inverse: eps at digit-reversed positions
+    fft_dif_p<N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3)
     for (int pos = threadIdx.x; pos < N; pos += kT) {
@@ -277,7 +310,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
       bool mixed = false;
 #pragma unroll
       for (int r = 0; r < kFastRows; ++r) {
-        lab[r] = r < nr ? __ldg(lab0 + (size_t)r * N + pos) : 0u;
+        lab[r] = r < nr ? slab[r * N + pos] : 0u;
         mixed |= (lab[r] & HOM_MIXED_BIT) != 0;
       }
       float4 e[NP];
@@ -333,7 +366,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
       }
     }
     __syncthreads();
-    fft_dit_p<N, true>(s, fp.tw4);  // forward: natural order
+    fft_dit_p<N, true>(s, tws);  // forward: natural order
 
     // 3. split the two real rows of each line; store the half spectra of tau
     float2* tout = taub + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
@@ -409,14 +442,36 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   float2* out = static_cast<float2*>(A.eps[(it + 1) & 1]) + base;
   const float2 z2 = make_float2(0.f, 0.f);
 
-  for (int f = threadIdx.x; f < N * NP; f += kT) {
-    const int y = f / NP, k = f - y * NP;
-    const float2 a = in[(size_t)y * rs + k];
-    const float2 b = hasB ? in[(size_t)y * rs + NP + k] : z2;
-    s[f] = make_float4(a.x, b.x, a.y, b.y);
+  // g of this column pair, [position][4 complex] = (kx0 d0, kx0 d1, kx0+1 d0, kx0+1 d1), and the
+  // wave numbers of the positions: copied to shared memory while the forward transform runs
+  float4* gb = static_cast<float4*>(A.g) +
+               (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 4) / 2;
+  float4* tws = s + N * NP;
+  float* sx = reinterpret_cast<float*>(tws + N);
+  for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
+  for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
+  cp_commit();
+  {
+    constexpr int U = 8;
+    for (int f0 = threadIdx.x; f0 < N * NP; f0 += U * kT) {
+      float2 a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
+        const int y = f / NP, k = f - y * NP;
+        a[u] = f < N * NP ? in[(size_t)y * rs + k] : z2;
+        b[u] = (f < N * NP && hasB) ? in[(size_t)y * rs + NP + k] : z2;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
+        if (f < N * NP) s[f] = make_float4(a[u].x, b[u].x, a[u].y, b[u].y);
+      }
+    }
   }
+  cp_wait_all();
   __syncthreads();
-  fft_dif_p<N, true>(s, fp.tw4);  // forward: bin ky at position perm(ky)
+  fft_dif_p<N, true>(s, tws);  // forward: bin ky at position perm(ky)
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -426,16 +481,22 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   const float2 X = make_float2(__ldg(fp.xinat + kx0), hasB ? __ldg(fp.xinat + kx0 + 1) : 0.f);
   const float2 X2 = mul2(X, X);
   const float2 wgt = make_float2(kx0 == 0 ? 1.f : 2.f, hasB ? 2.f : 0.f);
-  // g of this column pair: [position][4 complex] = (kx0 d0, kx0 d1, kx0+1 d0, kx0+1 d1)
-  float4* gb = static_cast<float4*>(A.g) +
-               (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 4) / 2;
   const double* Eld = A.E + (size_t)cl * NP;
   float2 r2s = z2, r2c = z2, rns = z2, rnc = z2;  // Kahan sums (value, lost low part) per lane
+  // g of the next position is loaded while the current one is processed
+  float4 gn0 = make_float4(0.f, 0.f, 0.f, 0.f), gn1 = gn0;
+  if (threadIdx.x < N) {
+    gn0 = gb[2 * threadIdx.x];
+    gn1 = gb[2 * threadIdx.x + 1];
+  }
   for (int pos = threadIdx.x; pos < N; pos += kT) {
-    const float Yv = __ldg(fp.xipos + pos);
-    const float2 Y = f2(Yv);
+    const float4 ga = gn0, gbv = gn1;
+    if (pos + kT < N) {
+      gn0 = gb[2 * (pos + kT)];
+      gn1 = gb[2 * (pos + kT) + 1];
+    }
+    const float2 Y = f2(sx[pos]);
     const P2 T0 = ldp(s[pos * NP]), T1 = ldp(s[pos * NP + 1]), T2 = ldp(s[pos * NP + 2]);
-    const float4 ga = gb[2 * pos], gbv = gb[2 * pos + 1];
     const P2 G0{make_float2(ga.x, gbv.x), make_float2(ga.y, gbv.y)};
     const P2 G1{make_float2(ga.z, gbv.z), make_float2(ga.w, gbv.w)};
     // v = tau_hat . xi (tau_01 = T2 / sqrt 2)
@@ -513,7 +574,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
     }
   }
-  fft_dit_p<N, false>(s, fp.tw4);  // inverse: natural order
+  fft_dit_p<N, false>(s, tws);  // inverse: natural order
   for (int f = threadIdx.x; f < N * NP; f += kT) {
     const int y = f / NP, k = f - y * NP;
     const float4 v = s[f];
@@ -555,7 +616,7 @@ __global__ void k_permute_labels(SolveArgs A, int ncells) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
     const long long y = i / c.n;
     const int pos = (int)(i - y * c.n);
-    const_cast<uint32_t*>(A.label_perm)[c.vox_off + i] = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
+    const_cast<uint32_t*>(A.label_perm)[c.lp_off + i] = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
   }
 }
 
@@ -641,7 +702,13 @@ void fast2d_release() {
   g_fast_cache.clear();
 }
 
-size_t fast2d_smem(int nmax) { return (size_t)nmax * NP * sizeof(float4); }
+// row: tile | labels of 4 rows | twiddles;  Green: tile | twiddles | wave numbers
+size_t fast2d_smem_row(int nmax) {
+  return (size_t)nmax * NP * sizeof(float4) + ((size_t)kFastRows * nmax + 3) / 4 * 16 + (size_t)nmax * sizeof(float4);
+}
+size_t fast2d_smem_green(int nmax) {
+  return (size_t)nmax * NP * sizeof(float4) + (size_t)nmax * sizeof(float4) + ((size_t)nmax + 3) / 4 * 16;
+}
 
 namespace {
 template <typename K>

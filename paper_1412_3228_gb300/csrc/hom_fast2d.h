@@ -28,12 +28,13 @@ constexpr int kFastCols = 2;  // kx columns per Green-pass task (one lane pair)
 bool fast2d_size(int n);
 // Device tables of size n (built and uploaded on first use, kept until hom_release).
 int fast2d_plan(int n, FastPlanDev* out);
-// Dynamic shared memory of the passes for the largest grid size n of a call.
-size_t fast2d_smem(int nmax);
-// Launches (one CTA per task); `smem` from fast2d_smem.
+// Dynamic shared memory of the row and Green passes for the largest grid size n of a call.
+size_t fast2d_smem_row(int nmax);
+size_t fast2d_smem_green(int nmax);
+// Launches (one CTA per task); `smem` from fast2d_smem_row / fast2d_smem_green.
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
 int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
-// label_perm[vox_off + y n + pos] = label[vox_off + y n + iperm[pos]] for every specialised cell.
+// label_perm[lp_off + y n + pos] = label[vox_off + y n + iperm[pos]] for every specialised cell.
 int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
 void fast2d_release();
 

@@ -945,8 +945,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
   long long nv_all = 0, nv_max = 0;
-  for (const CellDev& c : lay.cells) {
-    nv_all += c.nv;
+  for (CellDev& c : lay.cells) {
+    c.lp_off = nv_all;  // 4-voxel aligned, one spare group of 4 per cell for 16-byte copies
+    nv_all += (c.nv + 3) / 4 * 4 + 4;
     nv_max = std::max(nv_max, c.nv);
   }
   const size_t o_lperm = lay.fast ? take((size_t)nv_all * sizeof(uint32_t)) : 0;
@@ -1047,7 +1048,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label_perm = lay.fast ? reinterpret_cast<const uint32_t*>(ws + o_lperm) : nullptr;
-  const size_t smem_fast = lay.fast ? fast2d_smem(lay.fast_nmax) : 0;
+  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax) : 0;
+  const size_t smem_fgreen = lay.fast ? fast2d_smem_green(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
   if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
@@ -1075,7 +1077,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   int launched = 0;
   auto one_iteration = [&]() {
     tm.begin(HOM_K_ROW);
-    if (lay.fast) fast2d_row(A, nR, smem_fast, st);
+    if (lay.fast) fast2d_row(A, nR, smem_frow, st);
     else k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     if (DIM == 3) {
@@ -1084,7 +1086,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
       tm.end();
     }
     tm.begin(HOM_K_GREEN);
-    if (lay.fast) fast2d_green(A, nC, smem_fast, st);
+    if (lay.fast) fast2d_green(A, nC, smem_fgreen, st);
     else k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
     tm.end();
     if (DIM == 3) {
