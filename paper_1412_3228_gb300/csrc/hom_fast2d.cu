@@ -157,9 +157,11 @@ constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};
 
 // One stage over the NP pairs of every position; thread t takes the butterflies t, t + kT, ...
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
+// Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
+// (q = 1..R-1, j < L): neighbouring threads read neighbouring entries.
 template <int N, int R, int L, bool FWD, bool DIT>
 __device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
-  constexpr int NB = N / R, B = L * R, TS = N / B;
+  constexpr int NB = N / R, B = L * R;
   for (int t = threadIdx.x; t < NB * NP; t += kT) {
     const int cc = t / NB;
     const int b = t - cc * NB;
@@ -172,7 +174,7 @@ __device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         P2 x = ldp(base[q * L * NP]);
-        if (L > 1) x = twmul<FWD>(x, tw[j * q * TS]);
+        if (L > 1) x = twmul<FWD>(x, tw[(q - 1) * L + j]);
         v[q] = x;
       }
       dftp<R, FWD>(v);
@@ -186,16 +188,18 @@ __device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
 #pragma unroll
       for (int p = 1; p < R; ++p) {
         P2 x = v[out_pos<R>(p)];
-        if (L > 1) x = twmul<FWD>(x, tw[j * p * TS]);
+        if (L > 1) x = twmul<FWD>(x, tw[(p - 1) * L + j]);
         base[p * L * NP] = stp(x);
       }
     }
   }
 }
 
+// Stage tables are stored back to back: stage 1 (span r0) first, then stage 2 (span r0 r1).
 template <int N, bool FWD>
 __device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
   using P = Radix<N>;
+  constexpr int off2 = P::r0 * (P::r1 - 1);
   stage_p<N, P::r0, 1, FWD, true>(s, tw);
   __syncthreads();
   if constexpr (P::m > 1) {
@@ -203,7 +207,7 @@ __device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
     __syncthreads();
   }
   if constexpr (P::m > 2) {
-    stage_p<N, P::r2, P::r0 * P::r1, FWD, true>(s, tw);
+    stage_p<N, P::r2, P::r0 * P::r1, FWD, true>(s, tw + off2);
     __syncthreads();
   }
 }
@@ -211,8 +215,9 @@ __device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
 template <int N, bool FWD>
 __device__ __forceinline__ void fft_dif_p(float4* s, const float4* tw) {
   using P = Radix<N>;
+  constexpr int off2 = P::r0 * (P::r1 - 1);
   if constexpr (P::m > 2) {
-    stage_p<N, P::r2, P::r0 * P::r1, FWD, false>(s, tw);
+    stage_p<N, P::r2, P::r0 * P::r1, FWD, false>(s, tw + off2);
     __syncthreads();
   }
   if constexpr (P::m > 1) {
@@ -483,18 +488,22 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   const float2 wgt = make_float2(kx0 == 0 ? 1.f : 2.f, hasB ? 2.f : 0.f);
   const double* Eld = A.E + (size_t)cl * NP;
   float2 r2s = z2, r2c = z2, rns = z2, rnc = z2;  // Kahan sums (value, lost low part) per lane
-  // g of the next position is loaded while the current one is processed
-  float4 gn0 = make_float4(0.f, 0.f, 0.f, 0.f), gn1 = gn0;
-  if (threadIdx.x < N) {
-    gn0 = gb[2 * threadIdx.x];
-    gn1 = gb[2 * threadIdx.x + 1];
-  }
-  for (int pos = threadIdx.x; pos < N; pos += kT) {
-    const float4 ga = gn0, gbv = gn1;
-    if (pos + kT < N) {
-      gn0 = gb[2 * (pos + kT)];
-      gn1 = gb[2 * (pos + kT) + 1];
+  // g of every position of this thread, loaded at once
+  constexpr int NPOS = (N + kT - 1) / kT;
+  float4 gr[NPOS][2];
+#pragma unroll
+  for (int i = 0; i < NPOS; ++i) {
+    const int pos = threadIdx.x + i * kT;
+    if (pos < N) {
+      gr[i][0] = gb[2 * pos];
+      gr[i][1] = gb[2 * pos + 1];
     }
+  }
+#pragma unroll
+  for (int i = 0; i < NPOS; ++i) {
+    const int pos = threadIdx.x + i * kT;
+    if (pos >= N) break;
+    const float4 ga = gr[i][0], gbv = gr[i][1];
     const float2 Y = f2(sx[pos]);
     const P2 T0 = ldp(s[pos * NP]), T1 = ldp(s[pos * NP + 1]), T2 = ldp(s[pos * NP + 2]);
     const P2 G0{make_float2(ga.x, gbv.x), make_float2(ga.y, gbv.y)};
@@ -664,10 +673,19 @@ int fast2d_plan(int n, FastPlanDev* out) {
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4);
   std::vector<unsigned char> h(b_tw + b_ip + b_xp + b_xn, 0);
+  // per-stage twiddle tables (stages with span L > 1): entry (q - 1) L + j = w^(j q n / (L R))
   float* tw = reinterpret_cast<float*>(h.data());
-  for (int t = 0; t < n; ++t) {
-    tw[4 * t] = tw[4 * t + 1] = (float)hp.tw[2 * t];
-    tw[4 * t + 2] = tw[4 * t + 3] = (float)hp.tw[2 * t + 1];
+  {
+    size_t e = 0;
+    for (size_t st = 1; st < hp.radix.size(); ++st) {
+      const int R = hp.radix[st], L = hp.span[st], TS = n / (L * R);
+      for (int q = 1; q < R; ++q)
+        for (int j = 0; j < L; ++j, ++e) {
+          const int t = (j * q * TS) % n;
+          tw[4 * e] = tw[4 * e + 1] = (float)hp.tw[2 * t];
+          tw[4 * e + 2] = tw[4 * e + 3] = (float)hp.tw[2 * t + 1];
+        }
+    }
   }
   uint16_t* ip = reinterpret_cast<uint16_t*>(h.data() + b_tw);
   for (int k = 0; k < n; ++k) ip[hp.perm[k]] = (uint16_t)k;
