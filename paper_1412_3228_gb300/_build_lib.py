@@ -50,6 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         common += ["-Xptxas", "-v"]
     if os.environ.get("HOM_THREADS"):  # threads per CTA of the solver passes (tuning)
         common += ["-DHOM_THREADS=%d" % int(os.environ["HOM_THREADS"])]
+    if os.environ.get("HOM_FAST_THREADS"):  # threads per CTA of the specialised 2D passes (tuning)
+        common += ["-DHOM_FAST_THREADS=%d" % int(os.environ["HOM_FAST_THREADS"])]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

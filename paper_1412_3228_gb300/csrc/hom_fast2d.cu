@@ -28,7 +28,10 @@
 namespace hom {
 namespace {
 
-constexpr int kT = 256;  // threads per CTA
+#ifndef HOM_FAST_THREADS
+#define HOM_FAST_THREADS 256
+#endif
+constexpr int kT = HOM_FAST_THREADS;  // threads per CTA (a build-time tunable)
 constexpr int NP = 3;    // lane pairs per position (2D Mandel components)
 
 // ------------------------------------------------------------------ packed FP32x2 arithmetic
@@ -75,34 +78,56 @@ __device__ __forceinline__ P2 twmul(P2 a, float4 w4) {
   return P2{fma2(a.im, wi, mul2(a.re, wr)), sub2(mul2(a.im, wr), mul2(a.re, wi))};
 }
 
+// ------------------------------------------------------------------ butterfly constants
+// Every constant the register DFTs multiply by, duplicated into a lane pair, in constant memory:
+// the packed instructions can take such an operand without a register copy.
+#define HOM_TWP(R, m)                                                                              \
+  {(float)tw_cos(R, m), (float)tw_cos(R, m)}, {(float)tw_sin(R, m), (float)tw_sin(R, m)},          \
+      {(float)-tw_sin(R, m), (float)-tw_sin(R, m)}
+constexpr float kH3 = 0.866025403784438646763723170753f;  // sin(2 pi / 3)
+constexpr float kC51 = 0.309016994374947424102293417183f, kC52 = -0.809016994374947424102293417183f;
+constexpr float kS51 = 0.951056516295153572116439333379f, kS52 = 0.587785252292473129168705954639f;
+enum { KMH = 0, KH3, KNH3, KC51, KC52, KS51, KS52, KNS51, KNS52, KTW9 };
+constexpr int kTw15 = KTW9 + 27;
+__constant__ float2 kP[kTw15 + 45] = {
+    {-0.5f, -0.5f}, {kH3, kH3}, {-kH3, -kH3}, {kC51, kC51}, {kC52, kC52}, {kS51, kS51}, {kS52, kS52}, {-kS51, -kS51},
+    {-kS52, -kS52},
+    HOM_TWP(9, 0), HOM_TWP(9, 1), HOM_TWP(9, 2), HOM_TWP(9, 3), HOM_TWP(9, 4), HOM_TWP(9, 5), HOM_TWP(9, 6),
+    HOM_TWP(9, 7), HOM_TWP(9, 8),
+    HOM_TWP(15, 0), HOM_TWP(15, 1), HOM_TWP(15, 2), HOM_TWP(15, 3), HOM_TWP(15, 4), HOM_TWP(15, 5), HOM_TWP(15, 6),
+    HOM_TWP(15, 7), HOM_TWP(15, 8), HOM_TWP(15, 9), HOM_TWP(15, 10), HOM_TWP(15, 11), HOM_TWP(15, 12),
+    HOM_TWP(15, 13), HOM_TWP(15, 14)};
+#undef HOM_TWP
+template <int R> __device__ __forceinline__ constexpr int tw_base() { return R == 9 ? KTW9 : kTw15; }
+
 // ------------------------------------------------------------------ register DFTs on lane pairs
 // Forward transforms use w = exp(-2 pi i / r), inverse ones conj(w); no scaling.  Composite sizes
 // leave X[k] in v[out_pos<R>(k)] (hom_common.cuh).
 template <bool FWD>
 __device__ __forceinline__ void dft3p(P2* v) {
-  const float h = 0.866025403784438646763723170753f;  // sin(2 pi / 3)
   const P2 s = v[1] + v[2];
   const P2 d = v[1] - v[2];
-  const P2 m{fma2(s.re, f2(-0.5f), v[0].re), fma2(s.im, f2(-0.5f), v[0].im)};
+  const P2 m{fma2(s.re, kP[KMH], v[0].re), fma2(s.im, kP[KMH], v[0].im)};
   v[0] = v[0] + s;
-  const float hf = FWD ? h : -h;  // v1 = m - i hf d, v2 = m + i hf d
-  v[1] = P2{fma2(d.im, f2(hf), m.re), fma2(d.re, f2(-hf), m.im)};
-  v[2] = P2{fma2(d.im, f2(-hf), m.re), fma2(d.re, f2(hf), m.im)};
+  // v1 = m - i hf d, v2 = m + i hf d with hf = +-sin(2 pi / 3)
+  const float2 hp = kP[FWD ? KH3 : KNH3], hn = kP[FWD ? KNH3 : KH3];
+  v[1] = P2{fma2(d.im, hp, m.re), fma2(d.re, hn, m.im)};
+  v[2] = P2{fma2(d.im, hn, m.re), fma2(d.re, hp, m.im)};
 }
 
 template <bool FWD>
 __device__ __forceinline__ void dft5p(P2* v) {
-  const float c1 = 0.309016994374947424102293417183f, c2 = -0.809016994374947424102293417183f;
-  const float s1 = 0.951056516295153572116439333379f, s2 = 0.587785252292473129168705954639f;
   const P2 a1 = v[1] + v[4], b1 = v[1] - v[4];
   const P2 a2 = v[2] + v[3], b2 = v[2] - v[3];
-  const P2 r1{fma2(a2.re, f2(c2), fma2(a1.re, f2(c1), v[0].re)), fma2(a2.im, f2(c2), fma2(a1.im, f2(c1), v[0].im))};
-  const P2 r2{fma2(a2.re, f2(c1), fma2(a1.re, f2(c2), v[0].re)), fma2(a2.im, f2(c1), fma2(a1.im, f2(c2), v[0].im))};
-  const float t1 = FWD ? s1 : -s1, t2 = FWD ? s2 : -s2;
-  // i1 = t1 b1 + t2 b2, i2 = t2 b1 - t1 b2; X1 = r1 - i i1, X4 = r1 + i i1, X2 = r2 - i i2, X3 = r2 + i i2
-  const P2 i1{fma2(b2.re, f2(t2), mul2(b1.re, f2(t1))), fma2(b2.im, f2(t2), mul2(b1.im, f2(t1)))};
-  const P2 i2{fma2(b2.re, f2(-t1), mul2(b1.re, f2(t2))), fma2(b2.im, f2(-t1), mul2(b1.im, f2(t2)))};
+  const float2 c1 = kP[KC51], c2 = kP[KC52];
+  const P2 r1{fma2(a2.re, c2, fma2(a1.re, c1, v[0].re)), fma2(a2.im, c2, fma2(a1.im, c1, v[0].im))};
+  const P2 r2{fma2(a2.re, c1, fma2(a1.re, c2, v[0].re)), fma2(a2.im, c1, fma2(a1.im, c2, v[0].im))};
+  // t1 = +-s1, t2 = +-s2: i1 = t1 b1 + t2 b2, i2 = t2 b1 - t1 b2
+  const float2 t1 = kP[FWD ? KS51 : KNS51], t2 = kP[FWD ? KS52 : KNS52], nt1 = kP[FWD ? KNS51 : KS51];
+  const P2 i1{fma2(b2.re, t2, mul2(b1.re, t1)), fma2(b2.im, t2, mul2(b1.im, t1))};
+  const P2 i2{fma2(b2.re, nt1, mul2(b1.re, t2)), fma2(b2.im, nt1, mul2(b1.im, t2))};
   v[0] = v[0] + a1 + a2;
+  // X1 = r1 - i i1, X4 = r1 + i i1, X2 = r2 - i i2, X3 = r2 + i i2
   v[1] = P2{add2(r1.re, i1.im), sub2(r1.im, i1.re)};
   v[4] = P2{sub2(r1.re, i1.im), add2(r1.im, i1.re)};
   v[2] = P2{add2(r2.re, i2.im), sub2(r2.im, i2.re)};
@@ -128,8 +153,11 @@ __device__ __forceinline__ void dft_compositep(P2* v) {
       if (m == 0) {
         v[B * ka + nb] = x;
       } else {
-        const float c = (float)tw_cos(R, m), sn = FWD ? (float)(-tw_sin(R, m)) : (float)tw_sin(R, m);
-        v[B * ka + nb] = cmul_s(x, c, sn);
+        // x (cos + i sn), sn = -+sin(2 pi m / R)
+        const int b = tw_base<R>() + 3 * m;
+        const float2 c = kP[b], sp = kP[b + 1], sm = kP[b + 2];
+        const float2 sn = FWD ? sm : sp, nsn = FWD ? sp : sm;
+        v[B * ka + nb] = P2{fma2(x.im, nsn, mul2(x.re, c)), fma2(x.im, c, mul2(x.re, sn))};
       }
     }
   }
@@ -577,7 +605,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
     vv[1].add(rns.y);
     vv[1].add(-rnc.y);
     double tot[2];
-    block_sum<float, 2>(vv, tot);  // contains the barrier before the inverse transform
+    block_sum<float, 2, kT>(vv, tot);  // contains the barrier before the inverse transform
     if (threadIdx.x == 0) {
       A.partC[2 * (size_t)blockIdx.x] = tot[0];
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];

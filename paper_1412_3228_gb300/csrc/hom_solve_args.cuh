@@ -67,40 +67,51 @@ template <typename T> struct Acc {
   }
 };
 
-// Sum K compensated partials over the block; thread 0 gets FP64 totals in out[].  For FP32 the
-// warp stage adds (sum, error) pairs with the error-free TwoSum in FP32, so FP64 arithmetic (2
-// operations per SM and cycle on this GPU) is used only for the final per-warp combination.
-// Every thread must call.
-template <typename T, int K>
+// Error-free sum of (hi, lo) pairs across a warp: lane 0 ends with the total as hi + lo (TwoSum on
+// the high parts, the rounding errors collected in the low parts).
+template <typename T>
+__device__ __forceinline__ void warp_pair_sum(T& hi, T& lo) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ohi = __shfl_down_sync(0xffffffffu, hi, o);
+    const T olo = __shfl_down_sync(0xffffffffu, lo, o);
+    const T t = hi + ohi;
+    const T bp = t - hi;
+    const T err = (hi - (t - bp)) + (ohi - bp);
+    hi = t;
+    lo = lo + olo + err;
+  }
+}
+
+// Sum K compensated partials over a block of NT threads; thread 0 gets FP64 totals in out[].
+// Warps, then warp 0 over the per-warp pairs, add in the field precision with TwoSum, so FP64
+// arithmetic (2 operations per SM and cycle on this GPU) is one conversion and one addition per
+// total.  Every thread must call; blockDim.x must equal NT.
+template <typename T, int K, int NT = kThreads>
 __device__ __forceinline__ void block_sum(const Acc<T> (&v)[K], double (&out)[K]) {
-  __shared__ double red[kThreads / 32][K];
+  static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+  __shared__ T red[NT / 32][K][2];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     T hi = v[k].s, lo = -v[k].c;
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ohi = __shfl_down_sync(0xffffffffu, hi, o);
-      const T olo = __shfl_down_sync(0xffffffffu, lo, o);
-      const T t = hi + ohi;            // TwoSum(hi, ohi)
-      const T bp = t - hi;
-      const T err = (hi - (t - bp)) + (ohi - bp);
-      hi = t;
-      lo = lo + olo + err;
+    warp_pair_sum(hi, lo);
+    if (lane == 0) {
+      red[w][k][0] = hi;
+      red[w][k][1] = lo;
     }
-    if (lane == 0) red[w][k] = (double)hi + (double)lo;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (w == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < kThreads / 32; ++i) s += red[i][k];
-      out[k] = s;
+      T hi = lane < NT / 32 ? red[lane][k][0] : T(0);
+      T lo = lane < NT / 32 ? red[lane][k][1] : T(0);
+      warp_pair_sum(hi, lo);
+      if (lane == 0) out[k] = (double)hi + (double)lo;
     }
   }
   __syncthreads();
 }
-
 
 // Per-cell constants of the reference medium in the field precision (precomputed on the host).
 template <typename T> struct CellConst {
