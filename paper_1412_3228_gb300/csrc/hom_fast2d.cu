@@ -15,8 +15,14 @@
 // -> natural) of hom_common.cuh with the radices as template parameters: every index division is
 // by a compile-time constant.  The row pass works on x samples at digit-reversed positions and
 // reads labels permuted the same way (label_perm); the Green pass reads the wave number of each
-// position from a table, and keeps its displacement-like state g in its own layout
-// [load][column pair][position][4 complex], private to this pass.
+// position from a table.
+//
+// State in HBM.  The specialised passes keep the mixed-domain state (eps buffers, tau) tiled by kx
+// pairs (tile_index): one Green task reads one contiguous tile with 16-byte asynchronous copies
+// straight into its shared-memory layout, and a row task reads 192 contiguous bytes per pair.  The
+// Green pass keeps its displacement-like state g as [load][column pair][position][4 complex].
+// Both layouts are private to these passes: the initial state and the output fields are written
+// by the kernels here.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -39,15 +45,8 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  unsigned long long ra, rb, rd;
-  memcpy(&ra, &a, 8);
-  memcpy(&rb, &b, 8);
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-  float2 d;
-  memcpy(&d, &rd, 8);
-  return d;
-}
+// a - b as b * (-1) + a: one rounding, the same result as a subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // 16-byte asynchronous global -> shared copies (completed by cp_wait_all + a barrier).
 __device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
@@ -66,10 +65,6 @@ __device__ __forceinline__ float4 stp(const P2& p) { return make_float4(p.re.x, 
 __device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2{add2(a.re, b.re), add2(a.im, b.im)}; }
 __device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
 __device__ __forceinline__ P2 scale(float s, P2 a) { return P2{mul2(f2(s), a.re), mul2(f2(s), a.im)}; }
-// a * (c + i s) with scalar c, s (the same for both lines)
-__device__ __forceinline__ P2 cmul_s(P2 a, float c, float s) {
-  return P2{fma2(a.im, f2(-s), mul2(a.re, f2(c))), fma2(a.im, f2(c), mul2(a.re, f2(s)))};
-}
 // a * w (FWD) or a * conj(w) with w4 = (wr, wr, wi, wi)
 template <bool FWD>
 __device__ __forceinline__ P2 twmul(P2 a, float4 w4) {
@@ -256,39 +251,50 @@ __device__ __forceinline__ void fft_dif_p(float4* s, const float4* tw) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ state layout
+// The mixed-domain state of a cell (eps buffers and tau) is tiled by kx pairs: for load l, pair
+// p = kx / 2 (T = Hp / 2 pairs) and row y, the three components are float4 lane pairs
+// (re(kx = 2p), re(2p + 1), im(2p), im(2p + 1)).  A Green-pass task reads and writes one
+// contiguous tile of n rows; a row-pass task reads 4 consecutive rows of every pair (192 bytes).
+__device__ __forceinline__ size_t tile_index(const CellDev& c, int n, int l, int p, int y) {
+  return (size_t)c.ws_off / 2 + (((size_t)l * (c.Hp / 2) + p) * n + y) * NP;
+}
+
 // ------------------------------------------------------------------ row pass
 // eps (stored x half-spectra) -> inverse x-DFT -> tau = sigma - c0 : eps -> forward x-DFT -> tau.
+// OUT: the final fields eps and sigma of the returned iterate (real, solver output layout).
 struct RowShared {
   int al[kMaxLoads], nal;                    // active loads
   float dc[kMaxLoads][2][kFastRows][NP];     // [load][eps row mean, tau row sum][row][comp]
 };
 
-template <int N>
+template <int N, bool OUT>
 __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, const CellDev& c,
                                          const FastPlanDev& fp, float4* s, RowShared& sh) {
   constexpr int H = (N + 1) / 2;
+  constexpr int P = (H + 1) / 2;  // kx pairs holding data
   int* s_al = sh.al;
   int& s_nal = sh.nal;
   auto& s_dc = sh.dc;
   const int it = *A.it_dev;
   if (threadIdx.x == 0) {
     int nal = 0;
-    for (int l = 0; l < A.L; ++l)
-      if (A.active[t.cell * A.L + l]) s_al[nal++] = l;
+    for (int l = 0; l < A.L; ++l) {
+      const int cl = t.cell * A.L + l;
+      if (OUT || A.active[cl]) s_al[nal++] = l;
+    }
     s_nal = nal;
   }
   __syncthreads();
   const int nal = s_nal;
   if (nal == 0) return;
-  const int Hp = c.Hp, y0 = t.row0, nr = t.nrows;
-  const size_t rs = (size_t)Hp * NP;  // complex elements per stored row
-  const size_t load_stride = (size_t)N * rs;
+  const int y0 = t.row0, nr = t.nrows;
   CellConst<float> cc;
   cell_const(c, cc);
-  const float lam0 = cc.lam0, mu2_0 = cc.mu2;
-  const float2* epsb = static_cast<const float2*>(A.eps[it & 1]);
-  float2* taub = static_cast<float2*>(A.tau);
-  const float2 z2 = make_float2(0.f, 0.f);
+  // OUT: sigma = c~ : eps, i.e. the update with a zero reference medium
+  const float lam0 = OUT ? 0.f : cc.lam0, mu2_0 = OUT ? 0.f : cc.mu2;
+  float4* taub = static_cast<float4*>(A.tau);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // labels of the task's rows (transform order) and the twiddle table -> shared memory, behind
   // the first loads
   uint32_t* slab = reinterpret_cast<uint32_t*>(s + N * NP);
@@ -303,33 +309,44 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
 
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
-    const float2* ein = epsb + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
-    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component (U items
-    // per round: 4 U loads in flight per thread)
+    const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
+    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component; item
+    // (p, k) reads rows y0..y0+3 of pair p (U items per round: 4 U loads in flight per thread)
     constexpr int U = 4;
-    for (int f0 = threadIdx.x; f0 < H * NP; f0 += U * kT) {
-      float2 a[U][kFastRows];
+    for (int f0 = threadIdx.x; f0 < P * NP; f0 += U * kT) {
+      float4 v[U][kFastRows];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int f = f0 + u * kT;
+        const int p = f / NP, k = f - p * NP;
+        const size_t b = tile_index(c, N, l, p, y0) + k;
 #pragma unroll
-        for (int r = 0; r < kFastRows; ++r) a[u][r] = (f < H * NP && r < nr) ? ein[(size_t)r * rs + f] : z2;
+        for (int r = 0; r < kFastRows; ++r) v[u][r] = (f < P * NP && r < nr) ? ein[b + (size_t)r * NP] : z4;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int f = f0 + u * kT;
-        if (f >= H * NP) continue;
-        const int kx = f / NP, k = f - kx * NP;
-        // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
-        const float2 q0 = a[u][0], q1 = a[u][1], q2 = a[u][2], q3 = a[u][3];
-        s[f] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
-        if (kx > 0) {
-          s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
-        } else {
-          s_dc[la][0][0][k] = q0.x;
-          s_dc[la][0][1][k] = q1.x;
-          s_dc[la][0][2][k] = q2.x;
-          s_dc[la][0][3][k] = q3.x;
+        if (f >= P * NP) continue;
+        const int p = f / NP, k = f - p * NP;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kx = 2 * p + h;
+          if (kx >= H) break;
+          // row r at kx: (re, im) = lane h of v[u][r]
+          const float2 q0 = h ? make_float2(v[u][0].y, v[u][0].w) : make_float2(v[u][0].x, v[u][0].z);
+          const float2 q1 = h ? make_float2(v[u][1].y, v[u][1].w) : make_float2(v[u][1].x, v[u][1].z);
+          const float2 q2 = h ? make_float2(v[u][2].y, v[u][2].w) : make_float2(v[u][2].x, v[u][2].z);
+          const float2 q3 = h ? make_float2(v[u][3].y, v[u][3].w) : make_float2(v[u][3].x, v[u][3].z);
+          // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
+          s[kx * NP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
+          if (kx > 0) {
+            s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
+          } else {
+            s_dc[la][0][0][k] = q0.x;
+            s_dc[la][0][1][k] = q1.x;
+            s_dc[la][0][2][k] = q2.x;
+            s_dc[la][0][3][k] = q3.x;
+          }
         }
       }
     }
@@ -349,6 +366,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
       float4 e[NP];
 #pragma unroll
       for (int k = 0; k < NP; ++k) e[k] = s[pos * NP + k];
+      float4 o[NP];
       if (!mixed) {
         // pure voxels: tau = (lam - lam0) tr(eps) I + (2 mu - 2 mu0) eps
         float dl[kFastRows], dm[kFastRows];
@@ -371,7 +389,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
             lo = fma2(dl_lo, tr_lo, lo);
             hi = fma2(dl_hi, tr_hi, hi);
           }
-          s[pos * NP + k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+          o[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
       } else {
         float out[NP][kFastRows];
@@ -395,33 +413,79 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
           out[2][r] = sg2 - mu2_0 * ev[2];
         }
 #pragma unroll
-        for (int k = 0; k < NP; ++k) s[pos * NP + k] = make_float4(out[k][0], out[k][2], out[k][1], out[k][3]);
+        for (int k = 0; k < NP; ++k) o[k] = make_float4(out[k][0], out[k][2], out[k][1], out[k][3]);
+      }
+      if (OUT) {
+        // real fields of rows y0 + r at x = iperm[pos]
+        const int x = __ldg(fp.iperm + pos);
+        float* oe = static_cast<float*>(A.out_eps);
+        float* os = static_cast<float*>(A.out_sig);
+        const size_t base = c.fld_off + (size_t)l * NP * c.nv + (size_t)y0 * N + x;
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          if (r >= nr) break;
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            const float ev = r == 0 ? e[k].x : r == 1 ? e[k].z : r == 2 ? e[k].y : e[k].w;
+            const float sv = r == 0 ? o[k].x : r == 1 ? o[k].z : r == 2 ? o[k].y : o[k].w;
+            const size_t ad = base + (size_t)k * c.nv + (size_t)r * N;
+            if (oe) oe[ad] = ev;
+            if (os) os[ad] = sv;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) s[pos * NP + k] = o[k];
       }
     }
+    if (OUT) continue;
     __syncthreads();
     fft_dit_p<N, true>(s, tws);  // forward: natural order
 
-    // 3. split the two real rows of each line; store the half spectra of tau
-    float2* tout = taub + c.ws_off + (size_t)l * load_stride + (size_t)y0 * rs;
-    for (int f = threadIdx.x; f < H * NP; f += kT) {
-      const int kx = f / NP, k = f - kx * NP;
-      const float4 Z = s[kx * NP + k];
-      const float4 Zm = s[(kx == 0 ? 0 : N - kx) * NP + k];
-      // (Z[k] + conj Z[n-k]) / 2 -> first row of a line, (Z[k] - conj Z[n-k]) / 2i -> second row
-      float2 o[kFastRows];
-      o[0] = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.z - Zm.z));
-      o[1] = make_float2(0.5f * (Z.z + Zm.z), 0.5f * (Zm.x - Z.x));
-      o[2] = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Z.w - Zm.w));
-      o[3] = make_float2(0.5f * (Z.w + Zm.w), 0.5f * (Zm.y - Z.y));
+    // 3. split the two real rows of each line; store the half spectra of tau, pair by pair
+    for (int f = threadIdx.x; f < P * NP; f += kT) {
+      const int p = f / NP, k = f - p * NP;
+      float4 w[kFastRows];  // rows 0..3 at (kx = 2p, 2p + 1): (re, re, im, im)
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r) w[r] = z4;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int kx = 2 * p + h;
+        if (kx >= H) break;
+        const float4 Z = s[kx * NP + k];
+        const float4 Zm = s[(kx == 0 ? 0 : N - kx) * NP + k];
+        // (Z[k] + conj Z[n-k]) / 2 -> first row of a line, (Z[k] - conj Z[n-k]) / 2i -> second row
+        const float2 o0 = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.z - Zm.z));
+        const float2 o1 = make_float2(0.5f * (Z.z + Zm.z), 0.5f * (Zm.x - Z.x));
+        const float2 o2 = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Z.w - Zm.w));
+        const float2 o3 = make_float2(0.5f * (Z.w + Zm.w), 0.5f * (Zm.y - Z.y));
+        if (h == 0) {
+          w[0].x = o0.x; w[0].z = o0.y; w[1].x = o1.x; w[1].z = o1.y;
+          w[2].x = o2.x; w[2].z = o2.y; w[3].x = o3.x; w[3].z = o3.y;
+          if (kx == 0) {
+            s_dc[la][1][0][k] = o0.x;
+            s_dc[la][1][1][k] = o1.x;
+            s_dc[la][1][2][k] = o2.x;
+            s_dc[la][1][3][k] = o3.x;
+          }
+        } else {
+          w[0].y = o0.x; w[0].w = o0.y; w[1].y = o1.x; w[1].w = o1.y;
+          w[2].y = o2.x; w[2].w = o2.y; w[3].y = o3.x; w[3].w = o3.y;
+        }
+      }
+      const size_t b = tile_index(c, N, l, p, y0) + k;
 #pragma unroll
       for (int r = 0; r < kFastRows; ++r)
-        if (r < nr) tout[(size_t)r * rs + (size_t)kx * NP + k] = o[r];
-      if (kx == 0) {
-#pragma unroll
-        for (int r = 0; r < kFastRows; ++r) s_dc[la][1][r][k] = o[r].x;
-      }
+        if (r < nr) taub[b + (size_t)r * NP] = w[r];
     }
     __syncthreads();
+  }
+  if (OUT) {
+    if (threadIdx.x == 0)
+      atomicAdd(A.bytes + HOM_K_OUTPUT,
+                (unsigned long long)((size_t)nal * nr * NP * (H * sizeof(float2) + 2 * (size_t)N * sizeof(float)) +
+                                     (size_t)nr * N * 4));
+    return;
   }
   // sum of sigma over the task's rows per load and component (see the generic row pass):
   //   sum_x sigma = sum_x tau + c0 : (n * row mean of eps), rows combined in FP64
@@ -440,6 +504,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
               (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N * 4));
 }
 
+template <bool OUT>
 __global__ void __launch_bounds__(kT, 2) k_row_f2d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared sh;
@@ -448,13 +513,29 @@ __global__ void __launch_bounds__(kT, 2) k_row_f2d(SolveArgs A) {
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 45: row_body<45>(A, t, c, fp, s, sh); break;
-    case 75: row_body<75>(A, t, c, fp, s, sh); break;
-    case 135: row_body<135>(A, t, c, fp, s, sh); break;
-    case 225: row_body<225>(A, t, c, fp, s, sh); break;
-    case 405: row_body<405>(A, t, c, fp, s, sh); break;
-    case 1215: row_body<1215>(A, t, c, fp, s, sh); break;
+    case 45: row_body<45, OUT>(A, t, c, fp, s, sh); break;
+    case 75: row_body<75, OUT>(A, t, c, fp, s, sh); break;
+    case 135: row_body<135, OUT>(A, t, c, fp, s, sh); break;
+    case 225: row_body<225, OUT>(A, t, c, fp, s, sh); break;
+    case 405: row_body<405, OUT>(A, t, c, fp, s, sh); break;
+    case 1215: row_body<1215, OUT>(A, t, c, fp, s, sh); break;
     default: break;
+  }
+}
+
+// eps = E: the stored x-spectrum holds E at kx = 0 of every row (lane A of pair 0), zero elsewhere.
+__global__ void k_init_f2d(SolveArgs A, int ncells) {
+  for (int cell = blockIdx.y; cell < ncells; cell += gridDim.y) {
+    const CellDev c = A.cells[cell];
+    const long long items = (long long)A.L * c.n * NP;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < items; i += (long long)gridDim.x * blockDim.x) {
+      const int k = (int)(i % NP);
+      const long long r = i / NP;
+      const int y = (int)(r % c.n);
+      const int l = (int)(r / c.n);
+      static_cast<float4*>(A.eps[0])[tile_index(c, c.n, l, 0, y) + k] =
+          make_float4((float)A.E[((size_t)cell * A.L + l) * NP + k], 0.f, 0.f, 0.f);
+    }
   }
 }
 
@@ -469,39 +550,21 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   const int it = *A.it_dev;
   const int Hp = c.Hp, kx0 = t.kx0;
   const bool hasB = kx0 + 1 < H;
-  const size_t rs = (size_t)Hp * NP;
-  const size_t base = c.ws_off + (size_t)t.load * N * rs + (size_t)kx0 * NP;
-  const float2* in = static_cast<const float2*>(A.tau) + base;
-  float2* out = static_cast<float2*>(A.eps[(it + 1) & 1]) + base;
+  // this task's tile (pair kx0 / 2 of its load): n rows x 3 components, contiguous
+  const size_t tb = tile_index(c, N, t.load, kx0 / 2, 0);
+  const float4* in = static_cast<const float4*>(A.tau) + tb;
+  float4* out = static_cast<float4*>(A.eps[(it + 1) & 1]) + tb;
   const float2 z2 = make_float2(0.f, 0.f);
-
-  // g of this column pair, [position][4 complex] = (kx0 d0, kx0 d1, kx0+1 d0, kx0+1 d1), and the
-  // wave numbers of the positions: copied to shared memory while the forward transform runs
+  // g of this column pair, [position][4 complex] = (kx0 d0, kx0 d1, kx0+1 d0, kx0+1 d1)
   float4* gb = static_cast<float4*>(A.g) +
                (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 4) / 2;
+  // tile, twiddles and the wave numbers of the positions -> shared memory
   float4* tws = s + N * NP;
   float* sx = reinterpret_cast<float*>(tws + N);
+  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + i, in + i);
   for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
   for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
-  {
-    constexpr int U = 8;
-    for (int f0 = threadIdx.x; f0 < N * NP; f0 += U * kT) {
-      float2 a[U], b[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int f = f0 + u * kT;
-        const int y = f / NP, k = f - y * NP;
-        a[u] = f < N * NP ? in[(size_t)y * rs + k] : z2;
-        b[u] = (f < N * NP && hasB) ? in[(size_t)y * rs + NP + k] : z2;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int f = f0 + u * kT;
-        if (f < N * NP) s[f] = make_float4(a[u].x, b[u].x, a[u].y, b[u].y);
-      }
-    }
-  }
   cp_wait_all();
   __syncthreads();
   fft_dif_p<N, true>(s, tws);  // forward: bin ky at position perm(ky)
@@ -612,12 +675,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
     }
   }
   fft_dit_p<N, false>(s, tws);  // inverse: natural order
-  for (int f = threadIdx.x; f < N * NP; f += kT) {
-    const int y = f / NP, k = f - y * NP;
-    const float4 v = s[f];
-    out[(size_t)y * rs + k] = make_float2(v.x, v.z);
-    if (hasB) out[(size_t)y * rs + NP + k] = make_float2(v.y, v.w);
-  }
+  for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
   if (threadIdx.x == 0) {
     const int ntk = hasB ? 2 : 1;
     atomicAdd(A.bytes + HOM_K_GREEN,
@@ -765,9 +823,22 @@ int opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
-  int rc = opt_in(k_row_f2d, smem);
+  int rc = opt_in(k_row_f2d<false>, smem);
   if (rc != HOM_OK) return rc;
-  k_row_f2d<<<ntasks, kT, smem, st>>>(A);
+  k_row_f2d<false><<<ntasks, kT, smem, st>>>(A);
+  return HOM_OK;
+}
+
+int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
+  int rc = opt_in(k_row_f2d<true>, smem);
+  if (rc != HOM_OK) return rc;
+  k_row_f2d<true><<<ntasks, kT, smem, st>>>(A);
+  return HOM_OK;
+}
+
+int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st) {
+  dim3 grid(64, (unsigned)std::min(ncells, 65535));
+  k_init_f2d<<<grid, 256, 0, st>>>(A, ncells);
   return HOM_OK;
 }
 

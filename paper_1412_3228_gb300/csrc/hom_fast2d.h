@@ -34,6 +34,10 @@ size_t fast2d_smem_green(int nmax);
 // Launches (one CTA per task); `smem` from fast2d_smem_row / fast2d_smem_green.
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
 int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
+// Output pass (final eps and sigma fields) and the initial state eps = E, in the tiled layout of
+// the specialised passes (see hom_fast2d.cu).
+int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
+int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st);
 // label_perm[lp_off + y n + pos] = label[vox_off + y n + iperm[pos]] for every specialised cell.
 int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
 void fast2d_release();

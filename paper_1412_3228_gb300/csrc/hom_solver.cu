@@ -1065,7 +1065,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const unsigned nCtl = (unsigned)((npairs * 32 + kThreads - 1) / kThreads);
   tm.begin(HOM_K_INIT);
   k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
-  {
+  if (lay.fast) {
+    fast2d_init(A, ncells, st);
+  } else {
     dim3 grid(64, (unsigned)std::min(ncells, 65535));
     k_init<T><<<grid, 256, 0, st>>>(A, ncells, nc);
   }
@@ -1139,7 +1141,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
   if (want_fields) {
     tm.begin(HOM_K_OUTPUT);
-    k_row<T, DIM, true, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
+    if (lay.fast) fast2d_out(A, nR, smem_frow, st);
+    else k_row<T, DIM, true, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     HOM_CUDA_TRY(cudaGetLastError());
     if (out->eps && !eps_dev)
