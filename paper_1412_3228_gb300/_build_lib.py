@@ -50,6 +50,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         common += ["-Xptxas", "-v"]
     if os.environ.get("HOM_THREADS"):  # threads per CTA of the solver passes (tuning)
         common += ["-DHOM_THREADS=%d" % int(os.environ["HOM_THREADS"])]
+    if os.environ.get("HOM_GREEN_TW2"):  # Green pass with a scalar twiddle table (tuning)
+        common += ["-DHOM_GREEN_TW2=%d" % int(os.environ["HOM_GREEN_TW2"])]
+    if os.environ.get("HOM_ROW_TW2"):  # row pass with a scalar twiddle table (tuning)
+        common += ["-DHOM_ROW_TW2=%d" % int(os.environ["HOM_ROW_TW2"])]
     if os.environ.get("HOM_FAST_THREADS"):  # threads per CTA of the specialised 2D passes (tuning)
         common += ["-DHOM_FAST_THREADS=%d" % int(os.environ["HOM_FAST_THREADS"])]
 

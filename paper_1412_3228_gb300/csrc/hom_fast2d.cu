@@ -14,7 +14,7 @@
 // Transforms are the in-place mixed-radix DIF (natural -> digit-reversed) and DIT (digit-reversed
 // -> natural) of hom_common.cuh with the radices as template parameters: every index division is
 // by a compile-time constant.  The row pass works on x samples at digit-reversed positions and
-// reads labels permuted the same way (label_perm); the Green pass reads the wave number of each
+// reads one-byte labels permuted the same way (label8); the Green pass reads the wave number of each
 // position from a table.
 //
 // State in HBM.  The specialised passes keep the mixed-domain state (eps buffers, tau) tiled by kx
@@ -34,6 +34,12 @@
 namespace hom {
 namespace {
 
+#ifndef HOM_GREEN_TW2
+#define HOM_GREEN_TW2 1  // Green pass with a scalar twiddle table (three CTAs per SM)
+#endif
+#ifndef HOM_ROW_TW2
+#define HOM_ROW_TW2 0    // row pass with a scalar twiddle table (three CTAs per SM; measured slower)
+#endif
 #ifndef HOM_FAST_THREADS
 #define HOM_FAST_THREADS 256
 #endif
@@ -71,6 +77,12 @@ __device__ __forceinline__ P2 twmul(P2 a, float4 w4) {
   const float2 wr = make_float2(w4.x, w4.y), wi = make_float2(w4.z, w4.w);
   if (FWD) return P2{sub2(mul2(a.re, wr), mul2(a.im, wi)), fma2(a.re, wi, mul2(a.im, wr))};
   return P2{fma2(a.im, wi, mul2(a.re, wr)), sub2(mul2(a.im, wr), mul2(a.re, wi))};
+}
+
+// a * w (FWD) or a * conj(w) with a scalar twiddle w = (wr, wi), broadcast to both lanes
+template <bool FWD>
+__device__ __forceinline__ P2 twmul(P2 a, float2 w) {
+  return twmul<FWD>(a, make_float4(w.x, w.x, w.y, w.y));
 }
 
 // ------------------------------------------------------------------ butterfly constants
@@ -182,8 +194,8 @@ constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
 // Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
 // (q = 1..R-1, j < L): neighbouring threads read neighbouring entries.
-template <int N, int R, int L, bool FWD, bool DIT>
-__device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
+template <int N, int R, int L, bool FWD, bool DIT, typename TW>
+__device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
   constexpr int NB = N / R, B = L * R;
   for (int t = threadIdx.x; t < NB * NP; t += kT) {
     const int cc = t / NB;
@@ -219,8 +231,8 @@ __device__ __forceinline__ void stage_p(float4* s, const float4* tw) {
 }
 
 // Stage tables are stored back to back: stage 1 (span r0) first, then stage 2 (span r0 r1).
-template <int N, bool FWD>
-__device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
+template <int N, bool FWD, typename TW>
+__device__ __forceinline__ void fft_dit_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
   stage_p<N, P::r0, 1, FWD, true>(s, tw);
@@ -235,8 +247,8 @@ __device__ __forceinline__ void fft_dit_p(float4* s, const float4* tw) {
   }
 }
 
-template <int N, bool FWD>
-__device__ __forceinline__ void fft_dif_p(float4* s, const float4* tw) {
+template <int N, bool FWD, typename TW>
+__device__ __forceinline__ void fft_dif_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
   if constexpr (P::m > 2) {
@@ -259,6 +271,8 @@ __device__ __forceinline__ void fft_dif_p(float4* s, const float4* tw) {
 __device__ __forceinline__ size_t tile_index(const CellDev& c, int n, int l, int p, int y) {
   return (size_t)c.ws_off / 2 + (((size_t)l * (c.Hp / 2) + p) * n + y) * NP;
 }
+
+constexpr uint32_t kLabel8Mixed = 255;  // one-byte label of a mixed voxel
 
 // ------------------------------------------------------------------ row pass
 // eps (stored x half-spectra) -> inverse x-DFT -> tau = sigma - c0 : eps -> forward x-DFT -> tau.
@@ -295,17 +309,22 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
   const float lam0 = OUT ? 0.f : cc.lam0, mu2_0 = OUT ? 0.f : cc.mu2;
   float4* taub = static_cast<float4*>(A.tau);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // labels of the task's rows (transform order) and the twiddle table -> shared memory, behind
-  // the first loads
-  uint32_t* slab = reinterpret_cast<uint32_t*>(s + N * NP);
-  float4* tws = s + N * NP + (kFastRows * N + 3) / 4;
+  // one-byte labels of the task's rows (transform order) and the twiddle table -> shared memory,
+  // behind the first loads
+  constexpr int NL = (N + 15) / 16 * 16;  // label row stride (bytes)
+  uint8_t* slab = reinterpret_cast<uint8_t*>(s + N * NP);
   {
-    const uint4* src = reinterpret_cast<const uint4*>(A.label_perm + c.lp_off + (size_t)y0 * N);
-    const int nchunk = (nr * N + 3) / 4;
-    for (int i = threadIdx.x; i < nchunk; i += kT) cp16(slab + 4 * i, src + i);
-    for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
-    cp_commit();
+    const uint4* src = reinterpret_cast<const uint4*>(A.label8 + c.lp_off + (size_t)y0 * NL);
+    for (int i = threadIdx.x; i < nr * NL / 16; i += kT) cp16(slab + 16 * i, src + i);
   }
+#if HOM_ROW_TW2
+  float2* tws = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16);
+  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+#else
+  float4* tws = s + N * NP + kFastRows * NL / 16;
+  for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
+#endif
+  cp_commit();
 
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
@@ -354,14 +373,21 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     __syncthreads();
     fft_dif_p<N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
-    // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3)
+    // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3).  A one-byte
+    // label is the phase of a pure voxel, or kLabel8Mixed (full label read from the material).
     for (int pos = threadIdx.x; pos < N; pos += kT) {
       uint32_t lab[kFastRows];
       bool mixed = false;
 #pragma unroll
       for (int r = 0; r < kFastRows; ++r) {
-        lab[r] = r < nr ? slab[r * N + pos] : 0u;
-        mixed |= (lab[r] & HOM_MIXED_BIT) != 0;
+        lab[r] = r < nr ? (uint32_t)slab[r * NL + pos] : 0u;
+        mixed |= lab[r] == kLabel8Mixed;
+      }
+      if (mixed) {
+        const int x = __ldg(fp.iperm + pos);
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r)
+          if (lab[r] == kLabel8Mixed) lab[r] = __ldg(A.label + c.vox_off + (size_t)(y0 + r) * N + x);
       }
       float4 e[NP];
 #pragma unroll
@@ -501,11 +527,11 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_ROW,
-              (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N * 4));
+              (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N));
 }
 
 template <bool OUT>
-__global__ void __launch_bounds__(kT, 2) k_row_f2d(SolveArgs A) {
+__global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
@@ -559,10 +585,16 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   float4* gb = static_cast<float4*>(A.g) +
                (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 4) / 2;
   // tile, twiddles and the wave numbers of the positions -> shared memory
+#if HOM_GREEN_TW2
+  float2* tws = reinterpret_cast<float2*>(s + N * NP);  // scalar twiddles: 3 CTAs per SM fit
+  float* sx = reinterpret_cast<float*>(s + N * NP + (N + 1) / 2);
+  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+#else
   float4* tws = s + N * NP;
   float* sx = reinterpret_cast<float*>(tws + N);
-  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + i, in + i);
   for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
+#endif
+  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + i, in + i);
   for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
   cp_wait_all();
@@ -683,7 +715,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   }
 }
 
-__global__ void __launch_bounds__(kT, 2) k_green_f2d(SolveArgs A) {
+__global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const TaskL t = A.tC[blockIdx.x];
@@ -711,7 +743,10 @@ __global__ void k_permute_labels(SolveArgs A, int ncells) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
     const long long y = i / c.n;
     const int pos = (int)(i - y * c.n);
-    const_cast<uint32_t*>(A.label_perm)[c.lp_off + i] = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
+    const uint32_t lab = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
+    const int nl = (c.n + 15) / 16 * 16;
+    const_cast<uint8_t*>(A.label8)[c.lp_off + y * nl + pos] =
+        (lab & HOM_MIXED_BIT) ? (uint8_t)kLabel8Mixed : (uint8_t)lab;
   }
 }
 
@@ -757,8 +792,9 @@ int fast2d_plan(int n, FastPlanDev* out) {
   if (!fast2d_size(n) || !build_host_plan_radices(n, radices_of(n), hp))
     return set_error(HOM_ERR_UNSUPPORTED_SIZE, "no specialised plan for n = %d", n);
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4);
-  std::vector<unsigned char> h(b_tw + b_ip + b_xp + b_xn, 0);
+  const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4),
+               b_t2 = up((size_t)n * 8 + 8);
+  std::vector<unsigned char> h(b_tw + b_ip + b_xp + b_xn + b_t2, 0);
   // per-stage twiddle tables (stages with span L > 1): entry (q - 1) L + j = w^(j q n / (L R))
   float* tw = reinterpret_cast<float*>(h.data());
   {
@@ -770,6 +806,9 @@ int fast2d_plan(int n, FastPlanDev* out) {
           const int t = (j * q * TS) % n;
           tw[4 * e] = tw[4 * e + 1] = (float)hp.tw[2 * t];
           tw[4 * e + 2] = tw[4 * e + 3] = (float)hp.tw[2 * t + 1];
+          float* t2 = reinterpret_cast<float*>(h.data() + b_tw + b_ip + b_xp + b_xn);
+          t2[2 * e] = (float)hp.tw[2 * t];
+          t2[2 * e + 1] = (float)hp.tw[2 * t + 1];
         }
     }
   }
@@ -788,6 +827,7 @@ int fast2d_plan(int n, FastPlanDev* out) {
   p.iperm = reinterpret_cast<const uint16_t*>(m + b_tw);
   p.xipos = reinterpret_cast<const float*>(m + b_tw + b_ip);
   p.xinat = reinterpret_cast<const float*>(m + b_tw + b_ip + b_xp);
+  p.tw2 = reinterpret_cast<const float2*>(m + b_tw + b_ip + b_xp + b_xn);
   p.n = n;
   g_fast_cache.push_back({dev, n, p, mem});
   *out = p;
@@ -807,11 +847,15 @@ void fast2d_release() {
 }
 
 // row: tile | labels of 4 rows | twiddles;  Green: tile | twiddles | wave numbers
+// row: tile | one-byte labels of 4 rows | twiddles
 size_t fast2d_smem_row(int nmax) {
-  return (size_t)nmax * NP * sizeof(float4) + ((size_t)kFastRows * nmax + 3) / 4 * 16 + (size_t)nmax * sizeof(float4);
+  const size_t labels = (size_t)kFastRows * ((nmax + 15) / 16 * 16);
+  const size_t tw = HOM_ROW_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
+  return (size_t)nmax * NP * sizeof(float4) + labels + tw;
 }
 size_t fast2d_smem_green(int nmax) {
-  return (size_t)nmax * NP * sizeof(float4) + (size_t)nmax * sizeof(float4) + ((size_t)nmax + 3) / 4 * 16;
+  const size_t tw = HOM_GREEN_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
+  return (size_t)nmax * NP * sizeof(float4) + tw + ((size_t)nmax + 3) / 4 * 16;
 }
 
 namespace {

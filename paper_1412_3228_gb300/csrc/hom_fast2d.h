@@ -18,6 +18,7 @@ struct FastPlanDev {
   const uint16_t* iperm;  // iperm[pos]: index held at position pos after a DIF transform
   const float* xipos;     // 2 pi a(iperm[pos]): wave number of the bin at position pos
   const float* xinat;     // 2 pi a(k) in natural order
+  const float2* tw2;      // the twiddle tables as (cos, -sin) pairs
   int n, pad;
 };
 
@@ -38,7 +39,8 @@ int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t 
 // the specialised passes (see hom_fast2d.cu).
 int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
 int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st);
-// label_perm[lp_off + y n + pos] = label[vox_off + y n + iperm[pos]] for every specialised cell.
+// label8[lp_off + y nl + pos] = phase of label[vox_off + y n + iperm[pos]] (255 for a mixed voxel,
+// nl = n rounded up to 16) for every specialised cell; requires fewer than 255 phases.
 int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
 void fast2d_release();
 

@@ -104,7 +104,7 @@ struct CellDev {         // one cell of the solver
   double lam0, mu0;
   int rtask0, rtask1;    // row-pass task range
   int fplan;             // specialised passes: index of the size's tables (-1: generic passes)
-  long long lp_off;      // specialised passes: offset of the cell in the permuted labels (16-byte aligned)
+  long long lp_off;      // specialised passes: byte offset of the cell in the one-byte labels (16-aligned)
   // per-cell constants, computed on the host (FP64 arithmetic is slow on the device)
   float f_lam0, f_mu2, f_lpm, f_ratio, f_inv_mu0, f_inv_nv;
   double d_lam0, d_mu2, d_lpm, d_ratio, d_inv_mu0, d_inv_nv;

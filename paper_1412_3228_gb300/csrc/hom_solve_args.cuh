@@ -52,7 +52,7 @@ struct SolveArgs {
   const void* src;  // adjoint source S (nullptr for the forward solve)
   double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
-  const uint32_t* label_perm; // specialised row pass: labels with x in transform order
+  const uint8_t* label8;      // specialised row pass: phase (255: mixed) with x in transform order
 };
 
 // Kahan-compensated accumulation in the field precision: the running sum s and the negated

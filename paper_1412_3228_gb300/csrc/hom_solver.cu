@@ -915,7 +915,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   Layout lay;
   {
     const char* fe = std::getenv("HOM_FAST2D");
-    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && !(fe && fe[0] == '0');
+    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && mat->nphase < 255 &&
+               !(fe && fe[0] == '0');
   }
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
@@ -946,11 +947,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
   long long nv_all = 0, nv_max = 0;
   for (CellDev& c : lay.cells) {
-    c.lp_off = nv_all;  // 4-voxel aligned, one spare group of 4 per cell for 16-byte copies
-    nv_all += (c.nv + 3) / 4 * 4 + 4;
+    c.lp_off = nv_all;  // one-byte labels, rows padded to 16 bytes
+    nv_all += (long long)c.nrows * ((c.n + 15) / 16 * 16);
     nv_max = std::max(nv_max, c.nv);
   }
-  const size_t o_lperm = lay.fast ? take((size_t)nv_all * sizeof(uint32_t)) : 0;
+  const size_t o_lperm = lay.fast ? take((size_t)nv_all) : 0;
   const size_t o_fplans = lay.fast ? take(lay.fplans.size() * sizeof(FastPlanDev)) : 0;
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
@@ -1047,7 +1048,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.src = adj ? adj->source : nullptr;
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
-  A.label_perm = lay.fast ? reinterpret_cast<const uint32_t*>(ws + o_lperm) : nullptr;
+  A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
   const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax) : 0;
   const size_t smem_fgreen = lay.fast ? fast2d_smem_green(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
