@@ -121,6 +121,13 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
+# DRAM bytes (read + write) per algorithmic byte of the specialised FP32 2D passes, from the ncu
+# capture summarised in profiles/k_row_f2d_k_green_f2d_1215_fp32.md (two 1215^2 cells x 3 loads;
+# traffic grows with the tiles processed, so a launch's traffic is this ratio times its bytes).
+# Valid for the kernels as captured there; None for kernels without a capture.
+TRAFFIC_RATIO = {"row": (110.056 + 55.197) / 215.77, "green": (177.548 + 116.237) / 354.61}
+
+
 def golden_ceff():
     p = os.path.join(ROOT, "tests", "golden", "sweep2d_ceff.json")
     if not os.path.exists(p):
@@ -255,7 +262,9 @@ def run_ours(args, rank, world):
     total_kms = sum(v["ms"] for v in kstats.values())
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": peak_kind,
-                "traffic": None,
+                "traffic": (round(TRAFFIC_RATIO[dom] * kstats[dom]["bytes"] / max(1, kstats[dom]["launches"]))
+                            if dom in TRAFFIC_RATIO else None),
+                "traffic_source": "ncu capture of two 1215^2 cells scaled to the launch's bytes",
                 "bytes_per_launch": kstats[dom]["bytes"] / max(1, kstats[dom]["launches"]),
                 "kernel_share": {k: round(v["ms"] / total_kms, 4) for k, v in kstats.items() if v["ms"] > 0},
                 "achieved_gbs": {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) for k, v in kstats.items()
