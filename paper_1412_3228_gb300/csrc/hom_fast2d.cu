@@ -38,7 +38,10 @@ namespace {
 #define HOM_GREEN_TW2 1  // Green pass with a scalar twiddle table (three CTAs per SM)
 #endif
 #ifndef HOM_ROW_TW2
-#define HOM_ROW_TW2 0    // row pass with a scalar twiddle table (three CTAs per SM; measured slower)
+#define HOM_ROW_TW2 1    // row pass with a scalar twiddle table (three CTAs per SM)
+#endif
+#ifndef HOM_ROW_U
+#define HOM_ROW_U (HOM_ROW_TW2 ? 1 : 4)  // row-pass load batch (items in flight per thread; 1 measured best at 80 registers)
 #endif
 #ifndef HOM_FAST_THREADS
 #define HOM_FAST_THREADS 256
@@ -331,7 +334,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
     // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component; item
     // (p, k) reads rows y0..y0+3 of pair p (U items per round: 4 U loads in flight per thread)
-    constexpr int U = 4;
+    constexpr int U = HOM_ROW_U;
     for (int f0 = threadIdx.x; f0 < P * NP; f0 += U * kT) {
       float4 v[U][kFastRows];
 #pragma unroll
