@@ -518,58 +518,58 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
 }
 
 // ------------------------------------------------------------------ control
-// One warp per (cell, load): FP64 compensated sums of the partials, equilibrium errors,
-// stopping rule.  The last block to finish counts the active pairs and advances the iteration.
-__global__ void __launch_bounds__(kThreads) k_control(SolveArgs A, int nc) {
+// One CTA per (cell, load): FP64 sums of the pair's partials (per-task partials of the row pass
+// and of the Green pass, summed in a fixed order: deterministic), equilibrium errors, stopping
+// rule.  The last CTA to finish counts the active pairs and advances the iteration.
+constexpr int kCtlThreads = 128;
+__global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
   __shared__ bool s_last;
-  __shared__ int s_cnt[kThreads / 32];
-  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+  __shared__ double s_red[kCtlThreads / 32][8];
+  __shared__ int s_cnt[kCtlThreads / 32];
+  const int pair = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int it = *A.it_dev;
-  if (warp < A.npairs && A.active[warp]) {
-    const PairDev pr = A.pairs[warp];
+  if (A.active[pair]) {
+    const PairDev pr = A.pairs[pair];
     const CellDev c = A.cells[pr.cell];
-    double sum[6], cmp[6];
-    for (int k = 0; k < 6; ++k) sum[k] = cmp[k] = 0.0;
-    for (int tk = c.rtask0 + lane; tk < c.rtask1; tk += 32) {
+    // v[0..nc): sigma sums, v[6]: residual sum, v[7]: normalised residual sum
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = 0.0;
+    for (int tk = c.rtask0 + (int)threadIdx.x; tk < c.rtask1; tk += kCtlThreads) {
       const double* p = A.partR + ((size_t)tk * A.L + pr.load) * nc;
-      for (int k = 0; k < nc; ++k) {
-        const double x = p[k];
-        const double tt = sum[k] + x;  // Neumaier
-        cmp[k] += fabs(sum[k]) >= fabs(x) ? (sum[k] - tt) + x : (x - tt) + sum[k];
-        sum[k] = tt;
+      for (int k = 0; k < nc; ++k) v[k] += p[k];
+    }
+    for (int tk = pr.ctask0 + (int)threadIdx.x; tk < pr.ctask1; tk += kCtlThreads) {
+      v[6] += A.partC[2 * (size_t)tk];
+      v[7] += A.partC[2 * (size_t)tk + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s_red[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum[8];
+      for (int k = 0; k < 8; ++k) {
+        sum[k] = 0.0;
+        for (int w = 0; w < kCtlThreads / 32; ++w) sum[k] += s_red[w][k];
       }
-    }
-    double r2 = 0.0, rn2 = 0.0;
-    for (int tk = pr.ctask0 + lane; tk < pr.ctask1; tk += 32) {
-      r2 += A.partC[2 * (size_t)tk];
-      rn2 += A.partC[2 * (size_t)tk + 1];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      for (int k = 0; k < nc; ++k) {
-        const double os = __shfl_down_sync(0xffffffffu, sum[k], o);
-        const double oc = __shfl_down_sync(0xffffffffu, cmp[k], o);
-        const double tt = sum[k] + os;
-        cmp[k] += (fabs(sum[k]) >= fabs(os) ? (sum[k] - tt) + os : (os - tt) + sum[k]) + oc;
-        sum[k] = tt;
-      }
-      r2 += __shfl_down_sync(0xffffffffu, r2, o);
-      rn2 += __shfl_down_sync(0xffffffffu, rn2, o);
-    }
-    if (lane == 0) {
       double den2 = 0.0;
       for (int k = 0; k < nc; ++k) {
-        const double tot = sum[k] + cmp[k];
-        A.mean_sigma[(size_t)warp * nc + k] = tot / (double)c.nv;
-        den2 += tot * tot;
+        A.mean_sigma[(size_t)pair * nc + k] = sum[k] / (double)c.nv;
+        den2 += sum[k] * sum[k];
       }
+      const double r2 = sum[6], rn2 = sum[7];
       double e, en;
       if (A.res0) {  // adjoint: relative to the first iterate's residual
         if (it == 0) {
-          A.res0[2 * warp] = r2;
-          A.res0[2 * warp + 1] = rn2;
+          A.res0[2 * pair] = r2;
+          A.res0[2 * pair + 1] = rn2;
         }
-        const double d0 = A.res0[2 * warp], d1 = A.res0[2 * warp + 1];
+        const double d0 = A.res0[2 * pair], d1 = A.res0[2 * pair + 1];
         e = d0 > 0.0 ? sqrt(r2 / d0) : 0.0;
         en = d1 > 0.0 ? sqrt(rn2 / d1) : 0.0;
       } else {
@@ -577,23 +577,23 @@ __global__ void __launch_bounds__(kThreads) k_control(SolveArgs A, int nc) {
         e = sqrt(r2) / den;
         en = sqrt(rn2) / den;
       }
-      A.err[warp] = e;
-      A.errn[warp] = en;
+      A.err[pair] = e;
+      A.errn[pair] = en;
       const double crit = A.criterion == HOM_CRIT_E ? e : en;
       int st = -1;
       if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
       else if (crit < A.tol) st = HOM_STATUS_CONVERGED;
       else if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
       else if (A.diverge_window > 0) {
-        int gcount = crit > A.last_err[warp] ? A.grow[warp] + 1 : 0;
-        A.grow[warp] = gcount;
+        int gcount = crit > A.last_err[pair] ? A.grow[pair] + 1 : 0;
+        A.grow[pair] = gcount;
         if (gcount >= A.diverge_window) st = HOM_STATUS_DIVERGED;
       }
-      A.last_err[warp] = crit;
+      A.last_err[pair] = crit;
       if (st >= 0) {
-        A.status[warp] = st;
-        A.iters[warp] = it;
-        A.active[warp] = 0;
+        A.status[pair] = st;
+        A.iters[pair] = it;
+        A.active[pair] = 0;
       }
     }
   }
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) k_control(SolveArgs A, int nc) {
     int cnt = 0;
     for (int p = threadIdx.x; p < A.npairs; p += blockDim.x) cnt += ((volatile int*)A.active)[p] ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    if (lane == 0) s_cnt[threadIdx.x >> 5] = cnt;
+    if (lane == 0) s_cnt[wid] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
       int tot = 0;
@@ -1063,7 +1063,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
   Timer tm{out->stats, st, {}};
   const unsigned nR = (unsigned)lay.tR.size(), nC = (unsigned)lay.tC.size(), nY = (unsigned)lay.tY.size();
-  const unsigned nCtl = (unsigned)((npairs * 32 + kThreads - 1) / kThreads);
+  const unsigned nCtl = (unsigned)npairs;  // one control CTA per (cell, load)
   tm.begin(HOM_K_INIT);
   k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
   if (lay.fast) {
@@ -1098,7 +1098,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
       tm.end();
     }
     tm.begin(HOM_K_CONTROL);
-    k_control<<<nCtl, kThreads, 0, st>>>(A, nc);
+    k_control<<<nCtl, kCtlThreads, 0, st>>>(A, nc);
     tm.end();
   };
   // Graphs are captured on a private stream (the legacy default stream cannot be captured) and
