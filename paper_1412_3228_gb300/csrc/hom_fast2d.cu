@@ -298,7 +298,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     int nal = 0;
     for (int l = 0; l < A.L; ++l) {
       const int cl = t.cell * A.L + l;
-      if (OUT || A.active[cl]) s_al[nal++] = l;
+      if ((t.load < 0 || l == t.load) && (OUT || A.active[cl])) s_al[nal++] = l;
     }
     s_nal = nal;
   }

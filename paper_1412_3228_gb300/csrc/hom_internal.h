@@ -110,13 +110,13 @@ struct CellDev {         // one cell of the solver
   double d_lam0, d_mu2, d_lpm, d_ratio, d_inv_mu0, d_inv_nv;
 };
 
-struct TaskR { int cell, row0, nrows, pad; };              // rows [row0, row0+nrows) x all loads
+struct TaskR { int cell, row0, nrows, load; };  // rows [row0, row0+nrows) x one load (load < 0: every load)
 struct TaskL {  // lines along one axis for a tile of kx: ntk columns x nc components
   int cell, load, kx0, ntk, fixed, pad;
   FastDiv d_ntk, d_nl, d_ng;  // dividers by ntk, ntk * nc and ntk * dim
 };
 
 // Per (cell, load) pair
-struct PairDev { int cell, load, ctask0, ctask1; };
+struct PairDev { int cell, load, ctask0, ctask1, rtask0, rtask1; };  // Green- and row-pass task ranges
 
 }  // namespace hom

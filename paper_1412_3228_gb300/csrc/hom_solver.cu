@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
     double v[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = 0.0;
-    for (int tk = c.rtask0 + (int)threadIdx.x; tk < c.rtask1; tk += kCtlThreads) {
+    for (int tk = pr.rtask0 + (int)threadIdx.x; tk < pr.rtask1; tk += kCtlThreads) {
       const double* p = A.partR + ((size_t)tk * A.L + pr.load) * nc;
       for (int k = 0; k < nc; ++k) v[k] += p[k];
     }
@@ -816,8 +816,26 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * (sizeof(long long) + 2 * vsize / 2);
     if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
     lay.smem_row = std::max(lay.smem_row, need_r);
+    // row tasks: every load per task (generic passes), or one load per task (specialised passes:
+    // finer tasks, and tasks of finished loads exit at once), load-major within the cell
     c.rtask0 = (int)lay.tR.size();
-    for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), 0});
+    std::vector<int> rt0(L, c.rtask0), rt1(L, c.rtask0);
+    // HOM_ROW_PER_LOAD=1: one load per task (measured 3 % slower on the 2D sweep than every load
+    // per task, which shares labels and twiddles across the loads)
+    static const bool per_load = [] {
+      const char* e = std::getenv("HOM_ROW_PER_LOAD");
+      return e && e[0] == '1';
+    }();
+    if (lay.fast && per_load) {
+      for (int l = 0; l < L; ++l) {
+        rt0[l] = (int)lay.tR.size();
+        for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), l});
+        rt1[l] = (int)lay.tR.size();
+      }
+    } else {
+      for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), -1});
+      for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
+    }
     c.rtask1 = (int)lay.tR.size();
     // Green-pass and y-pass tiles of kx
     // Green/y tiles: ntk kx columns x nc lines, plus the twiddle table and the wave-number table
@@ -829,7 +847,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     lay.smem_green = std::max(lay.smem_green, need_l);
     lay.smem_y = std::max(lay.smem_y, need_l);
     for (int l = 0; l < L; ++l) {
-      PairDev pd{ci, l, (int)lay.tC.size(), 0};
+      PairDev pd{ci, l, (int)lay.tC.size(), 0, rt0[l], rt1[l]};
       const int nfix = dim == 2 ? 1 : k.n;
       for (int f = 0; f < nfix; ++f)
         for (int kx0 = 0; kx0 < c.H; kx0 += ntk) lay.tC.push_back(make_task(ci, l, kx0, std::min(ntk, c.H - kx0), f, nc, dim));
