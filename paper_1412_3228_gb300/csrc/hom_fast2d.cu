@@ -323,11 +323,18 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
 #if HOM_ROW_TW2
   float2* tws = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16);
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+  float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + (N + 1) / 2);
 #else
   float4* tws = s + N * NP + kFastRows * NL / 16;
   for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
+  float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + N);
 #endif
   cp_commit();
+  // per phase (lam - lam0, 2 mu - 2 mu0) for the pure-voxel update (visible after the next barrier)
+  for (int i = threadIdx.x; i < A.nphase; i += kT) {
+    const float lam = __ldg(A.phase_c32 + (size_t)i * 6 + 1);
+    sph[i] = make_float2(lam - lam0, (__ldg(A.phase_c32 + (size_t)i * 6) - lam) - mu2_0);
+  }
 
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
@@ -401,10 +408,9 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
         float dl[kFastRows], dm[kFastRows];
 #pragma unroll
         for (int r = 0; r < kFastRows; ++r) {
-          const float* pc = A.phase_c32 + (size_t)lab[r] * 6;
-          const float lam = __ldg(pc + 1);
-          dl[r] = lam - lam0;
-          dm[r] = (__ldg(pc) - lam) - mu2_0;
+          const float2 d = sph[lab[r]];
+          dl[r] = d.x;
+          dm[r] = d.y;
         }
         const float2 dl_lo = make_float2(dl[0], dl[2]), dl_hi = make_float2(dl[1], dl[3]);
         const float2 dm_lo = make_float2(dm[0], dm[2]), dm_hi = make_float2(dm[1], dm[3]);
@@ -850,11 +856,11 @@ void fast2d_release() {
 }
 
 // row: tile | labels of 4 rows | twiddles;  Green: tile | twiddles | wave numbers
-// row: tile | one-byte labels of 4 rows | twiddles
-size_t fast2d_smem_row(int nmax) {
+// row: tile | one-byte labels of 4 rows | twiddles | per-phase update constants
+size_t fast2d_smem_row(int nmax, int nphase) {
   const size_t labels = (size_t)kFastRows * ((nmax + 15) / 16 * 16);
   const size_t tw = HOM_ROW_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
-  return (size_t)nmax * NP * sizeof(float4) + labels + tw;
+  return (size_t)nmax * NP * sizeof(float4) + labels + tw + ((size_t)nphase * 8 + 15) / 16 * 16;
 }
 size_t fast2d_smem_green(int nmax) {
   const size_t tw = HOM_GREEN_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);

@@ -30,7 +30,7 @@ bool fast2d_size(int n);
 // Device tables of size n (built and uploaded on first use, kept until hom_release).
 int fast2d_plan(int n, FastPlanDev* out);
 // Dynamic shared memory of the row and Green passes for the largest grid size n of a call.
-size_t fast2d_smem_row(int nmax);
+size_t fast2d_smem_row(int nmax, int nphase);
 size_t fast2d_smem_green(int nmax);
 // Launches (one CTA per task); `smem` from fast2d_smem_row / fast2d_smem_green.
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);

@@ -53,6 +53,7 @@ struct SolveArgs {
   double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
   const uint8_t* label8;      // specialised row pass: phase (255: mixed) with x in transform order
+  int nphase;                 // entries of the phase tables
 };
 
 // Kahan-compensated accumulation in the field precision: the running sum s and the negated

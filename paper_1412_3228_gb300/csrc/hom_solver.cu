@@ -1067,7 +1067,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
-  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax) : 0;
+  A.nphase = mat->nphase;
+  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax, mat->nphase) : 0;
   const size_t smem_fgreen = lay.fast ? fast2d_smem_green(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
