@@ -330,10 +330,11 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
   float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + N);
 #endif
   cp_commit();
-  // per phase (lam - lam0, 2 mu - 2 mu0) for the pure-voxel update (visible after the next barrier)
-  for (int i = threadIdx.x; i < A.nphase; i += kT) {
-    const float lam = __ldg(A.phase_c32 + (size_t)i * 6 + 1);
-    sph[i] = make_float2(lam - lam0, (__ldg(A.phase_c32 + (size_t)i * 6) - lam) - mu2_0);
+  // per local phase (lam - lam0, 2 mu - 2 mu0) for the pure-voxel update (visible after the next barrier)
+  for (int i = threadIdx.x; i < c.nph; i += kT) {
+    const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 6;
+    const float lam = __ldg(pc + 1);
+    sph[i] = make_float2(lam - lam0, (__ldg(pc) - lam) - mu2_0);
   }
 
   for (int la = 0; la < nal; ++la) {
@@ -384,7 +385,8 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     fft_dif_p<N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3).  A one-byte
-    // label is the phase of a pure voxel, or kLabel8Mixed (full label read from the material).
+    // label is the local phase index of a pure voxel, or kLabel8Mixed (full label read from the
+    // material, which also covers any voxel whose phase is not in the cell's list).
     for (int pos = threadIdx.x; pos < N; pos += kT) {
       uint32_t lab[kFastRows];
       bool mixed = false;
@@ -393,11 +395,12 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
         lab[r] = r < nr ? (uint32_t)slab[r * NL + pos] : 0u;
         mixed |= lab[r] == kLabel8Mixed;
       }
-      if (mixed) {
+      if (mixed) {  // full labels: the material's for mixed voxels, global phases for the others
         const int x = __ldg(fp.iperm + pos);
 #pragma unroll
         for (int r = 0; r < kFastRows; ++r)
-          if (lab[r] == kLabel8Mixed) lab[r] = __ldg(A.label + c.vox_off + (size_t)(y0 + r) * N + x);
+          lab[r] = lab[r] == kLabel8Mixed ? __ldg(A.label + c.vox_off + (size_t)(y0 + r) * N + x)
+                                          : (uint32_t)__ldg(A.cell_phases + c.ph_off + lab[r]);
       }
       float4 e[NP];
 #pragma unroll
@@ -473,8 +476,8 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
         for (int k = 0; k < NP; ++k) s[pos * NP + k] = o[k];
       }
     }
+    __syncthreads();  // the tile is read above and rewritten below (or by the next load's fill)
     if (OUT) continue;
-    __syncthreads();
     fft_dit_p<N, true>(s, tws);  // forward: natural order
 
     // 3. split the two real rows of each line; store the half spectra of tau, pair by pair
@@ -754,8 +757,15 @@ __global__ void k_permute_labels(SolveArgs A, int ncells) {
     const int pos = (int)(i - y * c.n);
     const uint32_t lab = A.label[c.vox_off + y * c.n + fp.iperm[pos]];
     const int nl = (c.n + 15) / 16 * 16;
-    const_cast<uint8_t*>(A.label8)[c.lp_off + y * nl + pos] =
-        (lab & HOM_MIXED_BIT) ? (uint8_t)kLabel8Mixed : (uint8_t)lab;
+    // local index of a pure voxel's phase in the cell's list (not found: the full-label path)
+    uint32_t loc = kLabel8Mixed;
+    if (!(lab & HOM_MIXED_BIT))
+      for (int j = 0; j < c.nph; ++j)
+        if ((uint32_t)A.cell_phases[c.ph_off + j] == lab) {
+          loc = (uint32_t)j;
+          break;
+        }
+    const_cast<uint8_t*>(A.label8)[c.lp_off + y * nl + pos] = (uint8_t)loc;
   }
 }
 
@@ -857,10 +867,10 @@ void fast2d_release() {
 
 // row: tile | labels of 4 rows | twiddles;  Green: tile | twiddles | wave numbers
 // row: tile | one-byte labels of 4 rows | twiddles | per-phase update constants
-size_t fast2d_smem_row(int nmax, int nphase) {
+size_t fast2d_smem_row(int nmax, int nphase_cell) {
   const size_t labels = (size_t)kFastRows * ((nmax + 15) / 16 * 16);
   const size_t tw = HOM_ROW_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
-  return (size_t)nmax * NP * sizeof(float4) + labels + tw + ((size_t)nphase * 8 + 15) / 16 * 16;
+  return (size_t)nmax * NP * sizeof(float4) + labels + tw + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
 }
 size_t fast2d_smem_green(int nmax) {
   const size_t tw = HOM_GREEN_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);

@@ -30,7 +30,7 @@ bool fast2d_size(int n);
 // Device tables of size n (built and uploaded on first use, kept until hom_release).
 int fast2d_plan(int n, FastPlanDev* out);
 // Dynamic shared memory of the row and Green passes for the largest grid size n of a call.
-size_t fast2d_smem_row(int nmax, int nphase);
+size_t fast2d_smem_row(int nmax, int nphase_cell);
 size_t fast2d_smem_green(int nmax);
 // Launches (one CTA per task); `smem` from fast2d_smem_row / fast2d_smem_green.
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
@@ -39,8 +39,8 @@ int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t 
 // the specialised passes (see hom_fast2d.cu).
 int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
 int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st);
-// label8[lp_off + y nl + pos] = phase of label[vox_off + y n + iperm[pos]] (255 for a mixed voxel,
-// nl = n rounded up to 16) for every specialised cell; requires fewer than 255 phases.
+// label8[lp_off + y nl + pos] = index, in the cell's list of pure phases, of the phase of
+// label[vox_off + y n + iperm[pos]] (255 for a mixed voxel; nl = n rounded up to 16).
 int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
 void fast2d_release();
 

@@ -105,6 +105,7 @@ struct CellDev {         // one cell of the solver
   int rtask0, rtask1;    // row-pass task range
   int fplan;             // specialised passes: index of the size's tables (-1: generic passes)
   long long lp_off;      // specialised passes: byte offset of the cell in the one-byte labels (16-aligned)
+  int ph_off, nph;       // specialised passes: the cell's pure phases, cell_phases[ph_off .. ph_off + nph)
   // per-cell constants, computed on the host (FP64 arithmetic is slow on the device)
   float f_lam0, f_mu2, f_lpm, f_ratio, f_inv_mu0, f_inv_nv;
   double d_lam0, d_mu2, d_lpm, d_ratio, d_inv_mu0, d_inv_nv;

@@ -52,8 +52,8 @@ struct SolveArgs {
   const void* src;  // adjoint source S (nullptr for the forward solve)
   double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
-  const uint8_t* label8;      // specialised row pass: phase (255: mixed) with x in transform order
-  int nphase;                 // entries of the phase tables
+  const uint8_t* label8;      // specialised row pass: local phase index (255: mixed), x in transform order
+  const int* cell_phases;     // specialised row pass: per-cell lists of the phases of pure voxels
 };
 
 // Kahan-compensated accumulation in the field precision: the running sum s and the negated

@@ -933,8 +933,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   Layout lay;
   {
     const char* fe = std::getenv("HOM_FAST2D");
-    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && mat->nphase < 255 &&
-               !(fe && fe[0] == '0');
+    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && !(fe && fe[0] == '0');
   }
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
@@ -970,6 +969,23 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     nv_max = std::max(nv_max, c.nv);
   }
   const size_t o_lperm = lay.fast ? take((size_t)nv_all) : 0;
+  // pure-voxel phases of each cell: the matrix phase and its primitives' phases (one-byte local index)
+  std::vector<int> cell_phases;
+  int nph_max = 1;
+  if (lay.fast) {
+    for (int ci = 0; ci < ncells; ++ci) {
+      std::vector<int> ph{cells[ci].matrix_phase};
+      for (int p = 0; p < cells[ci].nprim; ++p) ph.push_back(cells[ci].prims[p].phase);
+      std::sort(ph.begin(), ph.end());
+      ph.erase(std::unique(ph.begin(), ph.end()), ph.end());
+      if (ph.size() > 254) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "cell %d holds more than 254 phases", ci);
+      lay.cells[ci].ph_off = (int)cell_phases.size();
+      lay.cells[ci].nph = (int)ph.size();
+      nph_max = std::max(nph_max, (int)ph.size());
+      cell_phases.insert(cell_phases.end(), ph.begin(), ph.end());
+    }
+  }
+  const size_t o_cphase = lay.fast ? take(cell_phases.size() * sizeof(int)) : 0;
   const size_t o_fplans = lay.fast ? take(lay.fplans.size() * sizeof(FastPlanDev)) : 0;
   const size_t o_stage_e = need_stage && out->eps && !eps_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
@@ -1014,6 +1030,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemcpyAsync(ws + host_lo, h.data(), h.size(), cudaMemcpyHostToDevice, st));
     if (lay.fast) {
       HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_fplans, lay.fplans.data(), lay.fplans.size() * sizeof(FastPlanDev),
+                                   cudaMemcpyHostToDevice, st));
+      HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_cphase, cell_phases.data(), cell_phases.size() * sizeof(int),
                                    cudaMemcpyHostToDevice, st));
       HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the staging vector goes out of scope
     }
@@ -1067,8 +1085,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
-  A.nphase = mat->nphase;
-  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax, mat->nphase) : 0;
+  A.cell_phases = lay.fast ? reinterpret_cast<const int*>(ws + o_cphase) : nullptr;
+  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax, nph_max) : 0;
   const size_t smem_fgreen = lay.fast ? fast2d_smem_green(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
