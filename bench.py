@@ -367,7 +367,8 @@ def spheres_3d(hom, dev, n=243):
     kb = {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) for k, v in r["stats"].items() if v["ms"] > 0 and v["bytes"] > 0}
     return {"value": vi / (ms / 1e3), "unit": UNIT, "solve_ms": round(ms, 2), "filter_build_ms": round(filt_ms, 2),
             "iterations": [int(i) for i in r["iterations"][0]], "spheres": len(cell.prims),
-            "mixed_voxels": int(mat.mixed_count), "achieved_gbs": kb, "passes": "generic (4 passes per iteration)"}
+            "mixed_voxels": int(mat.mixed_count), "achieved_gbs": kb,
+            "passes": "specialised FP32 3D (row, y forward, Green along z, y inverse)"}
 
 
 def ensemble_2d(hom, dev, count=256):

@@ -30,6 +30,7 @@
 #include "hom_fast2d.h"
 #include "hom_plan.h"
 #include "hom_solve_args.cuh"
+#include "hom_fastfft.cuh"
 
 namespace hom {
 namespace {
@@ -43,228 +44,8 @@ namespace {
 #ifndef HOM_ROW_U
 #define HOM_ROW_U (HOM_ROW_TW2 ? 1 : 4)  // row-pass load batch (items in flight per thread; 1 measured best at 80 registers)
 #endif
-#ifndef HOM_FAST_THREADS
-#define HOM_FAST_THREADS 256
-#endif
-constexpr int kT = HOM_FAST_THREADS;  // threads per CTA (a build-time tunable)
-constexpr int NP = 3;    // lane pairs per position (2D Mandel components)
-
-// ------------------------------------------------------------------ packed FP32x2 arithmetic
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b as b * (-1) + a: one rounding, the same result as a subtraction
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-
-// 16-byte asynchronous global -> shared copies (completed by cp_wait_all + a barrier).
-__device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Two complex numbers, one per line: re = (re_A, re_B), im = (im_A, im_B).
-struct P2 {
-  float2 re, im;
-};
-__device__ __forceinline__ P2 ldp(const float4& v) { return P2{make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
-__device__ __forceinline__ float4 stp(const P2& p) { return make_float4(p.re.x, p.re.y, p.im.x, p.im.y); }
-__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2{add2(a.re, b.re), add2(a.im, b.im)}; }
-__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
-__device__ __forceinline__ P2 scale(float s, P2 a) { return P2{mul2(f2(s), a.re), mul2(f2(s), a.im)}; }
-// a * w (FWD) or a * conj(w) with w4 = (wr, wr, wi, wi)
-template <bool FWD>
-__device__ __forceinline__ P2 twmul(P2 a, float4 w4) {
-  const float2 wr = make_float2(w4.x, w4.y), wi = make_float2(w4.z, w4.w);
-  if (FWD) return P2{sub2(mul2(a.re, wr), mul2(a.im, wi)), fma2(a.re, wi, mul2(a.im, wr))};
-  return P2{fma2(a.im, wi, mul2(a.re, wr)), sub2(mul2(a.im, wr), mul2(a.re, wi))};
-}
-
-// a * w (FWD) or a * conj(w) with a scalar twiddle w = (wr, wi), broadcast to both lanes
-template <bool FWD>
-__device__ __forceinline__ P2 twmul(P2 a, float2 w) {
-  return twmul<FWD>(a, make_float4(w.x, w.x, w.y, w.y));
-}
-
-// ------------------------------------------------------------------ butterfly constants
-// Every constant the register DFTs multiply by, duplicated into a lane pair, in constant memory:
-// the packed instructions can take such an operand without a register copy.
-#define HOM_TWP(R, m)                                                                              \
-  {(float)tw_cos(R, m), (float)tw_cos(R, m)}, {(float)tw_sin(R, m), (float)tw_sin(R, m)},          \
-      {(float)-tw_sin(R, m), (float)-tw_sin(R, m)}
-constexpr float kH3 = 0.866025403784438646763723170753f;  // sin(2 pi / 3)
-constexpr float kC51 = 0.309016994374947424102293417183f, kC52 = -0.809016994374947424102293417183f;
-constexpr float kS51 = 0.951056516295153572116439333379f, kS52 = 0.587785252292473129168705954639f;
-enum { KMH = 0, KH3, KNH3, KC51, KC52, KS51, KS52, KNS51, KNS52, KTW9 };
-constexpr int kTw15 = KTW9 + 27;
-__constant__ float2 kP[kTw15 + 45] = {
-    {-0.5f, -0.5f}, {kH3, kH3}, {-kH3, -kH3}, {kC51, kC51}, {kC52, kC52}, {kS51, kS51}, {kS52, kS52}, {-kS51, -kS51},
-    {-kS52, -kS52},
-    HOM_TWP(9, 0), HOM_TWP(9, 1), HOM_TWP(9, 2), HOM_TWP(9, 3), HOM_TWP(9, 4), HOM_TWP(9, 5), HOM_TWP(9, 6),
-    HOM_TWP(9, 7), HOM_TWP(9, 8),
-    HOM_TWP(15, 0), HOM_TWP(15, 1), HOM_TWP(15, 2), HOM_TWP(15, 3), HOM_TWP(15, 4), HOM_TWP(15, 5), HOM_TWP(15, 6),
-    HOM_TWP(15, 7), HOM_TWP(15, 8), HOM_TWP(15, 9), HOM_TWP(15, 10), HOM_TWP(15, 11), HOM_TWP(15, 12),
-    HOM_TWP(15, 13), HOM_TWP(15, 14)};
-#undef HOM_TWP
-template <int R> __device__ __forceinline__ constexpr int tw_base() { return R == 9 ? KTW9 : kTw15; }
-
-// ------------------------------------------------------------------ register DFTs on lane pairs
-// Forward transforms use w = exp(-2 pi i / r), inverse ones conj(w); no scaling.  Composite sizes
-// leave X[k] in v[out_pos<R>(k)] (hom_common.cuh).
-template <bool FWD>
-__device__ __forceinline__ void dft3p(P2* v) {
-  const P2 s = v[1] + v[2];
-  const P2 d = v[1] - v[2];
-  const P2 m{fma2(s.re, kP[KMH], v[0].re), fma2(s.im, kP[KMH], v[0].im)};
-  v[0] = v[0] + s;
-  // v1 = m - i hf d, v2 = m + i hf d with hf = +-sin(2 pi / 3)
-  const float2 hp = kP[FWD ? KH3 : KNH3], hn = kP[FWD ? KNH3 : KH3];
-  v[1] = P2{fma2(d.im, hp, m.re), fma2(d.re, hn, m.im)};
-  v[2] = P2{fma2(d.im, hn, m.re), fma2(d.re, hp, m.im)};
-}
-
-template <bool FWD>
-__device__ __forceinline__ void dft5p(P2* v) {
-  const P2 a1 = v[1] + v[4], b1 = v[1] - v[4];
-  const P2 a2 = v[2] + v[3], b2 = v[2] - v[3];
-  const float2 c1 = kP[KC51], c2 = kP[KC52];
-  const P2 r1{fma2(a2.re, c2, fma2(a1.re, c1, v[0].re)), fma2(a2.im, c2, fma2(a1.im, c1, v[0].im))};
-  const P2 r2{fma2(a2.re, c1, fma2(a1.re, c2, v[0].re)), fma2(a2.im, c1, fma2(a1.im, c2, v[0].im))};
-  // t1 = +-s1, t2 = +-s2: i1 = t1 b1 + t2 b2, i2 = t2 b1 - t1 b2
-  const float2 t1 = kP[FWD ? KS51 : KNS51], t2 = kP[FWD ? KS52 : KNS52], nt1 = kP[FWD ? KNS51 : KS51];
-  const P2 i1{fma2(b2.re, t2, mul2(b1.re, t1)), fma2(b2.im, t2, mul2(b1.im, t1))};
-  const P2 i2{fma2(b2.re, nt1, mul2(b1.re, t2)), fma2(b2.im, nt1, mul2(b1.im, t2))};
-  v[0] = v[0] + a1 + a2;
-  // X1 = r1 - i i1, X4 = r1 + i i1, X2 = r2 - i i2, X3 = r2 + i i2
-  v[1] = P2{add2(r1.re, i1.im), sub2(r1.im, i1.re)};
-  v[4] = P2{sub2(r1.re, i1.im), add2(r1.im, i1.re)};
-  v[2] = P2{add2(r2.re, i2.im), sub2(r2.im, i2.re)};
-  v[3] = P2{sub2(r2.re, i2.im), add2(r2.im, i2.re)};
-}
-
-template <int R, bool FWD> __device__ __forceinline__ void dftp(P2* v);
-
-// R = A * B inside the registers: X[ka + A kb] = sum_nb w_B^(nb kb) [w_R^(nb ka) sum_na x[B na + nb] w_A^(na ka)]
-template <int A, int B, bool FWD>
-__device__ __forceinline__ void dft_compositep(P2* v) {
-  constexpr int R = A * B;
-#pragma unroll
-  for (int nb = 0; nb < B; ++nb) {
-    P2 t[A];
-#pragma unroll
-    for (int na = 0; na < A; ++na) t[na] = v[B * na + nb];
-    dftp<A, FWD>(t);
-#pragma unroll
-    for (int ka = 0; ka < A; ++ka) {
-      const P2 x = t[out_pos<A>(ka)];
-      const int m = (nb * ka) % R;
-      if (m == 0) {
-        v[B * ka + nb] = x;
-      } else {
-        // x (cos + i sn), sn = -+sin(2 pi m / R)
-        const int b = tw_base<R>() + 3 * m;
-        const float2 c = kP[b], sp = kP[b + 1], sm = kP[b + 2];
-        const float2 sn = FWD ? sm : sp, nsn = FWD ? sp : sm;
-        v[B * ka + nb] = P2{fma2(x.im, nsn, mul2(x.re, c)), fma2(x.im, c, mul2(x.re, sn))};
-      }
-    }
-  }
-#pragma unroll
-  for (int ka = 0; ka < A; ++ka) dftp<B, FWD>(v + B * ka);
-}
-
-template <int R, bool FWD>
-__device__ __forceinline__ void dftp(P2* v) {
-  if constexpr (R == 3) dft3p<FWD>(v);
-  else if constexpr (R == 5) dft5p<FWD>(v);
-  else dft_compositep<split_a<R>(), R / split_a<R>(), FWD>(v);
-}
-
-// ------------------------------------------------------------------ compile-time plans
-// Radices in DIT order; registers bound the radix at 15 (15 lane pairs = 60 floats).
-template <int N> struct Radix;
-template <> struct Radix<45> { static constexpr int m = 2, r0 = 5, r1 = 9, r2 = 1; };
-template <> struct Radix<75> { static constexpr int m = 2, r0 = 5, r1 = 15, r2 = 1; };
-template <> struct Radix<135> { static constexpr int m = 2, r0 = 15, r1 = 9, r2 = 1; };
-template <> struct Radix<225> { static constexpr int m = 2, r0 = 15, r1 = 15, r2 = 1; };
-template <> struct Radix<405> { static constexpr int m = 3, r0 = 5, r1 = 9, r2 = 9; };
-template <> struct Radix<1215> { static constexpr int m = 3, r0 = 15, r1 = 9, r2 = 9; };
-constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};
-
-// One stage over the NP pairs of every position; thread t takes the butterflies t, t + kT, ...
-// (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
-// Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
-// (q = 1..R-1, j < L): neighbouring threads read neighbouring entries.
-template <int N, int R, int L, bool FWD, bool DIT, typename TW>
-__device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
-  constexpr int NB = N / R, B = L * R;
-  for (int t = threadIdx.x; t < NB * NP; t += kT) {
-    const int cc = t / NB;
-    const int b = t - cc * NB;
-    const int blk = b / L;
-    const int j = b - blk * L;
-    float4* base = s + (blk * B + j) * NP + cc;
-    P2 v[R];
-    if (DIT) {
-      v[0] = ldp(base[0]);
-#pragma unroll
-      for (int q = 1; q < R; ++q) {
-        P2 x = ldp(base[q * L * NP]);
-        if (L > 1) x = twmul<FWD>(x, tw[(q - 1) * L + j]);
-        v[q] = x;
-      }
-      dftp<R, FWD>(v);
-#pragma unroll
-      for (int p = 0; p < R; ++p) base[p * L * NP] = stp(v[out_pos<R>(p)]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < R; ++q) v[q] = ldp(base[q * L * NP]);
-      dftp<R, FWD>(v);
-      base[0] = stp(v[0]);
-#pragma unroll
-      for (int p = 1; p < R; ++p) {
-        P2 x = v[out_pos<R>(p)];
-        if (L > 1) x = twmul<FWD>(x, tw[(p - 1) * L + j]);
-        base[p * L * NP] = stp(x);
-      }
-    }
-  }
-}
-
-// Stage tables are stored back to back: stage 1 (span r0) first, then stage 2 (span r0 r1).
-template <int N, bool FWD, typename TW>
-__device__ __forceinline__ void fft_dit_p(float4* s, const TW* tw) {
-  using P = Radix<N>;
-  constexpr int off2 = P::r0 * (P::r1 - 1);
-  stage_p<N, P::r0, 1, FWD, true>(s, tw);
-  __syncthreads();
-  if constexpr (P::m > 1) {
-    stage_p<N, P::r1, P::r0, FWD, true>(s, tw);
-    __syncthreads();
-  }
-  if constexpr (P::m > 2) {
-    stage_p<N, P::r2, P::r0 * P::r1, FWD, true>(s, tw + off2);
-    __syncthreads();
-  }
-}
-
-template <int N, bool FWD, typename TW>
-__device__ __forceinline__ void fft_dif_p(float4* s, const TW* tw) {
-  using P = Radix<N>;
-  constexpr int off2 = P::r0 * (P::r1 - 1);
-  if constexpr (P::m > 2) {
-    stage_p<N, P::r2, P::r0 * P::r1, FWD, false>(s, tw + off2);
-    __syncthreads();
-  }
-  if constexpr (P::m > 1) {
-    stage_p<N, P::r1, P::r0, FWD, false>(s, tw);
-    __syncthreads();
-  }
-  stage_p<N, P::r0, 1, FWD, false>(s, tw);
-  __syncthreads();
-}
+constexpr int NP = 3;  // lane pairs per position (2D Mandel components)
+constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};  // sizes with specialised 2D passes
 
 // ------------------------------------------------------------------ state layout
 // The mixed-domain state of a cell (eps buffers and tau) is tiled by kx pairs: for load l, pair
@@ -382,7 +163,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     }
     cp_wait_all();
     __syncthreads();
-    fft_dif_p<N, false>(s, tws);  // inverse: eps at digit-reversed positions
+    fft_dif_p<NP, N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3).  A one-byte
     // label is the local phase index of a pure voxel, or kLabel8Mixed (full label read from the
@@ -478,7 +259,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
     }
     __syncthreads();  // the tile is read above and rewritten below (or by the next load's fill)
     if (OUT) continue;
-    fft_dit_p<N, true>(s, tws);  // forward: natural order
+    fft_dit_p<NP, N, true>(s, tws);  // forward: natural order
 
     // 3. split the two real rows of each line; store the half spectra of tau, pair by pair
     for (int f = threadIdx.x; f < P * NP; f += kT) {
@@ -611,7 +392,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   cp_commit();
   cp_wait_all();
   __syncthreads();
-  fft_dif_p<N, true>(s, tws);  // forward: bin ky at position perm(ky)
+  fft_dif_p<NP, N, true>(s, tws);  // forward: bin ky at position perm(ky)
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -718,7 +499,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
     }
   }
-  fft_dit_p<N, false>(s, tws);  // inverse: natural order
+  fft_dit_p<NP, N, false>(s, tws);  // inverse: natural order
   for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
   if (threadIdx.x == 0) {
     const int ntk = hasB ? 2 : 1;
@@ -751,7 +532,7 @@ __global__ void k_permute_labels(SolveArgs A, int ncells) {
   const CellDev c = A.cells[ci];
   if (c.fplan < 0) return;
   const FastPlanDev fp = A.fplans[c.fplan];
-  const long long nv = (long long)c.n * c.n;
+  const long long nv = c.nv;  // rows x n (rows are y in 2D, z n + y in 3D)
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
     const long long y = i / c.n;
     const int pos = (int)(i - y * c.n);
@@ -786,6 +567,9 @@ std::vector<int> radices_of(int n) {
     case 225: return {Radix<225>::r0, Radix<225>::r1};
     case 405: return {Radix<405>::r0, Radix<405>::r1, Radix<405>::r2};
     case 1215: return {Radix<1215>::r0, Radix<1215>::r1, Radix<1215>::r2};
+    case 27: return {Radix<27>::r0, Radix<27>::r1};
+    case 81: return {Radix<81>::r0, Radix<81>::r1};
+    case 243: return {Radix<243>::r0, Radix<243>::r1, Radix<243>::r2};
     default: return {};
   }
 }
@@ -808,7 +592,7 @@ int fast2d_plan(int n, FastPlanDev* out) {
       return HOM_OK;
     }
   HostPlan hp;
-  if (!fast2d_size(n) || !build_host_plan_radices(n, radices_of(n), hp))
+  if (radices_of(n).empty() || !build_host_plan_radices(n, radices_of(n), hp))
     return set_error(HOM_ERR_UNSUPPORTED_SIZE, "no specialised plan for n = %d", n);
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4),

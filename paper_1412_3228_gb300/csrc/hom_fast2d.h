@@ -25,9 +25,11 @@ struct FastPlanDev {
 constexpr int kFastRows = 4;  // real rows per row-pass task (two complex lines, one lane pair)
 constexpr int kFastCols = 2;  // kx columns per Green-pass task (one lane pair)
 
-// True if n has a specialised plan.
+// True if n has specialised 2D / 3D passes.
 bool fast2d_size(int n);
-// Device tables of size n (built and uploaded on first use, kept until hom_release).
+bool fast3d_size(int n);
+// Device tables of size n (built and uploaded on first use, kept until hom_release); every size
+// of fast2d_size or fast3d_size has one.
 int fast2d_plan(int n, FastPlanDev* out);
 // Dynamic shared memory of the row and Green passes for the largest grid size n of a call.
 size_t fast2d_smem_row(int nmax, int nphase_cell);
@@ -43,5 +45,15 @@ int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st);
 // label[vox_off + y n + iperm[pos]] (255 for a mixed voxel; nl = n rounded up to 16).
 int fast2d_permute_labels(const SolveArgs& A, int ncells, long long max_nv, cudaStream_t st);
 void fast2d_release();
+
+// Specialised 3D passes (hom_fast3d.cu): row, y forward / inverse, Green (z lines), the initial
+// state eps = E and the output pass, on the kx-pair tiled state of those passes.
+size_t fast3d_smem_row(int nmax, int nphase_cell);
+size_t fast3d_smem_y(int nmax);
+size_t fast3d_smem_green(int nmax);
+int fast3d_row(const SolveArgs& A, unsigned ntasks, size_t smem, bool out, cudaStream_t st);
+int fast3d_ypass(const SolveArgs& A, unsigned ntasks, size_t smem, bool fwd, cudaStream_t st);
+int fast3d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st);
+int fast3d_init(const SolveArgs& A, int ncells, cudaStream_t st);
 
 }  // namespace hom

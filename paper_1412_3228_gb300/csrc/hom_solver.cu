@@ -724,12 +724,8 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
   // The specialised passes take 4-row and 2-column tasks; the output pass (generic row kernel)
   // then needs 4 rows of every load on chip.
   if (lay.fast) {
-    for (int ci = 0; ci < ncells; ++ci) {
-      const size_t lines = (size_t)((kFastRows * L * nc + 1) / 2) + 1;
-      if (!fast2d_size(cells[ci].n) ||
-          lines * cells[ci].n * vsize + (size_t)kFastRows * L * nc * (sizeof(long long) + vsize) > kMaxSmem)
-        lay.fast = false;
-    }
+    for (int ci = 0; ci < ncells; ++ci)
+      if (!(dim == 2 ? fast2d_size(cells[ci].n) : fast3d_size(cells[ci].n))) lay.fast = false;
   }
   long long vox = 0;
   std::vector<int> plan_n;
@@ -826,7 +822,11 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
       const char* e = std::getenv("HOM_ROW_PER_LOAD");
       return e && e[0] == '1';
     }();
-    if (lay.fast && per_load) {
+    if (lay.fast && dim == 3) {  // groups of 4 rows (consecutive y) within each z plane
+      for (int z = 0; z < k.n; ++z)
+        for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), -1});
+      for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
+    } else if (lay.fast && per_load) {
       for (int l = 0; l < L; ++l) {
         rt0[l] = (int)lay.tR.size();
         for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), l});
@@ -933,7 +933,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   Layout lay;
   {
     const char* fe = std::getenv("HOM_FAST2D");
-    lay.fast = std::is_same<T, float>::value && DIM == 2 && !ext && !adj && !(fe && fe[0] == '0');
+    // HOM_FAST2D=0: generic passes everywhere; HOM_FAST2D=2: generic passes for 3D only
+    lay.fast = std::is_same<T, float>::value && !ext && !adj && !(fe && fe[0] == '0') &&
+               !(DIM == 3 && fe && fe[0] == '2');
   }
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
@@ -1086,8 +1088,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
   A.cell_phases = lay.fast ? reinterpret_cast<const int*>(ws + o_cphase) : nullptr;
-  const size_t smem_frow = lay.fast ? fast2d_smem_row(lay.fast_nmax, nph_max) : 0;
-  const size_t smem_fgreen = lay.fast ? fast2d_smem_green(lay.fast_nmax) : 0;
+  const size_t smem_frow =
+      !lay.fast ? 0 : DIM == 2 ? fast2d_smem_row(lay.fast_nmax, nph_max) : fast3d_smem_row(lay.fast_nmax, nph_max);
+  const size_t smem_fgreen =
+      !lay.fast ? 0 : DIM == 2 ? fast2d_smem_green(lay.fast_nmax) : fast3d_smem_green(lay.fast_nmax);
+  const size_t smem_fy = lay.fast && DIM == 3 ? fast3d_smem_y(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
   if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
@@ -1103,7 +1108,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const unsigned nCtl = (unsigned)npairs;  // one control CTA per (cell, load)
   tm.begin(HOM_K_INIT);
   k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
-  if (lay.fast) {
+  if (lay.fast && DIM == 3) {
+    fast3d_init(A, ncells, st);
+  } else if (lay.fast) {
     fast2d_init(A, ncells, st);
   } else {
     dim3 grid(64, (unsigned)std::min(ncells, 65535));
@@ -1117,21 +1124,25 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   int launched = 0;
   auto one_iteration = [&]() {
     tm.begin(HOM_K_ROW);
-    if (lay.fast) fast2d_row(A, nR, smem_frow, st);
+    if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, false, st);
+    else if (lay.fast) fast2d_row(A, nR, smem_frow, st);
     else k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     if (DIM == 3) {
       tm.begin(HOM_K_YFWD);
-      k_ypass<T, true, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
+      if (lay.fast) fast3d_ypass(A, nY, smem_fy, true, st);
+      else k_ypass<T, true, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
       tm.end();
     }
     tm.begin(HOM_K_GREEN);
-    if (lay.fast) fast2d_green(A, nC, smem_fgreen, st);
+    if (lay.fast && DIM == 3) fast3d_green(A, nC, smem_fgreen, st);
+    else if (lay.fast) fast2d_green(A, nC, smem_fgreen, st);
     else k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
     tm.end();
     if (DIM == 3) {
       tm.begin(HOM_K_YINV);
-      k_ypass<T, false, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
+      if (lay.fast) fast3d_ypass(A, nY, smem_fy, false, st);
+      else k_ypass<T, false, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
       tm.end();
     }
     tm.begin(HOM_K_CONTROL);
@@ -1179,7 +1190,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
   if (want_fields) {
     tm.begin(HOM_K_OUTPUT);
-    if (lay.fast) fast2d_out(A, nR, smem_frow, st);
+    if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, true, st);
+    else if (lay.fast) fast2d_out(A, nR, smem_frow, st);
     else k_row<T, DIM, true, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     HOM_CUDA_TRY(cudaGetLastError());
