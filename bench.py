@@ -126,7 +126,7 @@ def measured_peak_hbm():
 # capture summarised in profiles/k_row_f2d_k_green_f2d_1215_fp32.md (two 1215^2 cells x 3 loads;
 # traffic grows with the tiles processed, so a launch's traffic is this ratio times its bytes).
 # Valid for the kernels as captured there; None for kernels without a capture.
-TRAFFIC_RATIO = {"row": (110.056 + 55.197) / 215.77, "green": (177.548 + 116.237) / 354.61}
+TRAFFIC_RATIO = {"row": (110.363 + 54.692) / 215.77, "green": (177.533 + 116.269) / 354.61}
 
 
 def golden_ceff():
@@ -470,9 +470,30 @@ def profile_case(args):
                                                                           r["status"].ravel().tolist()))
 
 
+def profile_case3d(args):
+    """Small fixed 3D case for ncu captures: one 135^3 random-sphere cell (2-layer filter, contrast
+    10), 6 loads, exactly `args.iters` fixed-point iterations in FP32 (state ~380 MB per buffer)."""
+    import torch
+
+    import paper_1412_3228_gb300 as hom
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    torch.cuda.set_device(0)
+    n = 135
+    cell = H.rsa_spheres_cell(n, seed=1000 + n, vf=0.3, rmin=0.05, rmax=0.1, rule=H.RULE_TWO_LAYER,
+                              radius_px=1.0, subgrid=8, gap_voxels=n / 243.0)
+    phases = H.two_phases(10.0)
+    mat = hom.hom_filter_build([cell], phases)
+    r = hom.hom_solve(mat, np.eye(6), np.array([H.mean_lame(phases)]), precision=hom.HOM_FP32,
+                      criterion=hom.HOM_CRIT_EN, tol=-1.0, max_iter=args.iters, fields=False)
+    torch.cuda.synchronize()
+    print("profile case 3d: one cell of n=%d, %d iterations, status %s" % (n, args.iters, r["status"].ravel().tolist()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", action="store_true", help="run only the small fixed ncu case")
+    ap.add_argument("--profile-case3d", action="store_true", help="run only the small fixed 3D ncu case")
     ap.add_argument("--profile-n", type=int, default=1215)
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--fp64-case", action="store_true")
@@ -490,6 +511,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.profile_case:
         profile_case(args)
+        return
+    if args.profile_case3d:
+        profile_case3d(args)
         return
     if args.impl == "reference":
         if rank == 0:

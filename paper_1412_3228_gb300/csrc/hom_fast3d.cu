@@ -1,7 +1,8 @@
 // Specialised FP32 passes of the 3D fixed-point scheme (section 2, eqs. 1-a, 1-b, 2) for grid
 // sizes n with a compile-time radix plan (27, 45, 81, 135, 243).  Same lane-pair scheme as the 2D
 // passes (hom_fast2d.cu): shared memory holds float4 (re_A, re_B, im_A, im_B) per (position,
-// component), with the six Mandel components side by side (96-byte stride, conflict-free stages).
+// component), with the six Mandel components side by side; positions are 7 float4 apart in shared
+// memory (112 bytes: neighbouring threads' 16-byte accesses fall on distinct bank quads).
 //
 // One iteration is four passes, as in the generic 3D path:
 //   row pass   : 4 real rows (same z, consecutive y) x every active load; lines A = rows 0 + i 1,
@@ -26,6 +27,8 @@ namespace hom {
 namespace {
 
 constexpr int NP = 6;                       // lane pairs per position (3D Mandel components)
+constexpr int SP = 7;                       // shared-memory position stride (float4): 28 words keeps
+                                            // 8 neighbouring 16-byte accesses on distinct bank quads
 constexpr int kSizes3[] = {27, 45, 81, 135, 243};
 constexpr uint32_t kLabel8Mixed = 255;      // one-byte label of a mixed voxel
 
@@ -61,14 +64,14 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
   const float lam0 = OUT ? 0.f : cc.lam0, mu2_0 = OUT ? 0.f : cc.mu2;
   float4* taub = static_cast<float4*>(A.tau);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  uint8_t* slab = reinterpret_cast<uint8_t*>(s + N * NP);
+  uint8_t* slab = reinterpret_cast<uint8_t*>(s + N * SP);
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.label8 + c.lp_off + (size_t)t.row0 * NL);
     for (int i = threadIdx.x; i < nr * NL / 16; i += kT) cp16(slab + 16 * i, src + i);
   }
-  float2* tws = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16);
+  float2* tws = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16);
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
-  float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + (N + 1) / 2);
+  float2* sph = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16 + (N + 1) / 2);
   cp_commit();
   for (int i = threadIdx.x; i < c.nph; i += kT) {
     const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 21;
@@ -94,9 +97,9 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
         const float2 q1 = h ? make_float2(v[1].y, v[1].w) : make_float2(v[1].x, v[1].z);
         const float2 q2 = h ? make_float2(v[2].y, v[2].w) : make_float2(v[2].x, v[2].z);
         const float2 q3 = h ? make_float2(v[3].y, v[3].w) : make_float2(v[3].x, v[3].z);
-        s[kx * NP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
+        s[kx * SP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
         if (kx > 0) {
-          s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
+          s[(N - kx) * SP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
         } else {
           sh.dc[la][0][0][k] = q0.x;
           sh.dc[la][0][1][k] = q1.x;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
     }
     cp_wait_all();
     __syncthreads();
-    fft_dif_p<NP, N, false>(s, tws);  // inverse: eps at digit-reversed positions
+    fft_dif_p<NP, N, false, float2, SP>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update; lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3)
     for (int pos = threadIdx.x; pos < N; pos += kT) {
@@ -120,7 +123,7 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
       }
       float4 e[NP], o[NP];
 #pragma unroll
-      for (int k = 0; k < NP; ++k) e[k] = s[pos * NP + k];
+      for (int k = 0; k < NP; ++k) e[k] = s[pos * SP + k];
       if (!mixed) {
         float2 dl_lo, dl_hi, dm_lo, dm_hi;
         {
@@ -187,12 +190,12 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < NP; ++k) s[pos * NP + k] = o[k];
+        for (int k = 0; k < NP; ++k) s[pos * SP + k] = o[k];
       }
     }
     __syncthreads();  // the tile is read above and rewritten below (or by the next load's fill)
     if (OUT) continue;
-    fft_dit_p<NP, N, true>(s, tws);  // forward: natural order
+    fft_dit_p<NP, N, true, float2, SP>(s, tws);  // forward: natural order
 
     // 3. split the two real rows of each line; store the half spectra of tau pair by pair
     for (int f = threadIdx.x; f < P * NP; f += kT) {
@@ -204,8 +207,8 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
       for (int h = 0; h < 2; ++h) {
         const int kx = 2 * p + h;
         if (kx >= H) break;
-        const float4 Z = s[kx * NP + k];
-        const float4 Zm = s[(kx == 0 ? 0 : N - kx) * NP + k];
+        const float4 Z = s[kx * SP + k];
+        const float4 Zm = s[(kx == 0 ? 0 : N - kx) * SP + k];
         const float2 o0 = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.z - Zm.z));
         const float2 o1 = make_float2(0.5f * (Z.z + Zm.z), 0.5f * (Zm.x - Z.x));
         const float2 o2 = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Z.w - Zm.w));
@@ -283,15 +286,15 @@ __device__ __forceinline__ void ypass3_body(const SolveArgs& A, const TaskL& t, 
   const size_t tb = idx3(c, N, t.load, t.kx0 / 2, t.fixed, 0);
   const float4* in = static_cast<const float4*>(A.tau) + tb;
   float4* out = static_cast<float4*>(FWD ? A.tau : A.eps[(it + 1) & 1]) + tb;
-  float2* tws = reinterpret_cast<float2*>(s + N * NP);
-  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + i, in + i);
+  float2* tws = reinterpret_cast<float2*>(s + N * SP);
+  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + (i / NP) * SP + i % NP, in + i);
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   cp_commit();
   cp_wait_all();
   __syncthreads();
-  if (FWD) fft_dif_p<NP, N, true>(s, tws);
-  else fft_dit_p<NP, N, false>(s, tws);
-  for (int i = threadIdx.x; i < N * NP; i += kT) out[i] = s[i];
+  if (FWD) fft_dif_p<NP, N, true, float2, SP>(s, tws);
+  else fft_dit_p<NP, N, false, float2, SP>(s, tws);
+  for (int i = threadIdx.x; i < N * NP; i += kT) out[i] = s[(i / NP) * SP + i % NP];
   if (threadIdx.x == 0) {
     const int ntk = t.kx0 + 1 < c.H ? 2 : 1;
     atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)N * ntk * NP * sizeof(float2)));
@@ -327,18 +330,18 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   float4* st = static_cast<float4*>(A.tau);
   const size_t zs = (size_t)N * NP;  // float4 stride between z planes at fixed y
   const size_t b0 = idx3(c, N, t.load, p, 0, py);
-  float2* tws = reinterpret_cast<float2*>(s + N * NP);
-  float* sx = reinterpret_cast<float*>(s + N * NP + (N + 1) / 2);
+  float2* tws = reinterpret_cast<float2*>(s + N * SP);
+  float* sx = reinterpret_cast<float*>(s + N * SP + (N + 1) / 2);
   for (int i = threadIdx.x; i < N * NP; i += kT) {
     const int zz = i / NP, k = i - zz * NP;
-    cp16(s + i, st + b0 + zz * zs + k);
+    cp16(s + zz * SP + k, st + b0 + zz * zs + k);
   }
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
   cp_wait_all();
   __syncthreads();
-  fft_dif_p<NP, N, true>(s, tws);  // forward: bin kz at position perm(kz)
+  fft_dif_p<NP, N, true, float2, SP>(s, tws);  // forward: bin kz at position perm(kz)
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -358,7 +361,7 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
     const float2 Z = f2(sx[pos]);
     P2 T[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) T[k] = ldp(s[pos * NP + k]);
+    for (int k = 0; k < NP; ++k) T[k] = ldp(s[pos * SP + k]);
     P2 G[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) G[d] = ldp(gb[3 * pos + d]);
@@ -424,7 +427,7 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
       wr.x = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < NP; ++k) s[pos * NP + k] = stp(E[k]);
+    for (int k = 0; k < NP; ++k) s[pos * SP + k] = stp(E[k]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) gb[3 * pos + d] = stp(Gn[d]);
     const float2 a1 = mul2(wr, r2), a2 = mul2(a1, iq);
@@ -456,10 +459,10 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
     }
   }
-  fft_dit_p<NP, N, false>(s, tws);  // inverse: natural z order
+  fft_dit_p<NP, N, false, float2, SP>(s, tws);  // inverse: natural z order
   for (int i = threadIdx.x; i < N * NP; i += kT) {
     const int zz = i / NP, k = i - zz * NP;
-    st[b0 + zz * zs + k] = s[i];
+    st[b0 + zz * zs + k] = s[zz * SP + k];
   }
   if (threadIdx.x == 0) {
     const int ntk = hasB ? 2 : 1;
@@ -518,12 +521,12 @@ bool fast3d_size(int n) {
 // row: tile | one-byte labels of 4 rows | twiddles | per-phase constants;  y: tile | twiddles;
 // Green: tile | twiddles | wave numbers
 size_t fast3d_smem_row(int nmax, int nphase_cell) {
-  return (size_t)nmax * NP * sizeof(float4) + (size_t)kFastRows * ((nmax + 15) / 16 * 16) +
+  return (size_t)nmax * SP * sizeof(float4) + (size_t)kFastRows * ((nmax + 15) / 16 * 16) +
          ((size_t)nmax + 1) / 2 * 16 + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
 }
-size_t fast3d_smem_y(int nmax) { return (size_t)nmax * NP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16; }
+size_t fast3d_smem_y(int nmax) { return (size_t)nmax * SP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16; }
 size_t fast3d_smem_green(int nmax) {
-  return (size_t)nmax * NP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16 + ((size_t)nmax + 3) / 4 * 16;
+  return (size_t)nmax * SP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16 + ((size_t)nmax + 3) / 4 * 16;
 }
 
 int fast3d_row(const SolveArgs& A, unsigned ntasks, size_t smem, bool out, cudaStream_t st) {

@@ -167,7 +167,7 @@ template <> struct Radix<243> { static constexpr int m = 3, r0 = 3, r1 = 9, r2 =
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
 // Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
 // (q = 1..R-1, j < L): neighbouring threads read neighbouring entries.
-template <int NP, int N, int R, int L, bool FWD, bool DIT, typename TW>
+template <int NP, int N, int R, int L, bool FWD, bool DIT, typename TW, int SP = NP>
 __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
   constexpr int NB = N / R, B = L * R;
   for (int t = threadIdx.x; t < NB * NP; t += kT) {
@@ -175,64 +175,64 @@ __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
     const int b = t - cc * NB;
     const int blk = b / L;
     const int j = b - blk * L;
-    float4* base = s + (blk * B + j) * NP + cc;
+    float4* base = s + (blk * B + j) * SP + cc;
     P2 v[R];
     if (DIT) {
       v[0] = ldp(base[0]);
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        P2 x = ldp(base[q * L * NP]);
+        P2 x = ldp(base[q * L * SP]);
         if (L > 1) x = twmul<FWD>(x, tw[(q - 1) * L + j]);
         v[q] = x;
       }
       dftp<R, FWD>(v);
 #pragma unroll
-      for (int p = 0; p < R; ++p) base[p * L * NP] = stp(v[out_pos<R>(p)]);
+      for (int p = 0; p < R; ++p) base[p * L * SP] = stp(v[out_pos<R>(p)]);
     } else {
 #pragma unroll
-      for (int q = 0; q < R; ++q) v[q] = ldp(base[q * L * NP]);
+      for (int q = 0; q < R; ++q) v[q] = ldp(base[q * L * SP]);
       dftp<R, FWD>(v);
       base[0] = stp(v[0]);
 #pragma unroll
       for (int p = 1; p < R; ++p) {
         P2 x = v[out_pos<R>(p)];
         if (L > 1) x = twmul<FWD>(x, tw[(p - 1) * L + j]);
-        base[p * L * NP] = stp(x);
+        base[p * L * SP] = stp(x);
       }
     }
   }
 }
 
 // Stage tables are stored back to back: stage 1 (span r0) first, then stage 2 (span r0 r1).
-template <int NP, int N, bool FWD, typename TW>
+template <int NP, int N, bool FWD, typename TW, int SP = NP>
 __device__ __forceinline__ void fft_dit_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
-  stage_p<NP, N, P::r0, 1, FWD, true>(s, tw);
+  stage_p<NP, N, P::r0, 1, FWD, true, TW, SP>(s, tw);
   __syncthreads();
   if constexpr (P::m > 1) {
-    stage_p<NP, N, P::r1, P::r0, FWD, true>(s, tw);
+    stage_p<NP, N, P::r1, P::r0, FWD, true, TW, SP>(s, tw);
     __syncthreads();
   }
   if constexpr (P::m > 2) {
-    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, true>(s, tw + off2);
+    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, true, TW, SP>(s, tw + off2);
     __syncthreads();
   }
 }
 
-template <int NP, int N, bool FWD, typename TW>
+template <int NP, int N, bool FWD, typename TW, int SP = NP>
 __device__ __forceinline__ void fft_dif_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
   if constexpr (P::m > 2) {
-    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, false>(s, tw + off2);
+    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, false, TW, SP>(s, tw + off2);
     __syncthreads();
   }
   if constexpr (P::m > 1) {
-    stage_p<NP, N, P::r1, P::r0, FWD, false>(s, tw);
+    stage_p<NP, N, P::r1, P::r0, FWD, false, TW, SP>(s, tw);
     __syncthreads();
   }
-  stage_p<NP, N, P::r0, 1, FWD, false>(s, tw);
+  stage_p<NP, N, P::r0, 1, FWD, false, TW, SP>(s, tw);
   __syncthreads();
 }
 
