@@ -52,7 +52,7 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
   if (threadIdx.x == 0) {
     int nal = 0;
     for (int l = 0; l < A.L; ++l)
-      if (OUT || A.active[t.cell * A.L + l]) sh.al[nal++] = l;
+      if ((t.load < 0 || l == t.load) && (OUT || A.active[t.cell * A.L + l])) sh.al[nal++] = l;
     sh.nal = nal;
   }
   __syncthreads();

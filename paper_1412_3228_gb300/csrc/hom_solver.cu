@@ -822,10 +822,23 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
       const char* e = std::getenv("HOM_ROW_PER_LOAD");
       return e && e[0] == '1';
     }();
+    static const bool per_load3 = [] {  // 3D: HOM_ROW_PER_LOAD3=1 gives one load per row task
+      const char* e = std::getenv("HOM_ROW_PER_LOAD3");
+      return e && e[0] == '1';
+    }();
     if (lay.fast && dim == 3) {  // groups of 4 rows (consecutive y) within each z plane
-      for (int z = 0; z < k.n; ++z)
-        for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), -1});
-      for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
+      if (per_load3) {
+        for (int l = 0; l < L; ++l) {
+          rt0[l] = (int)lay.tR.size();
+          for (int z = 0; z < k.n; ++z)
+            for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), l});
+          rt1[l] = (int)lay.tR.size();
+        }
+      } else {
+        for (int z = 0; z < k.n; ++z)
+          for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), -1});
+        for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
+      }
     } else if (lay.fast && per_load) {
       for (int l = 0; l < L; ++l) {
         rt0[l] = (int)lay.tR.size();
