@@ -30,6 +30,12 @@ constexpr int NP = 6;                       // lane pairs per position (3D Mande
 constexpr int SP = 7;                       // shared-memory position stride (float4): 28 words keeps
                                             // 8 neighbouring 16-byte accesses on distinct bank quads
 constexpr int kSizes3[] = {27, 45, 81, 135, 243};
+#ifndef HOM_FAST3D_THREADS
+#define HOM_FAST3D_THREADS 128
+#endif
+constexpr int kT3 = HOM_FAST3D_THREADS;     // threads per CTA: the 3D lines (n <= 243) give few
+                                            // butterflies per stage, so smaller CTAs idle less
+constexpr int kMinB3 = 768 / kT3;           // resident CTAs per SM the register budget targets
 constexpr uint32_t kLabel8Mixed = 255;      // one-byte label of a mixed voxel
 
 __device__ __forceinline__ size_t idx3(const CellDev& c, int n, int l, int p, int z, int y) {
@@ -67,13 +73,13 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
   uint8_t* slab = reinterpret_cast<uint8_t*>(s + N * SP);
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.label8 + c.lp_off + (size_t)t.row0 * NL);
-    for (int i = threadIdx.x; i < nr * NL / 16; i += kT) cp16(slab + 16 * i, src + i);
+    for (int i = threadIdx.x; i < nr * NL / 16; i += kT3) cp16(slab + 16 * i, src + i);
   }
   float2* tws = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16);
-  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   float2* sph = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16 + (N + 1) / 2);
   cp_commit();
-  for (int i = threadIdx.x; i < c.nph; i += kT) {
+  for (int i = threadIdx.x; i < c.nph; i += kT3) {
     const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 21;
     const float lam = __ldg(pc + 1);
     sph[i] = make_float2(lam - lam0, (__ldg(pc) - lam) - mu2_0);
@@ -83,7 +89,7 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
     const int l = sh.al[la];
     const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
     // 1. four half-spectrum rows -> two Hermitian-extended lines per component
-    for (int f = threadIdx.x; f < P * NP; f += kT) {
+    for (int f = threadIdx.x; f < P * NP; f += kT3) {
       const int p = f / NP, k = f - p * NP;
       const size_t b = idx3(c, N, l, p, z, y0) + k;
       float4 v[kFastRows];
@@ -110,10 +116,10 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
     }
     cp_wait_all();
     __syncthreads();
-    fft_dif_p<NP, N, false, float2, SP>(s, tws);  // inverse: eps at digit-reversed positions
+    fft_dif_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update; lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3)
-    for (int pos = threadIdx.x; pos < N; pos += kT) {
+    for (int pos = threadIdx.x; pos < N; pos += kT3) {
       uint32_t lab[kFastRows];
       bool mixed = false;
 #pragma unroll
@@ -195,10 +201,10 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
     }
     __syncthreads();  // the tile is read above and rewritten below (or by the next load's fill)
     if (OUT) continue;
-    fft_dit_p<NP, N, true, float2, SP>(s, tws);  // forward: natural order
+    fft_dit_p<NP, N, true, float2, SP, kT3>(s, tws);  // forward: natural order
 
     // 3. split the two real rows of each line; store the half spectra of tau pair by pair
-    for (int f = threadIdx.x; f < P * NP; f += kT) {
+    for (int f = threadIdx.x; f < P * NP; f += kT3) {
       const int p = f / NP, k = f - p * NP;
       float4 w[kFastRows];
 #pragma unroll
@@ -258,7 +264,7 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
 }
 
 template <bool OUT>
-__global__ void __launch_bounds__(kT, 3) k_row_f3d(SolveArgs A) {
+__global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared3 sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
@@ -287,14 +293,14 @@ __device__ __forceinline__ void ypass3_body(const SolveArgs& A, const TaskL& t, 
   const float4* in = static_cast<const float4*>(A.tau) + tb;
   float4* out = static_cast<float4*>(FWD ? A.tau : A.eps[(it + 1) & 1]) + tb;
   float2* tws = reinterpret_cast<float2*>(s + N * SP);
-  for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + (i / NP) * SP + i % NP, in + i);
-  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+  for (int i = threadIdx.x; i < N * NP; i += kT3) cp16(s + (i / NP) * SP + i % NP, in + i);
+  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   cp_commit();
   cp_wait_all();
   __syncthreads();
-  if (FWD) fft_dif_p<NP, N, true, float2, SP>(s, tws);
-  else fft_dit_p<NP, N, false, float2, SP>(s, tws);
-  for (int i = threadIdx.x; i < N * NP; i += kT) out[i] = s[(i / NP) * SP + i % NP];
+  if (FWD) fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);
+  else fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);
+  for (int i = threadIdx.x; i < N * NP; i += kT3) out[i] = s[(i / NP) * SP + i % NP];
   if (threadIdx.x == 0) {
     const int ntk = t.kx0 + 1 < c.H ? 2 : 1;
     atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)N * ntk * NP * sizeof(float2)));
@@ -302,7 +308,7 @@ __device__ __forceinline__ void ypass3_body(const SolveArgs& A, const TaskL& t, 
 }
 
 template <bool FWD>
-__global__ void __launch_bounds__(kT, 4) k_ypass_f3d(SolveArgs A) {
+__global__ void __launch_bounds__(kT3, 1024 / kT3) k_ypass_f3d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const TaskL t = A.tY[blockIdx.x];
@@ -332,16 +338,16 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   const size_t b0 = idx3(c, N, t.load, p, 0, py);
   float2* tws = reinterpret_cast<float2*>(s + N * SP);
   float* sx = reinterpret_cast<float*>(s + N * SP + (N + 1) / 2);
-  for (int i = threadIdx.x; i < N * NP; i += kT) {
+  for (int i = threadIdx.x; i < N * NP; i += kT3) {
     const int zz = i / NP, k = i - zz * NP;
     cp16(s + zz * SP + k, st + b0 + zz * zs + k);
   }
-  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
-  for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
+  for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
+  for (int i = threadIdx.x; i < (N + 3) / 4; i += kT3) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
   cp_wait_all();
   __syncthreads();
-  fft_dif_p<NP, N, true, float2, SP>(s, tws);  // forward: bin kz at position perm(kz)
+  fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);  // forward: bin kz at position perm(kz)
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -357,7 +363,7 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
                (c.g_off + (((size_t)t.load * (c.Hp / 2) + p) * N + py) * (size_t)N * 6) / 2;
   const double* Eld = A.E + (size_t)cl * NP;
   float2 r2s = make_float2(0.f, 0.f), r2c = r2s, rns = r2s, rnc = r2s;
-  for (int pos = threadIdx.x; pos < N; pos += kT) {
+  for (int pos = threadIdx.x; pos < N; pos += kT3) {
     const float2 Z = f2(sx[pos]);
     P2 T[NP];
 #pragma unroll
@@ -453,14 +459,14 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
     vv[1].add(rns.y);
     vv[1].add(-rnc.y);
     double tot[2];
-    block_sum<float, 2, kT>(vv, tot);  // contains the barrier before the inverse transform
+    block_sum<float, 2, kT3>(vv, tot);  // contains the barrier before the inverse transform
     if (threadIdx.x == 0) {
       A.partC[2 * (size_t)blockIdx.x] = tot[0];
       A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
     }
   }
-  fft_dit_p<NP, N, false, float2, SP>(s, tws);  // inverse: natural z order
-  for (int i = threadIdx.x; i < N * NP; i += kT) {
+  fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: natural z order
+  for (int i = threadIdx.x; i < N * NP; i += kT3) {
     const int zz = i / NP, k = i - zz * NP;
     st[b0 + zz * zs + k] = s[zz * SP + k];
   }
@@ -471,7 +477,7 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   }
 }
 
-__global__ void __launch_bounds__(kT, 3) k_green_f3d(SolveArgs A) {
+__global__ void __launch_bounds__(kT3, kMinB3) k_green_f3d(SolveArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const TaskL t = A.tC[blockIdx.x];
@@ -533,10 +539,10 @@ int fast3d_row(const SolveArgs& A, unsigned ntasks, size_t smem, bool out, cudaS
   int rc;
   if (out) {
     if ((rc = opt_in3(k_row_f3d<true>, smem)) != HOM_OK) return rc;
-    k_row_f3d<true><<<ntasks, kT, smem, st>>>(A);
+    k_row_f3d<true><<<ntasks, kT3, smem, st>>>(A);
   } else {
     if ((rc = opt_in3(k_row_f3d<false>, smem)) != HOM_OK) return rc;
-    k_row_f3d<false><<<ntasks, kT, smem, st>>>(A);
+    k_row_f3d<false><<<ntasks, kT3, smem, st>>>(A);
   }
   return HOM_OK;
 }
@@ -545,10 +551,10 @@ int fast3d_ypass(const SolveArgs& A, unsigned ntasks, size_t smem, bool fwd, cud
   int rc;
   if (fwd) {
     if ((rc = opt_in3(k_ypass_f3d<true>, smem)) != HOM_OK) return rc;
-    k_ypass_f3d<true><<<ntasks, kT, smem, st>>>(A);
+    k_ypass_f3d<true><<<ntasks, kT3, smem, st>>>(A);
   } else {
     if ((rc = opt_in3(k_ypass_f3d<false>, smem)) != HOM_OK) return rc;
-    k_ypass_f3d<false><<<ntasks, kT, smem, st>>>(A);
+    k_ypass_f3d<false><<<ntasks, kT3, smem, st>>>(A);
   }
   return HOM_OK;
 }
@@ -556,7 +562,7 @@ int fast3d_ypass(const SolveArgs& A, unsigned ntasks, size_t smem, bool fwd, cud
 int fast3d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
   int rc = opt_in3(k_green_f3d, smem);
   if (rc != HOM_OK) return rc;
-  k_green_f3d<<<ntasks, kT, smem, st>>>(A);
+  k_green_f3d<<<ntasks, kT3, smem, st>>>(A);
   return HOM_OK;
 }
 

@@ -167,10 +167,10 @@ template <> struct Radix<243> { static constexpr int m = 3, r0 = 3, r1 = 9, r2 =
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
 // Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
 // (q = 1..R-1, j < L): neighbouring threads read neighbouring entries.
-template <int NP, int N, int R, int L, bool FWD, bool DIT, typename TW, int SP = NP>
+template <int NP, int N, int R, int L, bool FWD, bool DIT, typename TW, int SP = NP, int NT = kT>
 __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
   constexpr int NB = N / R, B = L * R;
-  for (int t = threadIdx.x; t < NB * NP; t += kT) {
+  for (int t = threadIdx.x; t < NB * NP; t += NT) {
     const int cc = t / NB;
     const int b = t - cc * NB;
     const int blk = b / L;
@@ -204,35 +204,35 @@ __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
 }
 
 // Stage tables are stored back to back: stage 1 (span r0) first, then stage 2 (span r0 r1).
-template <int NP, int N, bool FWD, typename TW, int SP = NP>
+template <int NP, int N, bool FWD, typename TW, int SP = NP, int NT = kT>
 __device__ __forceinline__ void fft_dit_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
-  stage_p<NP, N, P::r0, 1, FWD, true, TW, SP>(s, tw);
+  stage_p<NP, N, P::r0, 1, FWD, true, TW, SP, NT>(s, tw);
   __syncthreads();
   if constexpr (P::m > 1) {
-    stage_p<NP, N, P::r1, P::r0, FWD, true, TW, SP>(s, tw);
+    stage_p<NP, N, P::r1, P::r0, FWD, true, TW, SP, NT>(s, tw);
     __syncthreads();
   }
   if constexpr (P::m > 2) {
-    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, true, TW, SP>(s, tw + off2);
+    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, true, TW, SP, NT>(s, tw + off2);
     __syncthreads();
   }
 }
 
-template <int NP, int N, bool FWD, typename TW, int SP = NP>
+template <int NP, int N, bool FWD, typename TW, int SP = NP, int NT = kT>
 __device__ __forceinline__ void fft_dif_p(float4* s, const TW* tw) {
   using P = Radix<N>;
   constexpr int off2 = P::r0 * (P::r1 - 1);
   if constexpr (P::m > 2) {
-    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, false, TW, SP>(s, tw + off2);
+    stage_p<NP, N, P::r2, P::r0 * P::r1, FWD, false, TW, SP, NT>(s, tw + off2);
     __syncthreads();
   }
   if constexpr (P::m > 1) {
-    stage_p<NP, N, P::r1, P::r0, FWD, false, TW, SP>(s, tw);
+    stage_p<NP, N, P::r1, P::r0, FWD, false, TW, SP, NT>(s, tw);
     __syncthreads();
   }
-  stage_p<NP, N, P::r0, 1, FWD, false, TW, SP>(s, tw);
+  stage_p<NP, N, P::r0, 1, FWD, false, TW, SP, NT>(s, tw);
   __syncthreads();
 }
 
