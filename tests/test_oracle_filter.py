@@ -250,3 +250,14 @@ def test_filter_build_pure_voxels_are_exact():
     d = np.hypot((xs + 0.5) / n - 0.5, (ys + 0.5) / n - 0.5) - math.sqrt(0.2 / math.pi)
     assert np.all(np.abs(d) <= 1.0 / n + 1e-9)
     assert mixed.sum() > 0
+
+
+def test_n_within_picks_the_first_resolution_that_stays_in_band():
+    """N_1% logic of the resolution study (section 3): the smallest n after which every larger
+    resolution stays within 1 % of the converged value."""
+    from paper_1412_3228_gb300.experiments import n_within
+    sizes = [9, 15, 21, 27, 45]
+    assert n_within(sizes, [1.5, 1.0, 1.02, 0.995, 1.001], 1.0) == 27   # 21 is outside the band
+    assert n_within(sizes, [1.005, 0.995, 1.0, 1.0, 1.0], 1.0) == 9
+    assert n_within(sizes, [1.0, 1.0, 1.0, 1.0, 1.2], 1.0) is None     # the last point misses
+    assert n_within(list(reversed(sizes)), [1.001, 0.995, 1.02, 1.0, 1.5], 1.0) == 27  # order-free
