@@ -590,3 +590,40 @@ def default_reference(phases: Sequence[Tuple[float, float]]) -> Tuple[float, flo
     lams = [p[0] for p in phases]
     mus = [p[1] for p in phases]
     return 0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus))
+
+
+# =============================================================================================
+# Fourier extrapolation of the filtered stiffness (section 6, Fig. 4)
+
+
+def fourier_extrapolate(field: np.ndarray, dim: int, n: int, m: int) -> np.ndarray:
+    """Truncated Fourier series of a real grid field, evaluated on a finer grid (section 6, Fig. 4).
+
+    The Fourier coefficients are the FFT of the values at the grid points x_a = (a + 1/2)/n; the
+    series keeps the frequencies of J (-(n-1)/2 .. (n-1)/2 per axis) and is evaluated at the voxel
+    centres y_b = (b + 1/2)/m of an m^dim grid:
+        f(y) = n^-dim sum_{k in J} f_hat(k) exp(2 pi i k . (y - x_0)),   x_0 = 1/(2n) per axis,
+    the shift making f(x_a) reproduce the field's value at x_a.  field: [(n,) n, n] (numpy axis
+    order (z,) y, x).  Returns [(m,) m, m] float64 (J is symmetric for odd n, so the series is
+    real; the imaginary part of the sum is rounding and is dropped)."""
+    fh = _fft(np.asarray(field, dtype=np.float64).reshape((n,) * dim), dim)
+    k = signed_frequencies(n)
+    y = (np.arange(m) + 0.5) / m
+    W = np.exp(2j * np.pi * np.outer(y - 0.5 / n, k))     # [m, n] over (fine point, FFT index)
+    out = fh
+    for ax in range(dim):
+        out = np.moveaxis(np.tensordot(W, out, axes=([1], [ax])), 0, ax)
+    return out.real / float(n) ** dim
+
+
+def exact_property(cell: Cell, values: Sequence[float], m: int) -> np.ndarray:
+    """A per-phase scalar (values[phase]) at the voxel centres of an m^dim grid, m a multiple of
+    the cell's n: the unfiltered microstructure that Fig. 4-A shows, point-sampled by the same
+    exact membership recipe as the filter."""
+    if m % cell.n:
+        raise ValueError("m must be a multiple of n")
+    k = m // cell.n
+    b = np.arange(m)
+    grids = np.meshgrid(*([b] * cell.dim), indexing="ij")
+    su = np.stack([2.0 * grids[cell.dim - 1 - c] + 1.0 for c in range(cell.dim)], axis=-1)
+    return np.asarray(values, dtype=np.float64)[phase_at(cell, su, k)]
