@@ -15,7 +15,7 @@
  *   4. the adjoint (reverse-mode) derivative of a loss on C_eff and on the local stresses.
  *
  * Conventions shared by every call
- *   - Grids are odd, n voxels per side, n = 3^a 5^b 7^c, 3 <= n <= 2187.  The cell side is 1 and
+ *   - Grids are odd, n voxels per side, n = 3^a 5^b 7^c 11^d 13^e, 3 <= n <= 2187.  The cell side is 1 and
  *     the grid points are voxel centres x_a = (a + 1/2)/n.
  *   - Strains, stresses and stiffnesses use Mandel notation: 2D (plane strain) vectors hold
  *     (11, 22, sqrt2*12), nc = 3; 3D vectors hold (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
@@ -46,7 +46,7 @@ extern "C" {
 /* ------------------------------------------------------------------ status codes */
 #define HOM_OK 0
 #define HOM_ERR_INVALID_ARG 1       /* a pointer, size or option is invalid                   */
-#define HOM_ERR_UNSUPPORTED_SIZE 2  /* even n, a prime factor other than 3, 5, 7, n too large  */
+#define HOM_ERR_UNSUPPORTED_SIZE 2  /* even n, a prime factor above 13, n too large           */
 #define HOM_ERR_NOT_CONVERGED 3     /* some load case hit max_iter; every output is still set  */
 #define HOM_ERR_DIVERGED 4          /* some load case diverged (non-finite or growing error)  */
 #define HOM_ERR_TIMEOUT 5           /* a device-side wait ran out of its budget               */
@@ -98,7 +98,7 @@ typedef struct hom_primitive {
  * and a fine point is inside the ball of voxel a when its distance to x_a is <= radius_px / n. */
 typedef struct hom_cell {
   int32_t dim;          /* 2 or 3                                                 */
-  int32_t n;            /* voxels per side (odd, 3^a 5^b 7^c)                     */
+  int32_t n;            /* voxels per side (odd, 3^a 5^b 7^c 11^d 13^e)           */
   int32_t matrix_phase; /* phase of points outside every primitive                */
   int32_t rule;         /* HOM_RULE_*                                             */
   double radius_px;     /* filter radius in voxel units, 0 < radius_px <= (n-1)/2 */
@@ -270,6 +270,24 @@ int hom_solve_backward(const hom_cell* cells, int32_t ncells, const hom_material
  * Synchronises the stream before returning, like hom_solve. */
 int hom_solve_noalloc(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                       const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
+
+/* Fourier extrapolation of the filtered stiffness (section 6, Fig. 4): the truncated Fourier series
+ * of one component of c~ whose coefficients are the DFT of its grid values x_a = (a + 1/2)/n on the
+ * odd frequency set J, evaluated at the voxel centres y_b = (b + 1/2)/m of a finer m^dim grid:
+ *     f(y) = n^-dim sum_{k in J} c_hat(k) exp(2 pi i k.(y - x_0)),   x_0 = 1/(2n) per axis,
+ * which reproduces c~(x_a) wherever a fine point coincides with a grid point.  A diagnostic of how
+ * the spectral method "sees" the filtered microstructure between grid points.  Computed in FP64.
+ *   cells/ncells  the batch given to hom_filter_build, mat its material
+ *   cell          index of the cell to extrapolate
+ *   comp          packed component of c~ (upper triangle row by row: 0 = c~_11, 1 = c~_12, ...)
+ *   m             fine points per side, 1 <= m <= 32768 in 2D, <= 1024 in 3D (m < n samples the
+ *                 series more coarsely than the grid; m = n returns c~(x_a) itself)
+ *   out           host or device [(m,) m, m] float64, x fastest; caller-owned
+ *   stream        cudaStream_t or NULL
+ * Allocates scratch of about n^dim + n m^(dim-1) doubles (plus m^dim when out is host memory) on
+ * the stream; HOM_ERR_OOM if that fails.  Synchronises the stream. */
+int hom_fourier_extrapolate(const hom_cell* cells, int32_t ncells, const hom_material* mat, int32_t cell,
+                            int32_t comp, int32_t m, double* out, void* stream);
 
 /* Effective stiffness from mean stresses: <sigma^(l)> = C_eff E^(l) for the L = nc linearly
  * independent load cases of each cell, so C_eff = S^T (E^T)^-1 (with the nc unit Mandel strains

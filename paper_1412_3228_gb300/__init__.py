@@ -110,6 +110,9 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(hom_result), ctypes.c_void_p]
         h.hom_effective_stiffness.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        h.hom_fourier_extrapolate.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_void_p]
         h.hom_last_error.restype = ctypes.c_char_p
         h.hom_version.restype = ctypes.c_int32
         _lib_handle = h
@@ -411,6 +414,30 @@ def hom_effective_stiffness(E, mean_sigma, dim: int) -> np.ndarray:
                                          ctypes.c_void_p(S.ctypes.data),
                                          C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return C
+
+
+def packed_index(i: int, j: int, dim: int) -> int:
+    """Position of stiffness entry (i, j) (Mandel indices) in the packed upper triangle."""
+    nc = nc_of(dim)
+    i, j = min(i, j), max(i, j)
+    return i * nc - i * (i - 1) // 2 + (j - i)
+
+
+def hom_fourier_extrapolate(material: Material, cell: int, m: int, comp: int = 0, out: Optional[torch.Tensor] = None,
+                            stream=None) -> torch.Tensor:
+    """Truncated Fourier series of packed component `comp` of c~ for one cell of the material,
+    evaluated at the voxel centres of an m^dim grid (section 6, Fig. 4); see include/hom.h.
+    Returns a float64 tensor [(m,) m, m] on the material's device (or fills `out`, host or device)."""
+    dim = material.dim
+    if out is None:
+        out = torch.empty((m,) * dim, dtype=torch.float64, device=material.label.device)
+    if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != m ** dim:
+        raise ValueError("out must be a contiguous float64 tensor of m^dim elements")
+    with torch.cuda.device(material.label.device):
+        _check(lib().hom_fourier_extrapolate(material.marshalled.cells, len(material.cells),
+                                             ctypes.byref(material.struct), int(cell), int(comp), int(m),
+                                             out.data_ptr(), _stream_handle(stream)))
+    return out
 
 
 def field_views(result: dict, cells, dim: int) -> List[torch.Tensor]:

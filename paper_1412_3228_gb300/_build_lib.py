@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["hom_capi.cu", "hom_filter.cu", "hom_solver.cu", "hom_fast2d.cu", "hom_fast3d.cu", "hom_noalloc.cu", "hom_backward.cu"]
+SOURCES = ["hom_capi.cu", "hom_filter.cu", "hom_solver.cu", "hom_fast2d.cu", "hom_fast3d.cu", "hom_noalloc.cu", "hom_backward.cu", "hom_extrap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

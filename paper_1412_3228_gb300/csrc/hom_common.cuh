@@ -112,13 +112,44 @@ HOM_HD void dft7(V* v) {
   for (int p = 0; p < 7; ++p) v[p] = out[p];
 }
 
+// Register DFT of a prime size P >= 11 by symmetric pairs: with a_q = x_q + x_{P-q} and
+// b_q = x_q - x_{P-q} (q = 1 .. H, H = (P-1)/2),
+//   X_p, X_{P-p} = x_0 + sum_q cos(2 pi pq/P) a_q  -/+  i sum_q sin(2 pi pq/P) b_q   (forward),
+// with the signs of the imaginary part swapped for the inverse.  H^2 complex multiply-adds per
+// half, against (P-1)^2 for the plain sum.
+template <int P, bool FWD, typename V, typename T>
+HOM_HD void dft_prime(V* v) {
+  constexpr int H = (P - 1) / 2;
+  V a[H + 1], b[H + 1];
+#pragma unroll
+  for (int q = 1; q <= H; ++q) { a[q] = v[q] + v[P - q]; b[q] = v[q] - v[P - q]; }
+  V out[P];
+  out[0] = v[0];
+#pragma unroll
+  for (int q = 1; q <= H; ++q) out[0] = out[0] + a[q];
+#pragma unroll
+  for (int p = 1; p <= H; ++p) {
+    V re = v[0], im = mk(T(0), T(0));
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      const int k = (p * q) % P;
+      re = re + (T)tw_cos(P, k) * a[q];
+      im = im + (T)tw_sin(P, k) * b[q];
+    }
+    out[p] = FWD ? re + mul_mi(im) : re + mul_pi(im);
+    out[P - p] = FWD ? re + mul_pi(im) : re + mul_mi(im);
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) v[p] = out[p];
+}
+
 // Register DFTs.  dft_small<R> transforms v[0..R) in place; for a composite R the results come
 // out in a fixed, compile-time order: X[k] is left in v[out_pos<R>(k)].  Prime radices keep the
 // natural order.
 template <int R> HOM_HD constexpr int split_a() {  // R = A * B with A the first factor
   return R == 9 ? 3 : R == 15 ? 3 : R == 21 ? 3 : R == 25 ? 5 : R == 27 ? 3 : R == 35 ? 5 : R == 45 ? 5 : R == 49 ? 7 : 1;
 }
-template <int R> HOM_HD constexpr bool is_prime_radix() { return R == 3 || R == 5 || R == 7; }
+template <int R> HOM_HD constexpr bool is_prime_radix() { return R == 3 || R == 5 || R == 7 || R == 11 || R == 13; }
 
 template <int R> HOM_HD constexpr int out_pos(int k) {
   if constexpr (is_prime_radix<R>()) {
@@ -165,6 +196,7 @@ HOM_HD void dft_small(V* v) {
   if constexpr (R == 3) dft3<FWD, V, T>(v);
   else if constexpr (R == 5) dft5<FWD, V, T>(v);
   else if constexpr (R == 7) dft7<FWD, V, T>(v);
+  else if constexpr (R == 11 || R == 13) dft_prime<R, FWD, V, T>(v);
   else dft_composite<split_a<R>(), R / split_a<R>(), FWD, V, T>(v);
 }
 
@@ -331,6 +363,8 @@ HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
     case 5: STAGE(5); break;                                                \
     case 7: STAGE(7); break;                                                \
     case 9: if constexpr (MAXR >= 9) STAGE(9); break;                       \
+    case 11: if constexpr (MAXR >= 11) STAGE(11); break;                    \
+    case 13: if constexpr (MAXR >= 13) STAGE(13); break;                    \
     case 15: if constexpr (MAXR >= 15) STAGE(15); break;                    \
     case 21: if constexpr (MAXR >= 21) STAGE(21); break;                    \
     case 25: if constexpr (MAXR >= 25) STAGE(25); break;                    \

@@ -21,15 +21,15 @@ struct HostPlan {
   std::vector<double> xi;       // 2 pi a(k), a(k) the signed frequency of DFT bin k
 };
 
-// Factor n into the register radices {3, 5, 7, 9, 15, 21, 25, 27, 35, 45, 49} (each at most
-// `max_radix`) with the fewest stages, then the smallest largest radix.  Returns false if n has
-// a prime factor other than 3, 5, 7.
+// Factor n into the register radices {3, 5, 7, 9, 11, 13, 15, 21, 25, 27, 35, 45, 49} (each at
+// most `max_radix`) with the fewest stages, then the smallest largest radix.  Returns false if n
+// has a prime factor other than 3, 5, 7, 11, 13.
 inline bool factorize(int n, std::vector<int>& radix, int max_radix = 45) {
-  static const int kRadices[] = {45, 35, 27, 25, 21, 15, 9, 7, 5, 3, 49};
+  static const int kRadices[] = {45, 35, 27, 25, 21, 15, 13, 11, 9, 7, 5, 3, 49};
   radix.clear();
   if (n < 3 || (n % 2) == 0) return false;
   int m = n;
-  for (int r : {3, 5, 7})
+  for (int r : {3, 5, 7, 11, 13})
     while (m % r == 0) m /= r;
   if (m != 1) return false;
   std::vector<int> best, cur;

@@ -745,7 +745,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
       if (external) {
         HostPlan hp;
         if (!build_host_plan(k.n, hp, max_radix) || (int)hp.radix.size() > kMaxStages)
-          return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7", k.n);
+          return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7, 11, 13", k.n);
         p.n = k.n;
         p.nstage = (int)hp.radix.size();
         for (int s2 = 0; s2 < p.nstage; ++s2) {

@@ -7,9 +7,15 @@
 * `n_within` - N_1%: the smallest resolution from which every larger resolution of the study
   stays within a relative tolerance (1 %) of the converged value.
 * `n1pct_vs_radius` - N_1% as a function of the filter radius, per rule (Fig. 1-B and D).
+* `iteration_sweep` - section 5, Fig. 3: iterations at convergence against the elastic contrast
+  (reference medium at the optimal choice) and against the scale alpha of the reference medium
+  (fixed contrast), per filter radius, each as ONE batched solve.
+* `extrapolation_study` - section 6, Fig. 4: the truncated Fourier series of c~_11 on a finer grid,
+  per filter radius, with its overshoot beyond the phase range and its L2 gap to a point-sampled
+  exact microstructure supplied by the caller.
 
 Grid sizes must be odd (the frequency set J of section 1 is defined for odd N) and factor into
-3, 5 and 7.  The converged value is the unfiltered stress at a large resolution `n_ref` (the
+3, 5, 7, 11 and 13.  The converged value is the unfiltered stress at a large resolution `n_ref` (the
 filters' pixel-sized smoothing vanishes as the grid is refined, so every rule converges to it).
 
     python -m paper_1412_3228_gb300.experiments --contrast 1000 --sizes 9,15,21,25,27,35,45,63,75,81,105,125
@@ -61,8 +67,8 @@ def axial_stress_sweep(sizes: Iterable[int], contrast: float, rules: Iterable[st
     criterion = hom.HOM_CRIT_E if criterion is None else criterion
     sizes = [int(n) for n in sizes]
     for n in sizes + ([n_ref] if n_ref else []):
-        if n % 2 == 0 or not _factors_357(n):
-            raise ValueError("grid size %d must be odd with factors 3, 5, 7" % n)
+        if n % 2 == 0 or not _factors_supported(n):
+            raise ValueError("grid size %d must be odd with factors 3, 5, 7, 11, 13" % n)
     phases = H.two_phases(contrast)
     cells, keys = [], []
     for rule in rules:
@@ -105,8 +111,77 @@ def n1pct_vs_radius(study: Dict, rel: float = 0.01, reference: Optional[float] =
     return out
 
 
-def _factors_357(n: int) -> bool:
-    for p in (3, 5, 7):
+def iteration_sweep(n: int = 65, contrasts: Sequence[float] = (1e-3, 1e-2, 0.1, 10.0, 100.0, 1e3),
+                    alphas: Sequence[float] = (0.9, 1.0, 1.25, 1.5, 2.0, 3.0), alpha_contrast: float = 1e3,
+                    radii: Sequence[float] = (0.55, 1.0, 1.5), rule: str = "2-layers", radius: float = math.pi / 15,
+                    subgrid: int = 16, tol: float = 1e-4, max_iter: int = 20000, diverge_window: int = 50,
+                    precision: Optional[int] = None, criterion: Optional[int] = None, device=None) -> Dict:
+    """Iterations of the basic scheme at convergence (section 5, Fig. 3) on the centred disk.
+
+    A radius of 0 stands for the unfiltered cell.  Part A: one cell per (radius, contrast) with the
+    reference medium at the optimal choice
+    (lam0, mu0) = mid-range of the phase constants.  Part B: one cell per (radius, alpha) at contrast
+    `alpha_contrast` with the reference medium alpha * (lam0, mu0).  Each part is one filter build and
+    one solve over all its cells (every cell carries its own phase pair and reference medium).  A
+    record's status is 0 when the equilibrium error fell below `tol`, 1 at max_iter, 2 on
+    divergence (non-finite error, or `diverge_window` successive increases)."""
+    import paper_1412_3228_gb300 as hom
+    precision = hom.HOM_FP64 if precision is None else precision
+    criterion = hom.HOM_CRIT_E if criterion is None else criterion
+    if n % 2 == 0 or not _factors_supported(n):
+        raise ValueError("grid size %d must be odd with factors 3, 5, 7, 11, 13" % n)
+
+    def run(keys):
+        cells, phases, c0 = [], [], []
+        for r, contrast, alpha in keys:
+            cell = H.centred_disk_cell(n, rule=RULES[rule] if r else H.RULE_NONE, radius_px=r if r else 1.0,
+                                       subgrid=subgrid, radius=radius)
+            cells.append(H.remap_phases(cell, len(phases)))
+            pair = H.two_phases(contrast)
+            phases.extend(pair)
+            lam0, mu0 = H.mean_lame(pair)
+            c0.append((alpha * lam0, alpha * mu0))
+        mat = hom.hom_filter_build(cells, phases, device=device)
+        res = hom.hom_solve(mat, np.array([[1.0, 0.0, 0.0]]), c0, precision=precision, criterion=criterion,
+                            tol=tol, max_iter=max_iter, diverge_window=diverge_window, fields=False)
+        return [dict(radius_px=r, contrast=contrast, alpha=alpha, iterations=int(res["iterations"][i, 0]),
+                     status=int(res["status"][i, 0]), err=float(res["err"][i, 0]))
+                for i, (r, contrast, alpha) in enumerate(keys)]
+
+    part_a = run([(r, float(c), 1.0) for r in radii for c in contrasts])
+    part_b = run([(r, float(alpha_contrast), float(a)) for r in radii for a in alphas])
+    return dict(n=n, rule=rule, tol=tol, vs_contrast=part_a, vs_alpha=part_b)
+
+
+def extrapolation_study(n: int = 65, m: int = 325, radii: Sequence[float] = (0.0, 0.3, 0.55, 1.0, 1.5),
+                        rule: str = "voigt", contrast: float = 1e-3, radius: float = math.pi / 15, subgrid: int = 16,
+                        exact: Optional[np.ndarray] = None, device=None) -> Dict:
+    """Fourier extrapolation of c~_11 (section 6, Fig. 4) for each filter radius (0 = no filter), all
+    cells in one filter build.  Returns the fine-grid fields and, per radius, the overshoot of the
+    extrapolation beyond the phase range (relative to the range) and, if `exact` (the m^2 exact
+    property, e.g. point-sampled phases) is given, the relative L2 gap to it."""
+    import paper_1412_3228_gb300 as hom
+    phases = H.two_phases(contrast)
+    vals = [lam + 2.0 * mu for lam, mu in phases]            # c_11 of each isotropic phase
+    span = max(vals) - min(vals)
+    cells = [H.centred_disk_cell(n, rule=RULES[rule] if r else H.RULE_NONE, radius_px=r if r else 1.0,
+                                 subgrid=subgrid, radius=radius) for r in radii]
+    mat = hom.hom_filter_build(cells, phases, device=device)
+    records, fields = [], []
+    for i, r in enumerate(radii):
+        f = hom.hom_fourier_extrapolate(mat, i, m, 0)
+        fields.append(f)
+        fmax, fmin = float(f.max()), float(f.min())
+        rec = dict(radius_px=float(r), overshoot=max(fmax - max(vals), min(vals) - fmin) / span)
+        if exact is not None:
+            d = f.cpu().numpy() - exact
+            rec["l2_gap"] = float(np.sqrt(np.mean(d * d)) / span)
+        records.append(rec)
+    return dict(n=n, m=m, rule=rule, contrast=contrast, records=records, fields=fields)
+
+
+def _factors_supported(n: int) -> bool:
+    for p in (3, 5, 7, 11, 13):
         while n % p == 0:
             n //= p
     return n == 1
@@ -121,12 +196,17 @@ def main(argv=None):
     ap.add_argument("--n-ref", type=int, default=405)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--fp32", action="store_true", help="FP32 fields (criterion e_n) instead of FP64")
+    ap.add_argument("--study", choices=("resolution", "iterations"), default="resolution",
+                    help="resolution: section 3, Fig. 1; iterations: section 5, Fig. 3")
     args = ap.parse_args(argv)
     import torch
     import paper_1412_3228_gb300 as hom
     from paper_1412_3228_gb300 import _build_lib
     _build_lib.build()
     torch.cuda.set_device(0)
+    if args.study == "iterations":
+        print(json.dumps(iteration_sweep(n=65, tol=args.tol, radii=[float(x) for x in args.radii.split(",")])))
+        return
     study = axial_stress_sweep([int(x) for x in args.sizes.split(",")], args.contrast, args.rules.split(","),
                                [float(x) for x in args.radii.split(",")], tol=args.tol, n_ref=args.n_ref,
                                precision=hom.HOM_FP32 if args.fp32 else hom.HOM_FP64,

@@ -29,3 +29,30 @@ def test_voigt_filter_divides_the_required_resolution_for_a_compliant_inclusion(
     assert 2 * n1[("voigt", 0.55)] <= n1[("none", 1.0)]
     # the larger radius needs more resolution than the near-optimal 0.55 (section 3)
     assert n1[("voigt", 1.0)] >= n1[("voigt", 0.55)]
+
+
+def test_iteration_counts_against_contrast_and_reference_medium():
+    """Section 5, Fig. 3 (65^2): filtering neither helps nor hurts the basic scheme's iteration count
+    (the curves of radii 0.55, 1.0 and 1.5 and of the unfiltered cell stay within a factor 1.5 of each
+    other while the count itself spans orders of magnitude, so they coincide on a log axis); the count grows
+    with the contrast on both sides of 1; below the optimal reference medium (alpha < 1) the scheme
+    does not converge; far above it the count grows with alpha (here 1.5 -> 3; the paper states no
+    monotonicity right above the optimum, where the count measured at 1.25 is below the one at 1)."""
+    radii = (0.0, 0.55, 1.0, 1.5)
+    sweep = X.iteration_sweep(n=65, contrasts=(1e-3, 0.1, 10.0, 1e3), alphas=(0.9, 1.0, 1.5, 3.0), radii=radii)
+    a = {(r["radius_px"], r["contrast"]): r for r in sweep["vs_contrast"]}
+    assert all(r["status"] == 0 for r in sweep["vs_contrast"]), sweep["vs_contrast"]
+    for c in (1e-3, 0.1, 10.0, 1e3):
+        its = [a[(r, c)]["iterations"] for r in radii]
+        assert max(its) <= 1.5 * min(its), (c, its)    # within 0.18 decade on a log axis
+    for r in radii:
+        assert a[(r, 1e3)]["iterations"] > 2 * a[(r, 10.0)]["iterations"]
+        assert a[(r, 1e-3)]["iterations"] > 2 * a[(r, 0.1)]["iterations"]
+    b = {(r["radius_px"], r["alpha"]): r for r in sweep["vs_alpha"]}
+    for r in radii:
+        assert b[(r, 0.9)]["status"] != 0, b[(r, 0.9)]
+        assert all(b[(r, al)]["status"] == 0 for al in (1.0, 1.5, 3.0))
+        assert b[(r, 1.5)]["iterations"] < b[(r, 3.0)]["iterations"]
+    for al in (1.0, 1.5, 3.0):
+        its = [b[(r, al)]["iterations"] for r in radii]
+        assert max(its) <= 1.5 * min(its), (al, its)

@@ -182,6 +182,36 @@ def test_solve_fp32_3d_parity():
     assert _rel(C, Cref) < 1e-5
 
 
+def test_radix_11_and_13_grids():
+    """Grids with prime factors 11 and 13 (11, 13, 65 = 5 x 13 -- the paper's 65-pixel cell of
+    sections 4 to 6 -- and 143 = 11 x 13) in one batch, FP64 against the oracle (identical iteration
+    counts, 1e-10 on C_eff and fields), then FP32 within 1e-5; and a 3D 39 = 3 x 13 cell."""
+    cells = [H.centred_disk_cell(n, rule=rule, radius=math.pi / 15)
+             for n, rule in ((11, H.RULE_VOIGT), (13, H.RULE_NONE), (65, H.RULE_TWO_LAYER), (143, H.RULE_REUSS))]
+    phases = H.two_phases(10.0)
+    E = np.eye(3)
+    mat, res, refs = _solve_both(cells, phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    eps = cell_fields(res, cells, 2, "eps")
+    for i, ref in enumerate(refs):
+        assert list(res["iterations"][i]) == list(ref["iterations"]), cells[i].n
+        C = hom.hom_effective_stiffness(E, res["mean_sigma"][i:i + 1], 2)[0]
+        assert _rel(C, O.effective_stiffness(ref["mean_sigma"], E)) < 1e-10
+        assert _rel(eps[i], ref["eps"]) < 1e-10
+    res32 = hom.hom_solve(mat, E, [H.mean_lame(phases)] * len(cells), precision=hom.HOM_FP32,
+                          criterion=hom.HOM_CRIT_EN, tol=1e-6, max_iter=3000, fields=False)
+    for i, cell in enumerate(cells):
+        ref = O.solve(O.filter_build(cell, phases)["ctilde"], 2, cell.n, *H.mean_lame(phases), E, tol=1e-9,
+                      max_iter=3000)
+        C = hom.hom_effective_stiffness(E, res32["mean_sigma"][i:i + 1], 2)[0]
+        assert _rel(C, O.effective_stiffness(ref["mean_sigma"], E)) < 1e-5, cell.n
+    cell = H.rsa_spheres_cell(39, seed=39, vf=0.2, rmin=0.1, rmax=0.15, subgrid=4, gap_voxels=1.0)
+    E = np.eye(6)[:2]
+    mat, res, refs = _solve_both([cell], phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    assert list(res["iterations"][0]) == list(refs[0]["iterations"])
+    assert _rel(res["mean_sigma"][0], refs[0]["mean_sigma"]) < 1e-10
+    assert _rel(cell_fields(res, [cell], 3, "eps")[0], refs[0]["eps"]) < 1e-10
+
+
 def test_uneven_batch_matches_per_cell_oracle():
     """Cells of different sizes, rules and contrasts in one launch sequence."""
     base = [H.centred_disk_cell(15, rule=H.RULE_VOIGT), H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER),
