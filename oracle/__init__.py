@@ -627,3 +627,93 @@ def exact_property(cell: Cell, values: Sequence[float], m: int) -> np.ndarray:
     grids = np.meshgrid(*([b] * cell.dim), indexing="ij")
     su = np.stack([2.0 * grids[cell.dim - 1 - c] + 1.0 for c in range(cell.dim)], axis=-1)
     return np.asarray(values, dtype=np.float64)[phase_at(cell, su, k)]
+
+
+# =============================================================================================
+# Conjugate gradients on the same discrete problem (an accelerated scheme of the kind the
+# paper's introduction and section 5 call complementary to filtering)
+
+
+def projection_G(f: np.ndarray, dim: int, n: int) -> np.ndarray:
+    """G f: the compatible, zero-mean part of a real Mandel field f [nc, *grid].  G is eq. (2)'s
+    Green operator for the reference medium c0 = identity (lam0 = 0, mu0 = 1/2), for which
+    Gamma0 : c0 = Gamma0 is the L2-orthogonal projection onto compatible zero-mean strain fields."""
+    return -np.real(_ifft(apply_gamma0(_fft(f, dim), dim, n, 0.0, 0.5), dim))
+
+
+def _dot(a: np.ndarray, b: np.ndarray) -> float:
+    """L2 inner product of two real Mandel fields (Mandel components make it the tensor product)."""
+    return math.fsum((a * b).ravel())
+
+
+def solve_cg_one(ctilde: np.ndarray, dim: int, n: int, E: np.ndarray, tol: float, max_iter: int,
+                 history: bool = False) -> Dict:
+    """Conjugate gradients for the strain eps = E + x, x compatible with zero mean, such that the
+    stress c : eps is in equilibrium, i.e. G(c : eps) = 0:
+        A x = b   with  A x = G(c : x),  b = -G(c : E)
+    A is symmetric positive definite on compatible zero-mean fields (G is an orthogonal projection,
+    c is symmetric positive definite at every grid point), so plain CG applies:
+        x = 0, r = b, p = r
+        repeat k = 0, 1, ...:
+            sigma = c : (E + x);  e_G = sqrt(<r, r> / N_v) / |<sigma>|;  stop if e_G < tol
+            q = A p;  alpha = <r, r> / <p, q>
+            x += alpha p;  r -= alpha q
+            beta = <r, r>_new / <r, r>_old;  p = r + beta p
+    r = -G sigma is the projected stress, so e_G lies between e_n and sqrt(2) e_n (per frequency,
+    |G s| ^2 = 2 |s n|^2 - (n.s n)^2 for the unit wave vector n).  iterations = CG steps taken."""
+    nc = nc_of(dim)
+    grid = (n,) * dim
+    nv = n ** dim
+    Ef = np.empty((nc,) + grid)
+    for I in range(nc):
+        Ef[I] = E[I]
+    x = np.zeros((nc,) + grid)
+    r = -projection_G(constitutive(ctilde, Ef), dim, n)
+    p = r.copy()
+    rr = _dot(r, r)
+    errs, res = [], []
+    status = "max_iter"
+    it = 0
+    while True:
+        sigma = constitutive(ctilde, Ef + x)
+        mean_sigma = np.array([math.fsum(sigma[I].ravel()) for I in range(nc)]) / nv
+        e_g = math.sqrt(rr / nv) / float(np.linalg.norm(mean_sigma))
+        errs.append(e_g)
+        if history:
+            res.append(r.copy())
+        if not math.isfinite(e_g):
+            status = "diverged"
+            break
+        if e_g < tol:
+            status = "converged"
+            break
+        if it >= max_iter:
+            break
+        q = projection_G(constitutive(ctilde, p), dim, n)
+        pq = _dot(p, q)
+        if not pq > 0.0:
+            status = "diverged"
+            break
+        alpha = rr / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = _dot(r, r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    out = dict(eps=Ef + x, sigma=sigma, mean_sigma=mean_sigma, iterations=it, status=status,
+               errors=np.array(errs))
+    if history:
+        out["residuals"] = res
+    return out
+
+
+def solve_cg(ctilde: np.ndarray, dim: int, n: int, E: np.ndarray, tol: float = 1e-8,
+             max_iter: int = 1000) -> Dict:
+    """solve_cg_one for every load case (rows of E, Mandel [L, nc])."""
+    E = np.atleast_2d(np.asarray(E, dtype=np.float64))
+    runs = [solve_cg_one(ctilde, dim, n, E[l], tol, max_iter) for l in range(E.shape[0])]
+    return dict(eps=np.stack([r["eps"] for r in runs]), sigma=np.stack([r["sigma"] for r in runs]),
+                mean_sigma=np.stack([r["mean_sigma"] for r in runs]),
+                iterations=np.array([r["iterations"] for r in runs]),
+                status=[r["status"] for r in runs], errors=[r["errors"] for r in runs])
