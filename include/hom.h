@@ -216,6 +216,23 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 
+/* Conjugate-gradient solution of the same discrete problem as hom_solve.  The paper's introduction
+ * and section 5 name Krylov schemes (its refs. [3, 12]) as complementary to filtering: they remove
+ * the basic scheme's sensitivity to c0 and sharply reduce its sensitivity to the contrast.
+ *   Same arguments as hom_solve without c0: the operator is eq. (2)'s Green operator for the
+ *   reference medium c0 = identity (lambda0 = 0, mu0 = 1/2), G, the L2-orthogonal projection onto
+ *   compatible zero-mean strain fields.  CG solves G(c~ : (E + x)) = 0 for compatible zero-mean x,
+ *   with A x = G(c~ : x) symmetric positive definite.  Each step costs one row and one Green pass
+ *   (the passes of hom_solve) plus five short kernels (two inner products, the updates, the control).
+ *   opts->tol bounds e_G = sqrt(<r, r> / N_v) / |<sigma>| with r = -G(sigma) the projected stress of
+ *   the current iterate; e_n <= e_G <= sqrt(2) e_n, so e_G is comparable to HOM_CRIT_EN (criterion
+ *   is ignored, diverge_window too).  out->err and out->err_n both receive e_G; out->iterations
+ *   counts CG steps (each one Green-operator application; the start adds one more).
+ *   HOM_STATUS_DIVERGED flags a breakdown (<p, A p> <= 0 or a non-finite value).
+ * Runs the generic passes (any supported grid, FP32 or FP64).  Synchronises the stream. */
+int hom_solve_cg(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
+                 const hom_solve_opts* opts, hom_result* out, void* stream);
+
 /* Reverse-mode derivative of a loss L(C_eff, sigma) through the fixed point (section 2, eqs. 1-a,
  * 1-b, 2) and the filter rules (eqs. 3, 4, 5-a, 5-b).  The paper does not differentiate its method;
  * this is the implicit (adjoint) derivative of the discrete problem it solves.

@@ -103,6 +103,9 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(hom_solve_opts), ctypes.POINTER(hom_result), ctypes.c_void_p]
         h.hom_solve_noalloc.argtypes = h.hom_solve.argtypes
+        h.hom_solve_cg.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(hom_solve_opts),
+                                   ctypes.POINTER(hom_result), ctypes.c_void_p]
         h.hom_solve_backward.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                          ctypes.POINTER(hom_solve_opts), ctypes.c_void_p, ctypes.c_void_p,
@@ -301,10 +304,15 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                           check_every=int(check_every), diverge_window=int(diverge_window),
                           use_graph=int(bool(use_graph)))
     with torch.cuda.device(device):
-        code = getattr(lib(), _entry)(material.marshalled.cells, ncells, ctypes.byref(material.struct),
-                               E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L,
-                               c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
-                               ctypes.byref(res), _stream_handle(stream))
+        if _entry == "hom_solve_cg":
+            code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
+                                      E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),
+                                      ctypes.byref(res), _stream_handle(stream))
+        else:
+            code = getattr(lib(), _entry)(material.marshalled.cells, ncells, ctypes.byref(material.struct),
+                                          E.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L,
+                                          c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                                          ctypes.byref(res), _stream_handle(stream))
     allowed = (HOM_OK, HOM_ERR_NOT_CONVERGED, HOM_ERR_DIVERGED) if allow_not_converged else (HOM_OK,)
     _check(code, allowed)
     out = dict(eps=eps, sigma=sig, mean_sigma=mean_sigma, iterations=iters, status=status, err=err,
@@ -314,6 +322,13 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                                               bytes=float(st.bytes[k])) for k in range(HOM_NKERNEL)}
         out["voxel_iterations"] = float(st.voxel_iterations)
     return out
+
+
+def hom_solve_cg(material: Material, E, **kw) -> dict:
+    """Conjugate-gradient solve of the same discrete problem (reference medium c0 = identity, the
+    projection G); see include/hom.h.  Keyword arguments as hom_solve (criterion and diverge_window
+    are ignored; err and err_n both hold e_G, which lies between e_n and sqrt(2) e_n)."""
+    return hom_solve(material, E, [0.0, 0.5], _entry="hom_solve_cg", **kw)
 
 
 def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_dsigma: Optional[torch.Tensor] = None,

@@ -72,7 +72,7 @@ struct AdjointSpec {
 // plans and workspace; adj = nullptr: forward solve).
 int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
                 const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
-                const ExternalWorkspace* ext, const AdjointSpec* adj = nullptr);
+                const ExternalWorkspace* ext, const AdjointSpec* adj = nullptr, bool cg = false);
 
 // ------------------------------------------------------------------ kernel descriptors
 struct FCell {           // one cell of the filter build

@@ -28,6 +28,7 @@
 #include "hom_plan.h"
 #include "hom_solve_args.cuh"
 #include "hom_fast2d.h"
+#include "hom_cg.cuh"
 
 namespace hom {
 namespace {
@@ -940,14 +941,35 @@ bool is_device_ptr(const void* p) {
 template <typename T, int DIM, int MAXR>
 int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L, const double* c0,
               const hom_solve_opts* opts, hom_result* out, cudaStream_t st, const ExternalWorkspace* ext,
-              const AdjointSpec* adj) {
+              const AdjointSpec* adj, bool cg) {
   using V = typename Cx<T>::V;
   const int nc = nc_of(DIM);
   Layout lay;
+  // Conjugate gradients run on the generic passes with the reference medium c0 = s I per cell, s the
+  // smallest eigenvalue of the cell's phase stiffnesses (isotropic: min(2 mu, dim lambda + 2 mu))
+  std::vector<double> c0_cg;
+  if (cg) {
+    const int ns = DIM == 2 ? 6 : 21;
+    std::vector<double> ph((size_t)mat->nphase * ns);
+    HOM_CUDA_TRY(cudaMemcpy(ph.data(), mat->phase_c64, ph.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    auto smin = [&](int q) {
+      const double lam = ph[(size_t)q * ns + 1], mu2 = ph[(size_t)q * ns] - lam;
+      return std::min(mu2, DIM * lam + mu2);
+    };
+    c0_cg.resize(2 * (size_t)ncells);
+    for (int i = 0; i < ncells; ++i) {
+      double sm = smin(cells[i].matrix_phase);
+      for (int q = 0; q < cells[i].nprim; ++q) sm = std::min(sm, smin(cells[i].prims[q].phase));
+      if (!(sm > 0.0)) return set_error(HOM_ERR_INVALID_ARG, "hom_solve_cg: cell %d has a phase that is not positive definite", i);
+      c0_cg[2 * i] = 0.0;
+      c0_cg[2 * i + 1] = 0.5 * sm;
+    }
+    c0 = c0_cg.data();
+  }
   {
     const char* fe = std::getenv("HOM_FAST2D");
     // HOM_FAST2D=0: generic passes everywhere; HOM_FAST2D=2: generic passes for 3D only
-    lay.fast = std::is_same<T, float>::value && !ext && !adj && !(fe && fe[0] == '0') &&
+    lay.fast = std::is_same<T, float>::value && !ext && !adj && !cg && !(fe && fe[0] == '0') &&
                !(DIM == 3 && fe && fe[0] == '2');
   }
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
@@ -977,6 +999,15 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_dbl = take((size_t)npairs * (3 + nc) * sizeof(double));
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
+  int cg_nchunk = 1;
+  for (const CellDev& c : lay.cells)
+    cg_nchunk = std::max(cg_nchunk, (c.nrows + cg_rows_per_cta(c.Hp, nc) - 1) / cg_rows_per_cta(c.Hp, nc));
+  if (cg && cg_nchunk > 65535) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "hom_solve_cg: cell too large");
+  const size_t o_cgx = cg ? take(lay.ws_elems * sizeof(V)) : 0, o_cgr = cg ? take(lay.ws_elems * sizeof(V)) : 0;
+  const size_t o_cgpart = cg ? take((size_t)npairs * cg_nchunk * sizeof(double)) : 0;
+  const size_t o_cgsc = cg ? take((size_t)npairs * (3 + nc) * sizeof(double)) : 0;
+  const size_t o_cgint = cg ? take((size_t)npairs * 2 * sizeof(int)) : 0;
+  const size_t o_E0 = cg ? take((size_t)npairs * nc * sizeof(double)) : 0;
   long long nv_all = 0, nv_max = 0;
   for (CellDev& c : lay.cells) {
     c.lp_off = nv_all;  // one-byte labels, rows padded to 16 bytes
@@ -1054,6 +1085,10 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_eps0, 0, lay.ws_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_g, 0, lay.g_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_bytes, 0, HOM_NKERNEL * sizeof(unsigned long long), st));
+  if (cg) {
+    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_E0, 0, (size_t)npairs * nc * sizeof(double), st));
+    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_cgint, 0, (size_t)npairs * 2 * sizeof(int), st));
+  }
 
   SolveArgs A{};
   A.cells = reinterpret_cast<const CellDev*>(ws + o_cells);
@@ -1101,6 +1136,21 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
   A.cell_phases = lay.fast ? reinterpret_cast<const int*>(ws + o_cphase) : nullptr;
+  CgArgs G{};
+  if (cg) {
+    G.x = ws + o_cgx;
+    G.r = ws + o_cgr;
+    G.part = reinterpret_cast<double*>(ws + o_cgpart);
+    double* sc = reinterpret_cast<double*>(ws + o_cgsc);
+    G.rr = sc;
+    G.alpha = sc + npairs;
+    G.beta = sc + 2 * (size_t)npairs;
+    G.ssum = sc + 3 * (size_t)npairs;
+    G.vmode = reinterpret_cast<int*>(ws + o_cgint);
+    G.steps = G.vmode + npairs;
+    G.E = A.E;
+    G.nchunk = cg_nchunk;
+  }
   const size_t smem_frow =
       !lay.fast ? 0 : DIM == 2 ? fast2d_smem_row(lay.fast_nmax, nph_max) : fast3d_smem_row(lay.fast_nmax, nph_max);
   const size_t smem_fgreen =
@@ -1135,7 +1185,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const int check = opts->check_every > 0 ? opts->check_every : 8;
   int host_nactive = npairs;
   int launched = 0;
-  auto one_iteration = [&]() {
+  const dim3 cg_grid((unsigned)npairs, (unsigned)cg_nchunk);
+  auto one_pass = [&]() {
     tm.begin(HOM_K_ROW);
     if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, false, st);
     else if (lay.fast) fast2d_row(A, nR, smem_frow, st);
@@ -1158,16 +1209,40 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
       else k_ypass<T, false, MAXR><<<nY, kThreads, lay.smem_y, st>>>(A);
       tm.end();
     }
+  };
+  auto one_iteration = [&]() {
+    one_pass();
     tm.begin(HOM_K_CONTROL);
-    k_control<<<nCtl, kCtlThreads, 0, st>>>(A, nc);
+    if (cg) {
+      k_cg_elems<T, DIM, kCgPq><<<cg_grid, kCgThreads, 0, st>>>(A, G);
+      k_cg_control<kCgPq><<<nCtl, kCgCtlThreads, 0, st>>>(A, G, nc);
+      k_cg_elems<T, DIM, kCgUpdate><<<cg_grid, kCgThreads, 0, st>>>(A, G);
+      k_cg_control<kCgUpdate><<<nCtl, kCgCtlThreads, 0, st>>>(A, G, nc);
+      k_cg_elems<T, DIM, kCgDir><<<cg_grid, kCgThreads, 0, st>>>(A, G);
+    } else {
+      k_control<<<nCtl, kCtlThreads, 0, st>>>(A, nc);
+    }
     tm.end();
   };
+  if (cg) {
+    // start: the passes on the uniform field E with zero mean strain give the first residual
+    A.E = reinterpret_cast<const double*>(ws + o_E0);
+    one_pass();
+    tm.begin(HOM_K_CONTROL);
+    k_cg_elems<T, DIM, kCgStart><<<cg_grid, kCgThreads, 0, st>>>(A, G);
+    k_cg_control<kCgStart><<<nCtl, kCgCtlThreads, 0, st>>>(A, G, nc);
+    tm.end();
+    HOM_CUDA_TRY(cudaGetLastError());
+    HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   // Graphs are captured on a private stream (the legacy default stream cannot be captured) and
   // launched on the caller's stream.
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t cap_stream = nullptr;
   while (host_nactive > 0) {
-    const int remaining = opts->max_iter + 1 - launched;
+    // CG: a verification pass takes a launch without a step, and is followed by a step or a stop
+    const int remaining = (cg ? 2 * opts->max_iter + 2 : opts->max_iter + 1) - launched;
     if (remaining <= 0) break;  // the control kernel has stopped every pair by now
     const int k = std::min(check, remaining);
     if (opts->use_graph && !out->stats) {
@@ -1200,6 +1275,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   if (gexec) cudaGraphExecDestroy(gexec);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (host_nactive > 0) return set_error(HOM_ERR_TIMEOUT, "iteration control did not terminate");
+  if (cg) {
+    // the returned iterate E + x, in the buffer the output pass reads for each pair
+    k_cg_elems<T, DIM, kCgFinal><<<cg_grid, kCgThreads, 0, st>>>(A, G);
+    HOM_CUDA_TRY(cudaGetLastError());
+  }
 
   if (want_fields) {
     tm.begin(HOM_K_OUTPUT);
@@ -1253,7 +1333,7 @@ namespace hom {
 
 int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L,
                 const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream,
-                const ExternalWorkspace* ext, const AdjointSpec* adj) {
+                const ExternalWorkspace* ext, const AdjointSpec* adj, bool cg) {
   if (!cells || ncells <= 0 || !mat || !E || !c0 || !opts || !out || !out->mean_sigma)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: null or empty argument");
   if (L < 1 || L > kMaxLoads) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: L must be in [1, %d]", kMaxLoads);
@@ -1283,16 +1363,16 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   const int r32 = env ? std::atoi(env) : 27;
   if (opts->precision == HOM_FP32) {
     if (r32 >= 45)
-      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
-                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
+      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
+                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
     if (r32 <= 15)
-      return dim == 2 ? run_solve<float, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
-                      : run_solve<float, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
-    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
-                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
+      return dim == 2 ? run_solve<float, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
+                      : run_solve<float, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
+    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
+                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
   }
-  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj)
-                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj);
+  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
+                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
 }
 
 }  // namespace hom
@@ -1300,4 +1380,11 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
 extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                          const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
   return solve_entry(cells, ncells, mat, E, L, c0, opts, out, stream, nullptr);
+}
+
+extern "C" int hom_solve_cg(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E,
+                            int32_t L, const hom_solve_opts* opts, hom_result* out, void* stream) {
+  if (!cells || ncells <= 0) return set_error(HOM_ERR_INVALID_ARG, "hom_solve_cg: null or empty argument");
+  std::vector<double> c0(2 * (size_t)ncells, 0.5);  // validated only; the solve uses c0 = identity
+  return solve_entry(cells, ncells, mat, E, L, c0.data(), opts, out, stream, nullptr, nullptr, true);
 }
