@@ -543,10 +543,28 @@ def profile_case3d(args):
     print("profile case 3d: one cell of n=%d, %d iterations, status %s" % (n, args.iters, r["status"].ravel().tolist()))
 
 
+def profile_cg(args):
+    """Small fixed case for ncu captures of the conjugate-gradient path: one n^2 Voigt disk
+    (n = --profile-n, radius pi/15, contrast 1e3), 3 loads, FP64, exactly `args.iters` CG steps
+    (n = 1215: each mixed-domain field is 106 MB, above L2; about 0.7 GB on the device)."""
+    import torch
+
+    import paper_1412_3228_gb300 as hom
+    from paper_1412_3228_gb300 import _build_lib
+    _build_lib.build()
+    torch.cuda.set_device(0)
+    cell = H.centred_disk_cell(args.profile_n, rule=H.RULE_VOIGT, radius=math.pi / 15)
+    mat = hom.hom_filter_build([cell], H.two_phases(1e3))
+    r = hom.hom_solve_cg(mat, np.eye(3), precision=hom.HOM_FP64, tol=1e-30, max_iter=args.iters, fields=False)
+    torch.cuda.synchronize()
+    print("profile cg: one %d^2 cell, %d CG steps, status %s" % (args.profile_n, args.iters, r["status"].ravel().tolist()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-case", action="store_true", help="run only the small fixed ncu case")
     ap.add_argument("--profile-case3d", action="store_true", help="run only the small fixed 3D ncu case")
+    ap.add_argument("--profile-cg", action="store_true", help="run only the small fixed conjugate-gradient ncu case")
     ap.add_argument("--profile-n", type=int, default=1215)
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--fp64-case", action="store_true")
@@ -565,6 +583,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.profile_case:
         profile_case(args)
+        return
+    if args.profile_cg:
+        profile_cg(args)
         return
     if args.profile_case3d:
         profile_case3d(args)

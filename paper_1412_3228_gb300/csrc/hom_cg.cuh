@@ -65,6 +65,25 @@ enum CgStage { kCgStart = 0, kCgPq = 1, kCgUpdate = 2, kCgDir = 3, kCgFinal = 4 
 //   kCgDir:    vmode 0 or 2: p = r + beta p;  vmode 1: E + x (the verification input)
 //              (runs after the control advanced the iteration counter)
 //   kCgFinal:  eps[iters & 1] = E + x for the output pass (every pair)
+// Divider by d for Iter2 (computed once per CTA: one 64-bit division).
+__device__ __forceinline__ FastDiv make_fastdiv_dev(int d) {
+  FastDiv f;
+  f.d = d;
+  f.m = d <= 1 ? 0u : (unsigned)((((unsigned long long)1 << 32) + (unsigned)d - 1) / (unsigned)d);
+  return f;
+}
+
+// Running sum of the element kernels: Kahan-compensated in FP32; plain in FP64 (at most a few
+// dozen terms per thread, and FP64 arithmetic is scarce on this GPU).
+template <typename T> struct CgSum {
+  Acc<T> a;
+  __device__ __forceinline__ void add(T x) { a.add(x); }
+};
+template <> struct CgSum<double> {
+  Acc<double> a;
+  __device__ __forceinline__ void add(double x) { a.s += x; }
+};
+
 template <typename T, int DIM, int STAGE>
 __global__ void __launch_bounds__(kCgThreads) k_cg_elems(SolveArgs A, CgArgs G) {
   using V = typename Cx<T>::V;
@@ -86,7 +105,6 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_elems(SolveArgs A, CgArgs G) 
   }
   const int nrow = min(rpc, c.nrows - row0);
   const size_t base = c.ws_off + ((size_t)pr.load * c.nrows + row0) * rowlen;
-  const int count = nrow * rowlen;
   // kCgDir runs after the counter advanced: the old p is in eps[(it + 1) & 1], the output goes to
   // eps[it & 1]; every other stage reads p from eps[it & 1] and the pass output p' from eps[(it + 1) & 1]
   const V* pv = static_cast<const V*>(A.eps[STAGE == kCgDir ? ((it + 1) & 1) : (it & 1)]) + base;
@@ -94,65 +112,73 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_elems(SolveArgs A, CgArgs G) 
   V* xv = static_cast<V*>(G.x) + base;
   V* rv = static_cast<V*>(G.r) + base;
   const T sc = (T)(2.0 * c.mu0);  // s of the reference medium c0 = s I
+  // the update folds s into the step: r -= (alpha s) (p - p')
   const T a = STAGE == kCgUpdate ? (T)G.alpha[pair] : T(0);
+  const T as = STAGE == kCgUpdate ? (T)(G.alpha[pair] * 2.0 * c.mu0) : T(0);
   const T b = STAGE == kCgDir ? (T)G.beta[pair] : T(0);
   V* outp = static_cast<V*>(A.eps[STAGE == kCgFinal ? (A.iters[pair] & 1) : STAGE == kCgStart ? ((it + 1) & 1) : (it & 1)]) +
             base;
   const double* Eld = G.E + (size_t)pair * NC;
   const bool write_state = STAGE == kCgFinal || (STAGE == kCgDir && vm == 1);
-  Acc<T> acc;
   const V zero = mk(T(0), T(0));
-  for (int f = threadIdx.x; f < count; f += kCgThreads) {
-    const int j = f % rowlen;  // position in the row: kx * NC + component
-    const int kx = j / NC;
-    if (kx >= c.H) {  // row padding: never read by the passes; kept at zero in the CG fields
+  // Sums over the row positions: kx = 0 entries count once, 0 < kx < H twice (Parseval for the
+  // half spectrum), padding kx >= H not at all; kept as sum_all and sum_kx0 (total = 2 all - kx0).
+  CgSum<T> acc_all, acc_0;
+  // (row, position) pairs enumerated with carries (no division per element)
+  const FastDiv drow = make_fastdiv_dev(rowlen);
+  for (Iter2 e(threadIdx.x, kCgThreads, drow); e.a < nrow; e.next()) {
+    const int j = e.b;                           // position in the row: kx * NC + component
+    const size_t f = (size_t)e.a * rowlen + j;
+    if (j >= c.H * NC) {  // row padding: never read by the passes; kept at zero in the CG fields
       if (STAGE == kCgStart) { rv[f] = zero; xv[f] = zero; outp[f] = zero; }
       else if (STAGE == kCgDir || STAGE == kCgFinal) outp[f] = zero;
       continue;
     }
-    const T w = kx == 0 ? T(1) : T(2);
+    T term = T(0);
     if (STAGE == kCgStart) {
       const V pp = fv[f];
       const V r = mk(sc * pp.x, sc * pp.y);
       rv[f] = r;
       outp[f] = r;  // p = r, in the buffer the next row pass reads
       xv[f] = zero;
-      acc.add(w * (r.x * r.x + r.y * r.y));
+      term = r.x * r.x + r.y * r.y;
     } else if (STAGE == kCgPq) {
       const V pp = fv[f];
       if (vm == 1) {  // true residual of E + x
         const V x = xv[f];
         const V r = mk(sc * (pp.x - x.x), sc * (pp.y - x.y));
         rv[f] = r;
-        acc.add(w * (r.x * r.x + r.y * r.y));
-      } else {
+        term = r.x * r.x + r.y * r.y;
+      } else {  // <p, p - p'> (times s in the control)
         const V p = pv[f];
-        const V q = mk(sc * (p.x - pp.x), sc * (p.y - pp.y));
-        acc.add(w * (p.x * q.x + p.y * q.y));
+        term = p.x * (p.x - pp.x) + p.y * (p.y - pp.y);
       }
     } else if (STAGE == kCgUpdate) {
       const V p = pv[f], pp = fv[f];
-      const V q = mk(sc * (p.x - pp.x), sc * (p.y - pp.y));
       V x = xv[f], r = rv[f];
       x = mk(x.x + a * p.x, x.y + a * p.y);
-      r = mk(r.x - a * q.x, r.y - a * q.y);
+      r = mk(r.x - as * (p.x - pp.x), r.y - as * (p.y - pp.y));
       xv[f] = x;
       rv[f] = r;
-      acc.add(w * (r.x * r.x + r.y * r.y));
+      term = r.x * r.x + r.y * r.y;
     } else if (!write_state) {  // kCgDir, vmode 0 or 2
       const V p = pv[f], r = rv[f];
       outp[f] = mk(r.x + b * p.x, r.y + b * p.y);
     } else {  // E + x
       V x = xv[f];
-      if (kx == 0) x.x += (T)Eld[j];
+      if (j < NC) x.x += (T)Eld[j];
       outp[f] = x;
+    }
+    if (STAGE != kCgDir && STAGE != kCgFinal) {
+      acc_all.add(term);
+      if (j < NC) acc_0.add(term);
     }
   }
   if (STAGE == kCgDir || STAGE == kCgFinal) return;
-  const Acc<T> vv[1] = {acc};
-  double tot[1];
-  block_sum<T, 1, kCgThreads>(vv, tot);
-  if (threadIdx.x == 0) *part = tot[0];
+  const Acc<T> vv[2] = {acc_all.a, acc_0.a};
+  double tot[2];
+  block_sum<T, 2, kCgThreads>(vv, tot);
+  if (threadIdx.x == 0) *part = (2.0 * tot[0] - tot[1]) * (STAGE == kCgPq && vm != 1 ? (double)sc : 1.0);
 }
 
 // Per-pair control, one CTA per pair (fixed-order FP64 sums: deterministic).
