@@ -18,7 +18,8 @@ What it computes, in the paper's order:
   * the stress-equilibrium stopping criterion of Moulinec & Suquet (ref. [9] of the paper).
 
 Readings where the paper is silent or garbled (each is listed in the design notes):
-  * J is the integer range -(N-1)/2 .. (N-1)/2 per axis (odd N only);
+  * J is the integer range -(N-1)/2 .. (N-1)/2 per axis for odd N; on even grids (which the paper
+    does not define) the Nyquist bins get zero strain and are left out of the equilibrium errors;
   * grid points are voxel centres x_a = (a + 1/2) h, h = 1/N, cell side 1;
   * eq. (5-b) reads f1 sigma1^P + f2 sigma2^P = sigma^P and f1 eps1^OP + f2 eps2^OP = eps^OP;
   * 2D is plane strain, all rules act on the 3x3 in-plane Mandel matrices;
@@ -130,11 +131,26 @@ def rotate_tensor4(C: np.ndarray, R: np.ndarray) -> np.ndarray:
 
 
 def signed_frequencies(n: int) -> np.ndarray:
-    """DFT bin m -> signed frequency a in J = {-(n-1)/2, ..., (n-1)/2} (odd n)."""
-    if n % 2 == 0:
-        raise ValueError("the truncated frequency set J is defined for odd grids only")
+    """DFT bin m -> signed frequency a: J = {-(n-1)/2, ..., (n-1)/2} for odd n (section 2).  The
+    paper defines J for odd grids only; for even n the bins run -n/2+1 ... n/2, the last being the
+    Nyquist frequency, which `nyquist_mask` singles out."""
     m = np.arange(n)
-    return np.where(m <= (n - 1) // 2, m, m - n)
+    return np.where(m <= n // 2, m, m - n)
+
+
+def nyquist_mask(dim: int, n: int) -> np.ndarray:
+    """[*grid] True at the DFT bins with a Nyquist component (bin n/2 along some axis) of an even
+    grid; all False for odd n.  A real field's spectrum has no conjugate partner there, so on even
+    grids the Green operator gives zero strain at those bins and the equilibrium errors leave them
+    out (a reading: the paper does not define even grids)."""
+    if n % 2:
+        return np.zeros((n,) * dim, dtype=bool)
+    nyq = np.arange(n) == n // 2
+    grids = np.meshgrid(*([nyq] * dim), indexing="ij")
+    out = grids[0].copy()
+    for g in grids[1:]:
+        out |= g
+    return out
 
 
 def wave_vectors(dim: int, n: int) -> np.ndarray:
@@ -180,6 +196,7 @@ def apply_gamma0(tau_hat: np.ndarray, dim: int, n: int, lam0: float, mu0: float,
             continue
         G = gamma0_tensor(x[nz], lam0, mu0)
         out[s:e][nz] = -np.einsum("pkhij,pij->pkh", G, t[s:e][nz])
+    out[nyquist_mask(dim, n).reshape(npts)] = 0.0  # even grids only
     v = tensor2_to_mandel(out, dim)  # [npts, nc]
     return np.moveaxis(v, -1, 0).reshape((nc,) + shape)
 
@@ -216,6 +233,7 @@ def equilibrium_errors(sig_hat: np.ndarray, dim: int, n: int) -> Tuple[float, fl
     div = np.einsum("pij,pj->pi", t, xi)
     q2 = np.sum(xi * xi, axis=-1)
     d2 = np.sum(np.abs(div) ** 2, axis=-1)
+    d2[nyquist_mask(dim, n).reshape(npts)] = 0.0  # even grids: Nyquist bins left out
     nz = q2 > 0
     den = math.sqrt(float(np.sum(np.abs(t[0]) ** 2)))  # k = 0 is the first bin
     e = math.sqrt(float(np.sum(d2))) / den
@@ -606,6 +624,8 @@ def fourier_extrapolate(field: np.ndarray, dim: int, n: int, m: int) -> np.ndarr
     the shift making f(x_a) reproduce the field's value at x_a.  field: [(n,) n, n] (numpy axis
     order (z,) y, x).  Returns [(m,) m, m] float64 (J is symmetric for odd n, so the series is
     real; the imaginary part of the sum is rounding and is dropped)."""
+    if n % 2 == 0:
+        raise ValueError("the truncated series on J is real for odd grids only")
     fh = _fft(np.asarray(field, dtype=np.float64).reshape((n,) * dim), dim)
     k = signed_frequencies(n)
     y = (np.arange(m) + 0.5) / m

@@ -33,14 +33,18 @@ def test_naive_dft_matches_fft_nd(shape):
     assert abs(np.sum(np.abs(X) ** 2) / x.size - np.sum(x ** 2)) < 1e-9 * np.sum(x ** 2)
 
 
-def test_signed_frequencies_odd_only():
+def test_signed_frequencies():
     for n in [3, 5, 45, 1215]:
         a = O.signed_frequencies(n)
         assert sorted(a.tolist()) == list(range(-(n - 1) // 2, (n - 1) // 2 + 1))
         # bin m and bin n-m are opposite frequencies (conjugate pairs)
         assert np.all(a[1:] == -a[1:][::-1])
-    with pytest.raises(ValueError):
-        O.signed_frequencies(8)
+        assert not O.nyquist_mask(2, n).any()
+    for n in [4, 8, 30]:
+        a = O.signed_frequencies(n)
+        assert sorted(a.tolist()) == list(range(-n // 2 + 1, n // 2 + 1))
+        m = O.nyquist_mask(2, n)
+        assert m.sum() == 2 * n - 1 and m[n // 2, 0] and m[0, n // 2] and not m[1, 1]
 
 
 @pytest.mark.parametrize("dim", [2, 3])
