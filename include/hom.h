@@ -15,8 +15,10 @@
  *   4. the adjoint (reverse-mode) derivative of a loss on C_eff and on the local stresses.
  *
  * Conventions shared by every call
- *   - Grids are odd, n voxels per side, n = 3^a 5^b 7^c 11^d 13^e, 3 <= n <= 2187.  The cell side is 1 and
- *     the grid points are voxel centres x_a = (a + 1/2)/n.
+ *   - Grids have n voxels per side, n = 2^f 3^a 5^b 7^c 11^d 13^e, 3 <= n <= 2187.  The cell side is 1 and
+ *     the grid points are voxel centres x_a = (a + 1/2)/n.  The paper's frequency set J is defined
+ *     for odd n (section 2).  On even grids a wave vector with a Nyquist component (n/2) gets zero
+ *     strain from the Green operator and is left out of the equilibrium errors.
  *   - Strains, stresses and stiffnesses use Mandel notation: 2D (plane strain) vectors hold
  *     (11, 22, sqrt2*12), nc = 3; 3D vectors hold (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12),
  *     nc = 6.  A stiffness is an nc x nc symmetric matrix stored "packed": its upper triangle
@@ -46,7 +48,7 @@ extern "C" {
 /* ------------------------------------------------------------------ status codes */
 #define HOM_OK 0
 #define HOM_ERR_INVALID_ARG 1       /* a pointer, size or option is invalid                   */
-#define HOM_ERR_UNSUPPORTED_SIZE 2  /* even n, a prime factor above 13, n too large           */
+#define HOM_ERR_UNSUPPORTED_SIZE 2  /* a prime factor above 13, n too large                      */
 #define HOM_ERR_NOT_CONVERGED 3     /* some load case hit max_iter; every output is still set  */
 #define HOM_ERR_DIVERGED 4          /* some load case diverged (non-finite or growing error)  */
 #define HOM_ERR_TIMEOUT 5           /* a device-side wait ran out of its budget               */
@@ -98,7 +100,7 @@ typedef struct hom_primitive {
  * and a fine point is inside the ball of voxel a when its distance to x_a is <= radius_px / n. */
 typedef struct hom_cell {
   int32_t dim;          /* 2 or 3                                                 */
-  int32_t n;            /* voxels per side (odd, 3^a 5^b 7^c 11^d 13^e)           */
+  int32_t n;            /* voxels per side (2^f 3^a 5^b 7^c 11^d 13^e)           */
   int32_t matrix_phase; /* phase of points outside every primitive                */
   int32_t rule;         /* HOM_RULE_*                                             */
   double radius_px;     /* filter radius in voxel units, 0 < radius_px <= (n-1)/2 */
@@ -297,6 +299,7 @@ int hom_solve_noalloc(const hom_cell* cells, int32_t ncells, const hom_material*
  *   cells/ncells  the batch given to hom_filter_build, mat its material
  *   cell          index of the cell to extrapolate
  *   comp          packed component of c~ (upper triangle row by row: 0 = c~_11, 1 = c~_12, ...)
+ *   (odd grids only: J is symmetric there, so the series is real)
  *   m             fine points per side, 1 <= m <= 32768 in 2D, <= 1024 in 3D (m < n samples the
  *                 series more coarsely than the grid; m = n returns c~(x_a) itself)
  *   out           host or device [(m,) m, m] float64, x fastest; caller-owned

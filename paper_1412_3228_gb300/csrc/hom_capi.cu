@@ -62,7 +62,7 @@ int get_plan(int n, int max_radix, Plan* out) {
   }
   HostPlan hp;
   if (!build_host_plan(n, hp, max_radix) || (int)hp.radix.size() > kMaxStages)
-    return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7, 11, 13", n);
+    return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d has a prime factor above 13", n);
   std::vector<unsigned char> host(plan_table_bytes(n), 0);
   fill_plan_tables(hp, host.data());
   DevicePlan dp;

@@ -68,6 +68,13 @@ HOM_HD void dft3(V* v) {
 }
 
 template <bool FWD, typename V, typename T>
+HOM_HD void dft2(V* v) {
+  const V s = v[0] + v[1];
+  v[1] = v[0] - v[1];
+  v[0] = s;
+}
+
+template <bool FWD, typename V, typename T>
 HOM_HD void dft5(V* v) {
   const T c1 = T(0.309016994374947424102293417183), c2 = T(-0.809016994374947424102293417183);
   const T s1 = T(0.951056516295153572116439333379), s2 = T(0.587785252292473129168705954639);
@@ -147,9 +154,10 @@ HOM_HD void dft_prime(V* v) {
 // out in a fixed, compile-time order: X[k] is left in v[out_pos<R>(k)].  Prime radices keep the
 // natural order.
 template <int R> HOM_HD constexpr int split_a() {  // R = A * B with A the first factor
-  return R == 9 ? 3 : R == 15 ? 3 : R == 21 ? 3 : R == 25 ? 5 : R == 27 ? 3 : R == 35 ? 5 : R == 45 ? 5 : R == 49 ? 7 : 1;
+  return R == 4 ? 2 : R == 8 ? 2 : R == 16 ? 4 : R == 9 ? 3 : R == 15 ? 3 : R == 21 ? 3 : R == 25 ? 5 : R == 27 ? 3 :
+         R == 35 ? 5 : R == 45 ? 5 : R == 49 ? 7 : 1;
 }
-template <int R> HOM_HD constexpr bool is_prime_radix() { return R == 3 || R == 5 || R == 7 || R == 11 || R == 13; }
+template <int R> HOM_HD constexpr bool is_prime_radix() { return R == 2 || R == 3 || R == 5 || R == 7 || R == 11 || R == 13; }
 
 template <int R> HOM_HD constexpr int out_pos(int k) {
   if constexpr (is_prime_radix<R>()) {
@@ -193,7 +201,8 @@ HOM_HD void dft_composite(V* v) {
 
 template <int R, bool FWD, typename V, typename T>
 HOM_HD void dft_small(V* v) {
-  if constexpr (R == 3) dft3<FWD, V, T>(v);
+  if constexpr (R == 2) dft2<FWD, V, T>(v);
+  else if constexpr (R == 3) dft3<FWD, V, T>(v);
   else if constexpr (R == 5) dft5<FWD, V, T>(v);
   else if constexpr (R == 7) dft7<FWD, V, T>(v);
   else if constexpr (R == 11 || R == 13) dft_prime<R, FWD, V, T>(v);
@@ -248,7 +257,7 @@ struct Plan {
   int span[kMaxStages];   // L_s = radix[0] * ... * radix[s-1]
   FastDiv div_nb[kMaxStages];  // n / radix[s] (butterflies per line)
   FastDiv div_L[kMaxStages];   // span[s]
-  FastDiv div_n, div_h;        // n and (n + 1) / 2
+  FastDiv div_n, div_h;        // n and n / 2 + 1 (the half spectrum of a real line)
   const uint16_t* perm;   // perm[k] = position of index k in the digit-reversed layout
   const float2* tw32;     // exp(-2 pi i t / n), t < n
   const double2* tw64;
@@ -263,7 +272,7 @@ inline void plan_dividers(Plan& p) {
     p.div_L[s] = make_fastdiv(p.span[s]);
   }
   p.div_n = make_fastdiv(p.n);
-  p.div_h = make_fastdiv((p.n + 1) / 2);
+  p.div_h = make_fastdiv(p.n / 2 + 1);
 }
 
 template <typename V> HOM_HD const V* twiddles(const Plan& p);
@@ -359,13 +368,17 @@ HOM_HD void dif_stage(V* s, int nl, int ls, int n, int L, const V* tw, int tid, 
 // register footprint of a kernel is set by its largest radix).
 #define HOM_RADIX_CASES(STAGE)                                              \
   switch (r) {                                                              \
+    case 2: STAGE(2); break;                                                \
     case 3: STAGE(3); break;                                                \
+    case 4: STAGE(4); break;                                                \
     case 5: STAGE(5); break;                                                \
     case 7: STAGE(7); break;                                                \
+    case 8: STAGE(8); break;                                                \
     case 9: if constexpr (MAXR >= 9) STAGE(9); break;                       \
     case 11: if constexpr (MAXR >= 11) STAGE(11); break;                    \
     case 13: if constexpr (MAXR >= 13) STAGE(13); break;                    \
     case 15: if constexpr (MAXR >= 15) STAGE(15); break;                    \
+    case 16: if constexpr (MAXR >= 16) STAGE(16); break;                    \
     case 21: if constexpr (MAXR >= 21) STAGE(21); break;                    \
     case 25: if constexpr (MAXR >= 25) STAGE(25); break;                    \
     case 27: if constexpr (MAXR >= 27) STAGE(27); break;                    \

@@ -85,7 +85,8 @@ extern "C" int hom_fourier_extrapolate(const hom_cell* cells, int32_t ncells, co
     if (c < cell) off += dim == 2 ? (int64_t)cells[c].n * cells[c].n : (int64_t)cells[c].n * cells[c].n * cells[c].n;
   }
   const int n = cells[cell].n;
-  if (!grid_supported(n)) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "cell %d: unsupported grid %d", cell, n);
+  if (!grid_supported(n) || (n & 1) == 0)  // J is symmetric (a real series) for odd grids only
+    return set_error(HOM_ERR_UNSUPPORTED_SIZE, "cell %d: grid %d is not an odd supported size", cell, n);
   const int ns = dim == 2 ? 6 : 21;
   if (comp < 0 || comp >= ns)
     return set_error(HOM_ERR_INVALID_ARG, "hom_fourier_extrapolate: component %d out of range [0, %d)", comp, ns);

@@ -21,15 +21,15 @@ struct HostPlan {
   std::vector<double> xi;       // 2 pi a(k), a(k) the signed frequency of DFT bin k
 };
 
-// Factor n into the register radices {3, 5, 7, 9, 11, 13, 15, 21, 25, 27, 35, 45, 49} (each at
-// most `max_radix`) with the fewest stages, then the smallest largest radix.  Returns false if n
-// has a prime factor other than 3, 5, 7, 11, 13.
+// Factor n into the register radices {2, 3, 4, 5, 7, 8, 9, 11, 13, 15, 16, 21, 25, 27, 35, 45, 49}
+// (each at most `max_radix`) with the fewest stages, then the smallest largest radix.  Returns
+// false if n has a prime factor other than 2, 3, 5, 7, 11, 13.
 inline bool factorize(int n, std::vector<int>& radix, int max_radix = 45) {
-  static const int kRadices[] = {45, 35, 27, 25, 21, 15, 13, 11, 9, 7, 5, 3, 49};
+  static const int kRadices[] = {45, 35, 27, 25, 21, 16, 15, 13, 11, 9, 8, 7, 5, 4, 3, 2, 49};
   radix.clear();
-  if (n < 3 || (n % 2) == 0) return false;
+  if (n < 3) return false;
   int m = n;
-  for (int r : {3, 5, 7, 11, 13})
+  for (int r : {2, 3, 5, 7, 11, 13})
     while (m % r == 0) m /= r;
   if (m != 1) return false;
   std::vector<int> best, cur;
@@ -80,7 +80,8 @@ inline bool build_host_plan_radices(int n, const std::vector<int>& radix, HostPl
     p.perm[k] = (uint16_t)pos;
   }
   p.xi.assign(n, 0.0);
-  for (int k = 0; k < n; ++k) p.xi[k] = 6.28318530717958647692528676656 * (double)(k <= (n - 1) / 2 ? k : k - n);
+  // signed frequency of bin k: k up to n / 2 (the Nyquist bin of an even grid counts as +n/2), else k - n
+  for (int k = 0; k < n; ++k) p.xi[k] = 6.28318530717958647692528676656 * (double)(k <= n / 2 ? k : k - n);
   p.tw.assign(2 * (size_t)n, 0.0);
   const double two_pi = 6.28318530717958647692528676656;
   for (int t = 0; t < n; ++t) {

@@ -391,9 +391,12 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       xi[DIM - 1] = xi_tab[kk];
     }
     const bool k0 = kx == 0 && kk == 0 && (DIM == 2 || t.fixed == 0);
-    if (k0) {
+    // even grids: a wave vector with a Nyquist component (n/2) has no conjugate partner in the
+    // spectrum of a real field; its strain is set to zero and it is left out of the residual
+    const bool nyq = (n & 1) == 0 && (kx == (n >> 1) || kk == (n >> 1) || (DIM == 3 && t.fixed == (n >> 1)));
+    if (k0 || nyq) {
 #pragma unroll
-      for (int k = 0; k < NC; ++k) *tv[k] = mk((T)Eld[k], T(0));
+      for (int k = 0; k < NC; ++k) *tv[k] = k0 ? mk((T)Eld[k], T(0)) : mk(T(0), T(0));
 #pragma unroll
       for (int d = 0; d < DIM; ++d) gp[d] = mk(T(0), T(0));
       continue;
@@ -735,7 +738,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     CellDev c{};
     c.dim = dim;
     c.n = k.n;
-    c.H = (k.n + 1) / 2;
+    c.H = k.n / 2 + 1;  // kx = 0 .. n/2: (n+1)/2 bins for odd n, n/2 + 1 (with the Nyquist bin) for even n
     c.Hp = (c.H + 7) / 8 * 8;
     c.nc = nc;
     c.nrows = dim == 2 ? k.n : k.n * k.n;
@@ -746,7 +749,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
       if (external) {
         HostPlan hp;
         if (!build_host_plan(k.n, hp, max_radix) || (int)hp.radix.size() > kMaxStages)
-          return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d is not odd with factors 3, 5, 7, 11, 13", k.n);
+          return set_error(HOM_ERR_UNSUPPORTED_SIZE, "grid size %d has a prime factor above 13", k.n);
         p.n = k.n;
         p.nstage = (int)hp.radix.size();
         for (int s2 = 0; s2 < p.nstage; ++s2) {

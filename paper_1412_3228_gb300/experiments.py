@@ -14,8 +14,9 @@
   per filter radius, with its overshoot beyond the phase range and its L2 gap to a point-sampled
   exact microstructure supplied by the caller.
 
-Grid sizes must be odd (the frequency set J of section 1 is defined for odd N) and factor into
-3, 5, 7, 11 and 13.  The converged value is the unfiltered stress at a large resolution `n_ref` (the
+Grid sizes factor into 2, 3, 5, 7, 11 and 13.  The frequency set J of section 2 is defined for odd N;
+even N (the paper's sweep includes them) take the library's Nyquist convention (zero strain at
+wave vectors with a Nyquist component).  The converged value is the unfiltered stress at a large resolution `n_ref` (the
 filters' pixel-sized smoothing vanishes as the grid is refined, so every rule converges to it).
 
     python -m paper_1412_3228_gb300.experiments --contrast 1000 --sizes 9,15,21,25,27,35,45,63,75,81,105,125
@@ -67,8 +68,8 @@ def axial_stress_sweep(sizes: Iterable[int], contrast: float, rules: Iterable[st
     criterion = hom.HOM_CRIT_E if criterion is None else criterion
     sizes = [int(n) for n in sizes]
     for n in sizes + ([n_ref] if n_ref else []):
-        if n % 2 == 0 or not _factors_supported(n):
-            raise ValueError("grid size %d must be odd with factors 3, 5, 7, 11, 13" % n)
+        if not _factors_supported(n):
+            raise ValueError("grid size %d must factor into 2, 3, 5, 7, 11, 13" % n)
     phases = H.two_phases(contrast)
     cells, keys = [], []
     for rule in rules:
@@ -128,8 +129,8 @@ def iteration_sweep(n: int = 65, contrasts: Sequence[float] = (1e-3, 1e-2, 0.1, 
     import paper_1412_3228_gb300 as hom
     precision = hom.HOM_FP64 if precision is None else precision
     criterion = hom.HOM_CRIT_E if criterion is None else criterion
-    if n % 2 == 0 or not _factors_supported(n):
-        raise ValueError("grid size %d must be odd with factors 3, 5, 7, 11, 13" % n)
+    if not _factors_supported(n):
+        raise ValueError("grid size %d must factor into 2, 3, 5, 7, 11, 13" % n)
 
     def run(keys):
         cells, phases, c0 = [], [], []
@@ -181,7 +182,7 @@ def extrapolation_study(n: int = 65, m: int = 325, radii: Sequence[float] = (0.0
 
 
 def _factors_supported(n: int) -> bool:
-    for p in (3, 5, 7, 11, 13):
+    for p in (2, 3, 5, 7, 11, 13):
         while n % p == 0:
             n //= p
     return n == 1

@@ -1,5 +1,5 @@
 // Host-side check of the generic mixed-radix FFT (the templates of hom_common.cuh compile for the
-// host too): for every supported odd length n in [lo, hi], the DIF transform of natural-order input
+// host too): for every supported length n in [lo, hi] (odd and even), the DIF transform of natural-order input
 // and the DIT transform of digit-reversed input are compared with a long-double DFT at sampled bins,
 // under several thread schedules.  A schedule runs the threads of one stage one after another and
 // separates stages, which is what the kernels' barriers guarantee; butterflies of one stage touch
@@ -48,7 +48,7 @@ int main(int argc, char** argv) {
   std::mt19937 gen(12345);
   std::uniform_real_distribution<double> u(-1.0, 1.0);
   int bad = 0, checked = 0;
-  for (int n = lo | 1; n <= hi; n += 2) {
+  for (int n = lo; n <= hi; ++n) {
     std::vector<int> radices;
     if (!factorize(n, radices) || (int)radices.size() > kMaxStages) continue;
     HostPlan hp;

@@ -1,5 +1,5 @@
-"""The generic mixed-radix FFT (radices 3 ... 49, primes 11 and 13) run on the host: every supported
-odd length from 3 to 2187, DIF and DIT, forward and inverse, several thread schedules, against a
+"""The generic mixed-radix FFT (radices 2 ... 49, primes 11 and 13) run on the host: every supported
+length from 3 to 2187 (odd and even), DIF and DIT, forward and inverse, several thread schedules, against a
 long-double DFT at sampled bins.  Needs nvcc (compiles tests/fft_host_check.cu as host code); no GPU."""
 import os
 import shutil

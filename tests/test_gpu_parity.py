@@ -212,6 +212,41 @@ def test_radix_11_and_13_grids():
     assert _rel(cell_fields(res, [cell], 3, "eps")[0], refs[0]["eps"]) < 1e-10
 
 
+def test_even_grids():
+    """Even grids (Nyquist convention: zero strain at wave vectors with a Nyquist component, left out
+    of e and e_n): 16, 30, 64 and 128 in one batch, FP64 against the oracle (identical iteration
+    counts, 1e-10 on C_eff and fields), FP32 within 1e-5, conjugate gradients, and a 3D 16^3 cell."""
+    cells = [H.centred_disk_cell(n, rule=rule, radius=math.pi / 15)
+             for n, rule in ((16, H.RULE_VOIGT), (30, H.RULE_NONE), (64, H.RULE_TWO_LAYER), (128, H.RULE_REUSS))]
+    phases = H.two_phases(10.0)
+    E = np.eye(3)
+    mat, res, refs = _solve_both(cells, phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    eps = cell_fields(res, cells, 2, "eps")
+    for i, ref in enumerate(refs):
+        assert list(res["iterations"][i]) == list(ref["iterations"]), cells[i].n
+        C = hom.hom_effective_stiffness(E, res["mean_sigma"][i:i + 1], 2)[0]
+        assert _rel(C, O.effective_stiffness(ref["mean_sigma"], E)) < 1e-10
+        assert _rel(eps[i], ref["eps"]) < 1e-10
+    c0 = [H.mean_lame(phases)] * len(cells)
+    res32 = hom.hom_solve(mat, E, c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-6, max_iter=3000,
+                          fields=False)
+    cg = hom.hom_solve_cg(mat, E, precision=hom.HOM_FP64, tol=1e-10, max_iter=3000, fields=False)
+    for i, cell in enumerate(cells):
+        ct = O.filter_build(cell, phases)["ctilde"]
+        ref = O.solve(ct, 2, cell.n, *H.mean_lame(phases), E, tol=1e-10, max_iter=3000)
+        Cref = O.effective_stiffness(ref["mean_sigma"], E)
+        C = hom.hom_effective_stiffness(E, res32["mean_sigma"][i:i + 1], 2)[0]
+        assert _rel(C, Cref) < 1e-5, cell.n
+        Ccg = hom.hom_effective_stiffness(E, cg["mean_sigma"][i:i + 1], 2)[0]
+        assert _rel(Ccg, Cref) < 1e-9, cell.n
+    cell = H.rsa_spheres_cell(16, seed=16, vf=0.15, rmin=0.1, rmax=0.15, subgrid=4, gap_voxels=1.0)
+    E = np.eye(6)[:2]
+    mat, res, refs = _solve_both([cell], phases, E, hom.HOM_FP64, hom.HOM_CRIT_E, 1e-8)
+    assert list(res["iterations"][0]) == list(refs[0]["iterations"])
+    assert _rel(res["mean_sigma"][0], refs[0]["mean_sigma"]) < 1e-10
+    assert _rel(cell_fields(res, [cell], 3, "eps")[0], refs[0]["eps"]) < 1e-10
+
+
 def test_uneven_batch_matches_per_cell_oracle():
     """Cells of different sizes, rules and contrasts in one launch sequence."""
     base = [H.centred_disk_cell(15, rule=H.RULE_VOIGT), H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER),
