@@ -2,7 +2,8 @@
 // scheme of section 2 (eqs. 1-a, 1-b, 2) and the filter rules (eqs. 3, 4, 5-a, 5-b).
 //
 // With the converged fields eps^(j) of the nc unit Mandel loads, C_ij = <eps^(i) : c~ : eps^(j)>
-// holds exactly at the discrete solution (the odd-grid projection is orthogonal), so
+// holds exactly at the discrete solution (the projection onto compatible fields is orthogonal: on
+// odd grids, and on even grids with the Nyquist wave vectors set to zero strain), so
 //   dC_ij / dc~(x) = eps^(i)(x) (x) eps^(j)(x) / N_v.
 // For J = sum_j sum_x S^(j)(x) . sigma^(j)(x) with S^(j) = dL/dsigma^(j), the adjoint field
 // w^(j) (compatible, zero mean) solves the same Lippmann-Schwinger fixed point with source c~ S:
