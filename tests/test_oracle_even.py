@@ -43,9 +43,11 @@ def test_equilibrium_errors_on_even_grids():
     e, e_n = O.equilibrium_errors(np.fft.fftn(s, axes=(-2, -1)), 2, n)
     assert abs(e - math.sqrt(2) * math.pi * A) < 1e-12
     assert abs(e_n - A / math.sqrt(2)) < 1e-12
-    # variation only at the Nyquist frequency along x: left out, so e = e_n = 0
+    # variation only at the Nyquist frequency along x (sin(pi n x) = +-1 at the voxel centres): left
+    # out, so e = e_n = 0
     s2 = np.zeros((3, n, n))
-    s2[0] = 1.0 + A * np.cos(math.pi * n * x)[None, :]
+    s2[0] = 1.0 + A * np.sin(math.pi * n * x)[None, :]
+    assert np.abs(np.fft.fft(s2[0, 0])[n // 2]) > 0.1 * n
     e, e_n = O.equilibrium_errors(np.fft.fftn(s2, axes=(-2, -1)), 2, n)
     assert e < 1e-13 and e_n < 1e-13
 

@@ -6,6 +6,7 @@ mathematics and by the paper, none of which re-types the oracle's FFT-and-series
 * a single Fourier mode of J is reproduced everywhere (closed form);
 * the fine-grid mean equals the grid mean (every non-zero frequency of J sums to zero on the finer
   grid);
+* the exact (point-sampled) property of a slab, closed form at every fine point;
 * Fig. 4's statement for the Voigt filter: the extrapolated property overshoots the phase range less
   as the radius grows (none > 0.55 > 1.0), and the gap to the exact microstructure is smallest at
   0.55 among the radii 0.3, 0.55, 1.0, 1.5.
@@ -91,6 +92,20 @@ def test_exact_property_area():
     ex = O.exact_property(cell, [0.0, 1.0], 25 * 9)
     assert abs(ex.mean() - math.pi * 0.21 ** 2) < 4.0 * 2 * math.pi * 0.21 / (25 * 9)
     assert set(np.unique(ex)) == {0.0, 1.0}
+
+
+@pytest.mark.parametrize("axis,centre,thickness", [(0, 0.43, 0.37), (1, 0.05, 0.3)])
+def test_exact_property_of_a_slab_point_by_point(axis, centre, thickness):
+    """The slab holds the fine voxel centres y = (b + 1/2)/m within thickness/2 of its centre
+    (periodic distance): closed form at every point."""
+    n, m = 9, 27
+    cell = H.laminate_cell(n, 2, thickness, axis=axis, centre=centre)
+    ex = O.exact_property(cell, [0.0, 1.0], m)
+    y = (np.arange(m) + 0.5) / m
+    d = np.abs(y - centre)
+    inside = (np.minimum(d, 1.0 - d) <= thickness / 2).astype(float)
+    want = inside[None, :] if axis == 0 else inside[:, None]
+    np.testing.assert_array_equal(ex, np.broadcast_to(want, (m, m)))
 
 
 def test_fig4_voigt_filter_reduces_oscillations():
