@@ -228,9 +228,13 @@ int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, co
  *   (the passes of hom_solve) plus five short kernels (two inner products, the updates, the control).
  *   opts->tol bounds e_G = sqrt(<r, r> / N_v) / |<sigma>| with r = -G(sigma) the projected stress of
  *   the current iterate; e_n <= e_G <= sqrt(2) e_n, so e_G is comparable to HOM_CRIT_EN (criterion
- *   is ignored, diverge_window too).  out->err and out->err_n both receive e_G; out->iterations
- *   counts CG steps (each one Green-operator application; the start adds one more).
+ *   is ignored, diverge_window too).  When the recursively updated residual passes, one more pass
+ *   computes the true residual of E + x; the pair stops only if that passes too, else CG restarts
+ *   from it.  out->err and out->err_n both receive e_G; out->iterations counts CG steps (one
+ *   Green-operator application each; the start and each check add one more).
  *   HOM_STATUS_DIVERGED flags a breakdown (<p, A p> <= 0 or a non-finite value).
+ *   FP32 fields reach e_G of about 6e-8 times the contrast at best (the passes round relative to the
+ *   largest stress); use HOM_FP64 for contrasts of 100 and above.
  * Runs the generic passes (any supported grid, FP32 or FP64).  Synchronises the stream. */
 int hom_solve_cg(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                  const hom_solve_opts* opts, hom_result* out, void* stream);
