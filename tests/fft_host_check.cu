@@ -5,7 +5,9 @@
 // separates stages, which is what the kernels' barriers guarantee; butterflies of one stage touch
 // disjoint elements, so any interleaving inside a stage gives the same result.
 //
-//   fft_host_check lo hi   -> prints one line per length, "ok" or "FAIL" at the end, exit status 0/1
+//   fft_host_check lo hi [max_radix]   -> prints failing lengths, "ok" or "FAIL" at the end, exit 0/1
+// max_radix (default 45) bounds the register radices of the plans, as the kernels' MAXR does
+// (FP64 kernels use plans up to radix 15, FP32 ones up to 27 or 45).
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -45,6 +47,7 @@ static void run_dit(std::vector<double2>& a, const Plan& p, const std::vector<do
 
 int main(int argc, char** argv) {
   const int lo = argc > 1 ? atoi(argv[1]) : 3, hi = argc > 2 ? atoi(argv[2]) : 2187;
+  const int max_radix = argc > 3 ? atoi(argv[3]) : 45;
   std::mt19937 gen(12345);
   std::uniform_real_distribution<double> u(-1.0, 1.0);
   int bad = 0, checked = 0;
@@ -52,7 +55,7 @@ int main(int argc, char** argv) {
     std::vector<int> radices;
     if (!factorize(n, radices) || (int)radices.size() > kMaxStages) continue;
     HostPlan hp;
-    if (!build_host_plan(n, hp)) { printf("n %d: no plan\n", n); ++bad; continue; }
+    if (!build_host_plan(n, hp, max_radix)) { printf("n %d: no plan up to radix %d\n", n, max_radix); ++bad; continue; }
     Plan p{};
     p.n = n;
     p.nstage = (int)hp.radix.size();

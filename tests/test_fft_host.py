@@ -29,8 +29,10 @@ def checker(tmp_path_factory):
     return exe
 
 
+@pytest.mark.parametrize("max_radix", [15, 27, 45])
 @pytest.mark.parametrize("lo,hi", [(3, 255), (257, 1023), (1025, 2187)])
-def test_generic_fft_every_length(checker, lo, hi):
-    out = subprocess.run([checker, str(lo), str(hi)], capture_output=True, text=True, timeout=600)
+def test_generic_fft_every_length(checker, lo, hi, max_radix):
+    """max_radix as the kernels use it: FP64 plans up to radix 15, FP32 up to 27 (default) or 45."""
+    out = subprocess.run([checker, str(lo), str(hi), str(max_radix)], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:]
     assert out.stdout.strip().endswith("ok")
