@@ -123,8 +123,8 @@ def measured_peak_hbm():
 
 
 # DRAM bytes (read + write) per algorithmic byte of the specialised FP32 2D passes, from the ncu
-# capture summarised in profiles/k_row_f2d_k_green_f2d_1215_fp32.md (two 1215^2 cells x 3 loads;
-# traffic grows with the tiles processed, so a launch's traffic is this ratio times its bytes).
+# --set full capture of the profile case (--profile-case: two 1215^2 cells x 3 loads; traffic grows
+# with the tiles processed, so a launch's traffic is this ratio times its bytes).
 # Valid for the kernels as captured there; None for kernels without a capture.
 TRAFFIC_RATIO = {"row": (110.363 + 54.692) / 215.77, "green": (177.533 + 116.269) / 354.61}
 

@@ -71,6 +71,9 @@ extern "C" {
 #define HOM_FP32 0 /* FP32 fields, FFTs and Green operator; FP64 residual norm and averages   */
 #define HOM_FP64 1 /* FP64 everywhere                                                          */
 
+#define HOM_PASSES_AUTO 0    /* specialised FP32 passes where a compiled plan exists, else generic */
+#define HOM_PASSES_GENERIC 1 /* generic passes for every cell (any supported grid and precision)   */
+
 #define HOM_CRIT_E 0  /* e   = sqrt(sum_k |xi_k . sigma_hat(k)|^2) / ||sigma_hat(0)||          */
 #define HOM_CRIT_EN 1 /* e_n = sqrt(sum_{k!=0} |(xi_k/|xi_k|) . sigma_hat(k)|^2) / ||sigma_hat(0)|| */
 
@@ -150,6 +153,9 @@ typedef struct hom_solve_opts {
   int32_t check_every;    /* iterations launched between host polls (>= 1; 0 = default) */
   int32_t diverge_window; /* consecutive error increases that flag divergence (0 = off)  */
   int32_t use_graph;      /* 1: replay each poll interval as a captured CUDA graph       */
+  int32_t passes;         /* HOM_PASSES_AUTO or HOM_PASSES_GENERIC                       */
+  int32_t max_radix;      /* largest register radix of the generic FP32 FFT stages: 15, 27 or
+                             45 (0 = 27; FP64 always uses 15)                             */
 } hom_solve_opts;
 
 /* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every
@@ -275,21 +281,24 @@ int hom_solve_backward(const hom_cell* cells, int32_t ncells, const hom_material
  * or fragments the pool), callers under a hard per-process memory budget, and latency-sensitive
  * callers that cannot afford the device-wide synchronisation of cudaFree.
  *
- * Same arguments, results and kernels as hom_solve, but the call makes no device allocation: the
- * FFT plan tables and all solver scratch (mixed-domain state, partial sums, bookkeeping) live in
- * one fixed array of 64 MiB in the library's device memory (every device that loads the library
- * holds it until the process exits).  A batch needing more scratch than that is rejected with
- * HOM_ERR_UNSUPPORTED_SIZE and a message giving both sizes.  Roughly, 2D FP32 scratch per cell is
- * 88 * L * n * Hp bytes with Hp = (n+1)/2 rounded up to a multiple of 8 (one 405^2 cell with 3
- * loads takes 22 MB and fits, one 1215^2 cell with 3 loads takes 195 MB and does not); FP64
- * needs twice that, 3D cells n times more.
+ * Same arguments, results and kernels as hom_solve (the specialised FP32 passes included), but the
+ * call makes no device allocation: the FFT plan tables and all solver scratch (mixed-domain state,
+ * partial sums, bookkeeping) live in one fixed array of 64 MiB in the library's device memory
+ * (every device that loads the library holds it until the process exits).  A batch needing more
+ * scratch than that is rejected with HOM_ERR_UNSUPPORTED_SIZE and a message giving both sizes.
+ * Roughly, 2D FP32 scratch per cell is 88 * L * n * Hp bytes with Hp = (n+1)/2 rounded up to a
+ * multiple of 8 (one 405^2 cell with 3 loads takes 22 MB and fits, one 1215^2 cell with 3 loads
+ * takes 195 MB and does not); FP64 needs twice that, 3D cells n times more.
  *   - opts->use_graph must be 0 and out->stats must be NULL (both would allocate);
  *     HOM_ERR_INVALID_ARG otherwise.  Outputs in host memory are staged through the same array.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
- *     caches it; make that first call outside any stream capture.
+ *   - Every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress); the first call on a device may load the library's device code, so
+ *     make it outside any stream capture.
  *   - Every call reuses the same array and leaves its contents behind; each call re-initialises
  *     what it needs.  Calls whose GPU work overlaps (several streams or host threads at once) race
  *     on the array: serialise them.
+ *   - A call that fails after queuing work waits for that work (cudaStreamSynchronize) before it
+ *     returns, so its return always means that no kernel of it still uses the array.
  * Synchronises the stream before returning, like hom_solve. */
 int hom_solve_noalloc(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                       const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);

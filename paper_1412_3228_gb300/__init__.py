@@ -31,6 +31,7 @@ HOM_ERR_DIVERGED = 4
 HOM_ERR_CAPACITY = 8
 HOM_FP32, HOM_FP64 = 0, 1
 HOM_CRIT_E, HOM_CRIT_EN = 0, 1
+HOM_PASSES_AUTO, HOM_PASSES_GENERIC = 0, 1
 HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", -1: "active"}
 HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
@@ -73,7 +74,8 @@ class hom_material(ctypes.Structure):
 class hom_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("criterion", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("max_radix", ctypes.c_int32)]
 
 
 class hom_kernel_stats(ctypes.Structure):
@@ -262,7 +264,8 @@ def hom_solve_noalloc(material: Material, E, c0, **kw) -> dict:
 def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: int = HOM_FP64,
               criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
-              stats: bool = False, stream=None, allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
+              passes: int = HOM_PASSES_AUTO, max_radix: int = 0, stats: bool = False, stream=None,
+              allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
     """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
 
     E: [ncells, L, nc] (or [L, nc], shared by every cell) Mandel macroscopic strains.
@@ -302,7 +305,7 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                      err_n=err_n.ctypes.data, stats=ctypes.pointer(st) if st is not None else None)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=int(check_every), diverge_window=int(diverge_window),
-                          use_graph=int(bool(use_graph)))
+                          use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix))
     with torch.cuda.device(device):
         if _entry == "hom_solve_cg":
             code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
@@ -365,7 +368,7 @@ def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_
     info = hom_result(iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
                       err_n=err_n.ctypes.data)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
-                          check_every=0, diverge_window=0, use_graph=0)
+                          check_every=0, diverge_window=0, use_graph=0, passes=HOM_PASSES_AUTO, max_radix=0)
     with torch.cuda.device(device):
         code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                         c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),

@@ -582,22 +582,14 @@ bool fast2d_size(int n) {
   return false;
 }
 
-int fast2d_plan(int n, FastPlanDev* out) {
-  int dev = 0;
-  HOM_CUDA_TRY(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(g_fast_mu);
-  for (const auto& e : g_fast_cache)
-    if (e.dev == dev && e.n == n) {
-      *out = e.p;
-      return HOM_OK;
-    }
+int fast2d_plan_host(int n, std::vector<unsigned char>& h, FastPlanDev* out) {
   HostPlan hp;
   if (radices_of(n).empty() || !build_host_plan_radices(n, radices_of(n), hp))
     return set_error(HOM_ERR_UNSUPPORTED_SIZE, "no specialised plan for n = %d", n);
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t b_tw = up((size_t)n * 16), b_ip = up((size_t)n * 2), b_xp = up((size_t)n * 4), b_xn = up((size_t)n * 4),
                b_t2 = up((size_t)n * 8 + 8);
-  std::vector<unsigned char> h(b_tw + b_ip + b_xp + b_xn + b_t2, 0);
+  h.assign(b_tw + b_ip + b_xp + b_xn + b_t2, 0);
   // per-stage twiddle tables (stages with span L > 1): entry (q - 1) L + j = w^(j q n / (L R))
   float* tw = reinterpret_cast<float*>(h.data());
   {
@@ -621,17 +613,44 @@ int fast2d_plan(int n, FastPlanDev* out) {
   float* xn = reinterpret_cast<float*>(h.data() + b_tw + b_ip + b_xp);
   for (int p = 0; p < n; ++p) xp[p] = (float)hp.xi[ip[p]];
   for (int k = 0; k < n; ++k) xn[k] = (float)hp.xi[k];
+  // table pointers as byte offsets from the start of the tables (fast2d_plan_rebase adds the base)
+  FastPlanDev p{};
+  p.tw4 = reinterpret_cast<const float4*>(size_t(0));
+  p.iperm = reinterpret_cast<const uint16_t*>(b_tw);
+  p.xipos = reinterpret_cast<const float*>(b_tw + b_ip);
+  p.xinat = reinterpret_cast<const float*>(b_tw + b_ip + b_xp);
+  p.tw2 = reinterpret_cast<const float2*>(b_tw + b_ip + b_xp + b_xn);
+  p.n = n;
+  *out = p;
+  return HOM_OK;
+}
+
+void fast2d_plan_rebase(FastPlanDev& p, const unsigned char* base) {
+  auto at = [&](const void* off) { return base + reinterpret_cast<size_t>(off); };
+  p.tw4 = reinterpret_cast<const float4*>(at(p.tw4));
+  p.iperm = reinterpret_cast<const uint16_t*>(at(p.iperm));
+  p.xipos = reinterpret_cast<const float*>(at(p.xipos));
+  p.xinat = reinterpret_cast<const float*>(at(p.xinat));
+  p.tw2 = reinterpret_cast<const float2*>(at(p.tw2));
+}
+
+int fast2d_plan(int n, FastPlanDev* out) {
+  int dev = 0;
+  HOM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_fast_mu);
+  for (const auto& e : g_fast_cache)
+    if (e.dev == dev && e.n == n) {
+      *out = e.p;
+      return HOM_OK;
+    }
+  std::vector<unsigned char> h;
+  FastPlanDev p{};
+  int rc = fast2d_plan_host(n, h, &p);
+  if (rc != HOM_OK) return rc;
   void* mem = nullptr;
   HOM_CUDA_TRY(cudaMalloc(&mem, h.size()));
   HOM_CUDA_TRY(cudaMemcpy(mem, h.data(), h.size(), cudaMemcpyHostToDevice));
-  unsigned char* m = static_cast<unsigned char*>(mem);
-  FastPlanDev p{};
-  p.tw4 = reinterpret_cast<const float4*>(m);
-  p.iperm = reinterpret_cast<const uint16_t*>(m + b_tw);
-  p.xipos = reinterpret_cast<const float*>(m + b_tw + b_ip);
-  p.xinat = reinterpret_cast<const float*>(m + b_tw + b_ip + b_xp);
-  p.tw2 = reinterpret_cast<const float2*>(m + b_tw + b_ip + b_xp + b_xn);
-  p.n = n;
+  fast2d_plan_rebase(p, static_cast<const unsigned char*>(mem));
   g_fast_cache.push_back({dev, n, p, mem});
   *out = p;
   return HOM_OK;

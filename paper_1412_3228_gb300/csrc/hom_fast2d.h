@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace hom {
 
@@ -31,6 +32,11 @@ bool fast3d_size(int n);
 // Device tables of size n (built and uploaded on first use, kept until hom_release); every size
 // of fast2d_size or fast3d_size has one.
 int fast2d_plan(int n, FastPlanDev* out);
+// The same tables built on the host only (no device allocation): `h` receives them and `out` their
+// layout, with byte offsets from the start of `h` in place of the table pointers; after `h` is
+// copied to device memory at `base`, fast2d_plan_rebase turns the offsets into device pointers.
+int fast2d_plan_host(int n, std::vector<unsigned char>& h, FastPlanDev* out);
+void fast2d_plan_rebase(FastPlanDev& p, const unsigned char* base);
 // Dynamic shared memory of the row and Green passes for the largest grid size n of a call.
 size_t fast2d_smem_row(int nmax, int nphase_cell);
 size_t fast2d_smem_green(int nmax);

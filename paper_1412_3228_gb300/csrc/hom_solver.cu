@@ -20,7 +20,6 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
-#include <cstdlib>
 #include <type_traits>
 #include <vector>
 
@@ -685,7 +684,8 @@ struct Layout {
   std::vector<TaskR> tR;
   std::vector<TaskL> tC, tY;
   std::vector<PairDev> pairs;
-  std::vector<FastPlanDev> fplans;  // specialised 2D FP32 passes: per-size tables
+  std::vector<FastPlanDev> fplans;  // specialised FP32 passes: per-size tables
+  std::vector<std::vector<unsigned char>> fplan_host;  // external workspace: their host copies
   bool fast = false;
   int fast_nmax = 0;
   size_t ws_elems = 0, g_elems = 0, fld_elems = 0;
@@ -706,24 +706,16 @@ TaskL make_task(int cell, int load, int kx0, int ntk, int fixed, int nc, int dim
   return t;
 }
 
-// Per-CTA shared-memory budget of the Green and y passes: three kx columns of a 1215 line in FP32
-// (nine lines, two CTAs per SM); HOM_GREEN_BUDGET overrides it.
-size_t green_budget() {
-  const char* e = std::getenv("HOM_GREEN_BUDGET");
-  size_t b = e ? (size_t)std::atoll(e) : (size_t)110 * 1024;
-  return std::min<size_t>(std::max<size_t>(b, 8 * 1024), 227 * 1024);
-}
-
-size_t smem_budget() {
-  const char* e = std::getenv("HOM_SMEM_BUDGET");
-  size_t b = e ? (size_t)std::atoll(e) : (size_t)96 * 1024;  // two CTAs per SM (measured best)
-  return std::min<size_t>(std::max<size_t>(b, 8 * 1024), 227 * 1024);
-}
+// Per-CTA shared-memory budgets of the generic passes: the Green and y passes take three kx
+// columns of a 1215 line in FP32 (nine lines, two CTAs per SM), the row pass two CTAs per SM
+// (both measured best on the 2D sweep).
+constexpr size_t kGreenBudget = (size_t)110 * 1024;
+constexpr size_t kRowBudget = (size_t)96 * 1024;
 
 int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize, int max_radix, const double* c0,
                  bool external, Layout& lay) {
   const int nc = nc_of(dim);
-  const size_t budget = smem_budget();
+  const size_t budget = kRowBudget;
   const size_t kMaxSmem = 227 * 1024;
   // The specialised passes take 4-row and 2-column tasks; the output pass (generic row kernel)
   // then needs 4 rows of every load on chip.
@@ -770,13 +762,19 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     }
     c.fplan = -1;
     if (lay.fast) {
-      FastPlanDev fp{};
-      int rc = fast2d_plan(k.n, &fp);
-      if (rc != HOM_OK) return rc;
       int idx = -1;
       for (size_t i = 0; i < lay.fplans.size(); ++i)
         if (lay.fplans[i].n == k.n) idx = (int)i;
       if (idx < 0) {
+        FastPlanDev fp{};
+        int rc;
+        if (external) {  // host tables, uploaded into the caller's workspace with the call
+          lay.fplan_host.emplace_back();
+          rc = fast2d_plan_host(k.n, lay.fplan_host.back(), &fp);
+        } else {
+          rc = fast2d_plan(k.n, &fp);
+        }
+        if (rc != HOM_OK) return rc;
         lay.fplans.push_back(fp);
         idx = (int)lay.fplans.size() - 1;
       }
@@ -816,47 +814,20 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     const size_t need_r = row_lines(r) * line_bytes + (size_t)r * L * nc * (sizeof(long long) + 2 * vsize / 2);
     if (need_r > kMaxSmem) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "row of n = %d with %d loads does not fit on chip", k.n, L);
     lay.smem_row = std::max(lay.smem_row, need_r);
-    // row tasks: every load per task (generic passes), or one load per task (specialised passes:
-    // finer tasks, and tasks of finished loads exit at once), load-major within the cell
+    // row tasks: every load per task (one load per task measured 3 % slower on the 2D sweep)
     c.rtask0 = (int)lay.tR.size();
     std::vector<int> rt0(L, c.rtask0), rt1(L, c.rtask0);
-    // HOM_ROW_PER_LOAD=1: one load per task (measured 3 % slower on the 2D sweep than every load
-    // per task, which shares labels and twiddles across the loads)
-    static const bool per_load = [] {
-      const char* e = std::getenv("HOM_ROW_PER_LOAD");
-      return e && e[0] == '1';
-    }();
-    static const bool per_load3 = [] {  // 3D: HOM_ROW_PER_LOAD3=1 gives one load per row task
-      const char* e = std::getenv("HOM_ROW_PER_LOAD3");
-      return e && e[0] == '1';
-    }();
-    if (lay.fast && dim == 3) {  // groups of 4 rows (consecutive y) within each z plane
-      if (per_load3) {
-        for (int l = 0; l < L; ++l) {
-          rt0[l] = (int)lay.tR.size();
-          for (int z = 0; z < k.n; ++z)
-            for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), l});
-          rt1[l] = (int)lay.tR.size();
-        }
-      } else {
-        for (int z = 0; z < k.n; ++z)
-          for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), -1});
-        for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
-      }
-    } else if (lay.fast && per_load) {
-      for (int l = 0; l < L; ++l) {
-        rt0[l] = (int)lay.tR.size();
-        for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), l});
-        rt1[l] = (int)lay.tR.size();
-      }
-    } else {
+    if (lay.fast && dim == 3) {  // groups of 4 rows (consecutive y) within each z plane, every load
+      for (int z = 0; z < k.n; ++z)
+        for (int y0 = 0; y0 < k.n; y0 += r) lay.tR.push_back(TaskR{ci, z * k.n + y0, std::min(r, k.n - y0), -1});
+    } else {  // every load per task: labels and twiddles are shared across the loads
       for (int r0 = 0; r0 < c.nrows; r0 += r) lay.tR.push_back(TaskR{ci, r0, std::min(r, c.nrows - r0), -1});
-      for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
     }
+    for (int l = 0; l < L; ++l) rt1[l] = (int)lay.tR.size();
     c.rtask1 = (int)lay.tR.size();
     // Green-pass and y-pass tiles of kx
     // Green/y tiles: ntk kx columns x nc lines, plus the twiddle table and the wave-number table
-    const size_t gbudget = green_budget();
+    const size_t gbudget = kGreenBudget;
     int ntk = (int)std::max<size_t>(1, (gbudget - std::min(gbudget, 2 * line_bytes)) / ((size_t)nc * line_bytes));
     if (lay.fast) ntk = kFastCols;
     ntk = std::min(ntk, c.H);
@@ -969,12 +940,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     }
     c0 = c0_cg.data();
   }
-  {
-    const char* fe = std::getenv("HOM_FAST2D");
-    // HOM_FAST2D=0: generic passes everywhere; HOM_FAST2D=2: generic passes for 3D only
-    lay.fast = std::is_same<T, float>::value && !ext && !adj && !cg && !(fe && fe[0] == '0') &&
-               !(DIM == 3 && fe && fe[0] == '2');
-  }
+  // opts->passes == HOM_PASSES_GENERIC keeps every solve on the generic passes
+  lay.fast = std::is_same<T, float>::value && !adj && !cg && opts->passes != HOM_PASSES_GENERIC;
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1040,8 +1007,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_stage_s = need_stage && out->sigma && !sig_dev ? take(lay.fld_elems * sizeof(T)) : 0;
   const size_t host_lo = o_cells, host_hi = o_int;  // tables uploaded in one copy
   // external workspace: the plan tables follow the scratch
-  std::vector<size_t> o_plan_tab(lay.host_plans.size());
+  std::vector<size_t> o_plan_tab(lay.host_plans.size()), o_fplan_tab(lay.fplan_host.size());
   for (size_t i = 0; i < lay.host_plans.size(); ++i) o_plan_tab[i] = take(plan_table_bytes(lay.host_plans[i].n));
+  for (size_t i = 0; i < lay.fplan_host.size(); ++i) o_fplan_tab[i] = take(lay.fplan_host[i].size());
   void* wsv = nullptr;
   if (ext) {
     if (off > ext->capacity)
@@ -1062,6 +1030,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_plan_tab[i], plan_host.data(), plan_host.size(), cudaMemcpyHostToDevice, st));
     if (ext) HOM_CUDA_TRY(cudaStreamSynchronize(st));  // plan_host is reused for the next table
     set_plan_pointers(lay.plans[i], ws + o_plan_tab[i]);
+  }
+  for (size_t i = 0; i < lay.fplan_host.size(); ++i) {
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_fplan_tab[i], lay.fplan_host[i].data(), lay.fplan_host[i].size(),
+                                 cudaMemcpyHostToDevice, st));
+    fast2d_plan_rebase(lay.fplans[i], ws + o_fplan_tab[i]);
   }
   if (ext) HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging vectors above go out of scope
   {
@@ -1346,6 +1319,10 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown criterion");
   if (opts->max_iter < 0 || opts->check_every < 0 || opts->diverge_window < 0)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: negative option");
+  if (opts->passes != HOM_PASSES_AUTO && opts->passes != HOM_PASSES_GENERIC)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown passes option %d", opts->passes);
+  if (opts->max_radix != 0 && opts->max_radix != 15 && opts->max_radix != 27 && opts->max_radix != 45)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: max_radix must be 0, 15, 27 or 45");
   if (!mat->label || !mat->phase_c32 || !mat->phase_c64)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material not built");
   const int dim = cells[0].dim;
@@ -1360,10 +1337,9 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   if (mat->dim != dim) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material built for another dimension");
   cudaGetLastError();  // do not report an error left behind by an unrelated earlier call
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Largest register radix of the FFT stages: FP32 kernels are compiled for 15, 27 and 45, FP64
-  // ones for 15 (HOM_MAX_RADIX32 selects the FP32 variant).
-  const char* env = std::getenv("HOM_MAX_RADIX32");
-  const int r32 = env ? std::atoi(env) : 27;
+  // Largest register radix of the generic FFT stages: FP32 kernels are compiled for 15, 27 and 45
+  // (opts->max_radix; 0 = 27), FP64 ones for 15.
+  const int r32 = opts->max_radix > 0 ? opts->max_radix : 27;
   if (opts->precision == HOM_FP32) {
     if (r32 >= 45)
       return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)

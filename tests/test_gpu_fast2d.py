@@ -1,10 +1,9 @@
 """GPU tests of the specialised FP32 2D passes: every specialised grid size, ragged row groups and
 odd kx counts, output fields, batches with more phases than a one-byte label can name, and
-agreement with the generic passes (HOM_FAST2D=0) on the same inputs.
+agreement with the generic passes (passes=HOM_PASSES_GENERIC) on the same inputs.
 
 The oracle is the FP64 CPU implementation (FP64, tight tolerance); the FP32 bar is 1e-5 relative
 on C_eff, with local-field L2 errors stated."""
-import os
 
 import numpy as np
 import pytest
@@ -33,17 +32,8 @@ def _rel(a, b):
 
 
 def _solve(mat, E, c0, generic=False, **kw):
-    old = os.environ.get("HOM_FAST2D")
-    if generic:
-        os.environ["HOM_FAST2D"] = "0"
-    try:
-        return hom.hom_solve(mat, E, c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, **kw)
-    finally:
-        if generic:
-            if old is None:
-                del os.environ["HOM_FAST2D"]
-            else:
-                os.environ["HOM_FAST2D"] = old
+    passes = hom.HOM_PASSES_GENERIC if generic else hom.HOM_PASSES_AUTO
+    return hom.hom_solve(mat, E, c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, passes=passes, **kw)
 
 
 def _batch(specs):

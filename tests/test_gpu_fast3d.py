@@ -1,6 +1,5 @@
 """GPU tests of the specialised FP32 3D passes: sizes 27 and 45 against the FP64 oracle (C_eff,
-output fields), and 81 against the generic 3D passes (HOM_FAST2D=2 selects them for 3D)."""
-import os
+output fields), and 81 against the generic 3D passes (passes=HOM_PASSES_GENERIC)."""
 
 import numpy as np
 import pytest
@@ -29,17 +28,8 @@ def _rel(a, b):
 
 
 def _solve(mat, E, c0, generic=False, **kw):
-    old = os.environ.get("HOM_FAST2D")
-    if generic:
-        os.environ["HOM_FAST2D"] = "2"
-    try:
-        return hom.hom_solve(mat, E, c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, **kw)
-    finally:
-        if generic:
-            if old is None:
-                del os.environ["HOM_FAST2D"]
-            else:
-                os.environ["HOM_FAST2D"] = old
+    passes = hom.HOM_PASSES_GENERIC if generic else hom.HOM_PASSES_AUTO
+    return hom.hom_solve(mat, E, c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, passes=passes, **kw)
 
 
 CASES = [
