@@ -163,6 +163,11 @@ def reduce_across_ranks(ms: float, vox_it: float, device, world: int):
 
 
 def run_ours(args, rank, world):
+    # the oracle's worker pool for the all-core CPU baseline, spawned before the first GPU call
+    pool = None
+    if rank == 0 and not args.skip_cpu:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1))
     import torch
 
     import paper_1412_3228_gb300 as hom
@@ -242,23 +247,11 @@ def run_ours(args, rank, world):
     e2e_ms = e2e_total_s * 1e3 / max(1, args.steps)
     h2d = sum(48 * len(c.prims) + 40 for c in cells) + 16 * len(phases) + 8 * E.size + 16 * len(cells)
 
-    # ---- FP64 plain form: one cell at a time, FP64 everywhere (one untimed warm-up pass first)
+    # ---- FP64 plain form: one cell at a time and batched, FP64 everywhere, against the FP32 form at
+    # the same C_eff error (one untimed warm-up pass first)
     fp64 = None
     if not args.skip_fp64 and rank == 0:
-        for i in range(len(cells)):
-            step(precision=hom.HOM_FP64, subset=[i])
-        torch.cuda.synchronize()
-        tf = time.perf_counter()
-        ms64, vi64, ms_f64 = 0.0, 0.0, []
-        for i in range(len(cells)):
-            r64, C64 = step(precision=hom.HOM_FP64, subset=[i])
-            vi64 += float(sum(cells[i].n ** 2 * it for it in r64["iterations"][0]))
-            ms_f64.append(r64["mean_sigma"][0])
-        torch.cuda.synchronize()
-        ms64 = (time.perf_counter() - tf) * 1e3
-        err64, _ = ceff_errors(cells, phases, np.array(ms_f64), golden_ceff())
-        fp64 = {"value": vi64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64, "ceff_max_rel_err": err64}
-
+        fp64 = fp64_forms(hom, step, cells, phases, fp32_err)
     # ---- comparison (not on the product path): cuFFT via torch.fft, a forward real 2D FFT and its
     # inverse over the 18 real fields of two 1215^2 cells x 3 loads x 3 components, against one
     # iteration of this library on the same cells (row pass + Green pass + control, CUDA events)
@@ -266,10 +259,12 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.skip_cufft:
         comparison = cufft_comparison(hom, cells, phases, c0, dev)
 
-    # ---- secondary workload: one 243^3 random-sphere cell (2-layer filter, 6 loads, FP32, e_n < 1e-6)
-    spheres = None
+    # ---- secondary workloads: random-sphere cells (2-layer filter, 6 loads, FP32, e_n < 1e-6): 135^3
+    # at both contrasts (C_eff against the oracle's stored values) and 243^3 at contrast 10
+    spheres = spheres135 = None
     if rank == 0 and not args.skip_3d:
-        spheres = spheres_3d(hom, dev)
+        spheres135 = spheres_3d(hom, dev, n=135, contrasts=(10.0, 0.1))
+        spheres = spheres_3d(hom, dev, n=243, contrasts=(10.0,), fp64_check=not args.skip_fp64)
 
     # ---- secondary workload: the batched 2D ensemble (256 random-disk cells of uneven size)
     ensemble = None
@@ -308,11 +303,108 @@ def run_ours(args, rank, world):
                                                                         if c.rule == rr])) for rr in RULES}},
             "filter_build_ms": round(filter_ms, 3),
             "ceff_max_rel_err_vs_oracle": fp32_err, "ceff_cells_compared": ncmp,
-            "fp64_plain": fp64, "cufft_comparison": comparison, "spheres3d_243": spheres,
+            "fp64_plain": fp64,
+            "fp32_vs_fp64_equal_error": (None if fp64 is None else {
+                "fp32_value": value, "fp64_value": fp64["batched_equal_error"]["value"],
+                "fp64_tol": fp64["batched_equal_error"]["tol"], "ratio": value / fp64["batched_equal_error"]["value"],
+                "fp32_ceff_err": fp32_err, "fp64_ceff_err": fp64["batched_equal_error"]["ceff_max_rel_err"]}), "cufft_comparison": comparison, "spheres3d_243": spheres, "spheres3d_135": spheres135,
             "ensemble2d_256": ensemble, "cg_vs_fixed_point": cg}
     if rank == 0 and not args.skip_cpu:
-        line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_baseline"] = cpu_baseline(args, pool)
+    if pool is not None:
+        pool.close()
+        pool.join()
     return line
+
+
+def flops_per_voxel_iteration(n, dim=2):
+    """Algorithmic FLOPs of one voxel-iteration of one load (model): a forward and an inverse real
+    FFT of each of the nc components (2 x 2.5 log2(N_v) each), the constitutive update (2 nc^2) and
+    the Green operator with the residual (about 30 per voxel)."""
+    nc = 3 if dim == 2 else 6
+    return nc * 5.0 * math.log2(n ** dim) + 2 * nc * nc + 30.0
+
+
+def fp64_peak_tflops(reps=3, m=4096):
+    """FP64 throughput of this GPU measured in this process: a cuBLAS DGEMM (2 m^3 FLOPs) timed with
+    CUDA events, best of `reps` (no setting changed)."""
+    import torch
+    a = torch.randn(m, m, device="cuda", dtype=torch.float64)
+    b = torch.randn(m, m, device="cuda", dtype=torch.float64)
+    st = torch.cuda.current_stream()
+    torch.matmul(a, b)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        torch.matmul(a, b)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * m ** 3 / (best / 1e3) / 1e12
+
+
+def fp64_forms(hom, step, cells, phases, fp32_err):
+    """The plain FP64 form of the sweep: one cell at a time (e_n < 1e-6), batched (one call, e_n < 1e-6)
+    and batched at the loosest tolerance whose C_eff error against the oracle does not exceed the
+    FP32 form's (the metric's "at fixed C_eff error"), with the FP64 ALU fraction of the batched solve."""
+    import torch
+    gold = golden_ceff()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t) * 1e3
+
+    def vi_of(r, idx):
+        return float(sum(cells[i].n ** 2 * it for k, i in enumerate(idx) for it in r["iterations"][k]))
+
+    for i in range(len(cells)):  # warm-up: plans and workspace
+        step(precision=hom.HOM_FP64, subset=[i])
+    out = {}
+
+    def one_by_one():
+        res = [step(precision=hom.HOM_FP64, subset=[i]) for i in range(len(cells))]
+        return res
+    res, ms = timed(one_by_one)
+    vi = sum(vi_of(r, [i]) for i, (r, _) in enumerate(res))
+    err, _ = ceff_errors(cells, phases, np.array([r["mean_sigma"][0] for r, _ in res]), gold)
+    out["one_cell_at_a_time"] = {"value": vi / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tol": TOL,
+                                 "ceff_max_rel_err": err}
+    idx = list(range(len(cells)))
+    flops = sum(cells[i].n ** 2 * flops_per_voxel_iteration(cells[i].n) for i in idx)
+    for name, tols in (("batched", [TOL]), ("batched_equal_error", [1e-5, 5e-6, 2e-6, TOL])):
+        for tol in tols:
+            def run(tol=tol):
+                import paper_1412_3228_gb300 as h2
+                c0 = np.array([H.mean_lame(phases[c.matrix_phase:c.matrix_phase + 2]) for c in cells])
+                mat = h2.hom_filter_build(cells, phases)
+                return h2.hom_solve(mat, np.eye(3), c0, precision=h2.HOM_FP64, criterion=h2.HOM_CRIT_EN, tol=tol,
+                                    max_iter=MAX_ITER, fields=False)
+            run()
+            r, ms = timed(run)
+            vi = vi_of(r, idx)
+            err, _ = ceff_errors(cells, phases, r["mean_sigma"], gold)
+            fl = float(sum(cells[i].n ** 2 * flops_per_voxel_iteration(cells[i].n) * it
+                           for i in idx for it in r["iterations"][i]))
+            out[name] = {"value": vi / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "tol": tol, "ceff_max_rel_err": err,
+                         "tflops": fl / (ms / 1e3) / 1e12}
+            if name == "batched" or (err is not None and fp32_err is not None and err <= fp32_err):
+                break
+    peak = fp64_peak_tflops()
+    for name in ("batched", "batched_equal_error"):
+        out[name]["alu"] = {"bound": "alu (fp64)", "peak_tflops": round(peak, 3),
+                            "peak_source": "cuBLAS DGEMM 4096^3 timed in this process",
+                            "frac": round(out[name]["tflops"] / peak, 4),
+                            "flops_model": "per voxel-iteration: 15 log2(n^2) + 48 (FFTs, constitutive, Green)"}
+    out["fp32_ceff_max_rel_err"] = fp32_err
+    del flops
+    return out
 
 
 def cufft_comparison(hom, cells, phases, c0, dev, reps=10):
@@ -346,36 +438,62 @@ def cufft_comparison(hom, cells, phases, c0, dev, reps=10):
                     "constitutive update, Gamma0 and the residual"}
 
 
-def spheres_3d(hom, dev, n=243):
-    """One 243^3 random-sphere cell (volume fraction 0.3, radius U[0.05, 0.1], contrast 10, 2-layer
-    filter r = 1 px, 8^3 subgrid), 6 Mandel loads in one batched FP32 solve to e_n < 1e-6."""
+def golden_3d(n):
+    p = os.path.join(ROOT, "tests", "golden", "spheres3d_ceff.json")
+    if not os.path.exists(p):
+        return {}
+    return {e["contrast"]: np.array(e["ceff"]) for e in json.load(open(p))["cells"] if e["n"] == n}
+
+
+def spheres_3d(hom, dev, n=243, contrasts=(10.0,), fp64_check=True):
+    """Random-sphere cells of n^3 (volume fraction 0.3, radius U[0.05, 0.1], 2-layer filter r = 1 px,
+    8^3 subgrid), one per contrast, 6 Mandel loads each, in one batched FP32 solve to e_n < 1e-6.
+    C_eff error: against the oracle's stored values where they exist (tests/golden), else against
+    the FP64 generic passes on the same cells to e < 1e-9 (the FP64 path matches the oracle to 1e-8
+    at 81^3 and 135^3)."""
     import torch
-    cell = H.rsa_spheres_cell(n, seed=1000 + n, vf=0.3, rmin=0.05, rmax=0.1, rule=H.RULE_TWO_LAYER,
+    base = H.rsa_spheres_cell(n, seed=1000 + n, vf=0.3, rmin=0.05, rmax=0.1, rule=H.RULE_TWO_LAYER,
                               radius_px=1.0, subgrid=8, gap_voxels=n / 243.0)
-    phases = H.two_phases(10.0)
-    c0 = np.array([H.mean_lame(phases)])
+    phases, cells = [], []
+    for contrast in contrasts:
+        cells.append(H.remap_phases(base, len(phases)))
+        phases.extend(H.two_phases(contrast))
+    c0 = np.array([H.mean_lame(phases[2 * i:2 * i + 2]) for i in range(len(cells))])
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    mat = hom.hom_filter_build([cell], phases)  # warm-up
+    mat = hom.hom_filter_build(cells, phases)  # warm-up
     t0.record(torch.cuda.current_stream())
-    mat = hom.hom_filter_build([cell], phases)
+    mat = hom.hom_filter_build(cells, phases)
     t1.record(torch.cuda.current_stream())
     torch.cuda.synchronize()
     filt_ms = t0.elapsed_time(t1)
-    r = hom.hom_solve(mat, np.eye(6), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=TOL,
-                      max_iter=MAX_ITER, fields=False, stats=True)
+    kw = dict(precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=TOL, max_iter=MAX_ITER, fields=False, stats=True)
+    r = hom.hom_solve(mat, np.eye(6), c0, **kw)
     torch.cuda.synchronize()
     t0.record(torch.cuda.current_stream())
-    r = hom.hom_solve(mat, np.eye(6), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=TOL,
-                      max_iter=MAX_ITER, fields=False, stats=True)
+    r = hom.hom_solve(mat, np.eye(6), c0, **kw)
     t1.record(torch.cuda.current_stream())
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     vi = float(n ** 3 * np.sum(r["iterations"]))
     kb = {k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) for k, v in r["stats"].items() if v["ms"] > 0 and v["bytes"] > 0}
+    C = hom.hom_effective_stiffness(np.eye(6), r["mean_sigma"], 3)
+    gold = golden_3d(n)
+    err, ref = None, None
+    if all(c in gold for c in contrasts):
+        err = max(float(np.abs(C[i] - gold[c]).max() / np.abs(gold[c]).max()) for i, c in enumerate(contrasts))
+        ref = "oracle C_eff (tests/golden, e < 1e-9)"
+    elif fp64_check:
+        r64 = hom.hom_solve(mat, np.eye(6), c0, precision=hom.HOM_FP64, criterion=hom.HOM_CRIT_E, tol=1e-9,
+                            max_iter=MAX_ITER, fields=False)
+        C64 = hom.hom_effective_stiffness(np.eye(6), r64["mean_sigma"], 3)
+        err = max(float(np.abs(C[i] - C64[i]).max() / np.abs(C64[i]).max()) for i in range(len(cells)))
+        ref = "FP64 generic passes on the same cells, e < 1e-9"
+        del r64
     return {"value": vi / (ms / 1e3), "unit": UNIT, "solve_ms": round(ms, 2), "filter_build_ms": round(filt_ms, 2),
-            "iterations": [int(i) for i in r["iterations"][0]], "spheres": len(cell.prims),
-            "mixed_voxels": int(mat.mixed_count), "achieved_gbs": kb,
+            "cells": len(cells), "contrasts": list(contrasts),
+            "iterations": [[int(i) for i in row] for row in r["iterations"]], "spheres": len(base.prims),
+            "mixed_voxels": int(mat.mixed_count), "achieved_gbs": kb, "ceff_max_rel_err": err, "ceff_reference": ref,
             "passes": "specialised FP32 3D (row, y forward, Green along z, y inverse)"}
 
 
@@ -467,39 +585,114 @@ def ensemble_2d(hom, dev, count=256):
             "achieved_gbs": kb}
 
 
-def cpu_baseline(args, iters=4):
-    """The oracle as it stands, on a bounded sample of the workload: the 405^2 Voigt cell
-    (contrast 10), 3 loads x `iters` fixed iterations, plus its filter build."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_job(job):
+    """One oracle run (in a spawned worker or the main process); returns its voxel-iterations and time.
+    ("solve2d", n, contrast, rule, loads, tol, criterion): filter build + full solve of the centred
+    disk (volume fraction 0.2, r = 1 px, 16x16 subgrid) for the first `loads` unit Mandel loads;
+    ("iter3d", n, iters): `iters` fixed iterations of one load on an n^3 laminate (no filter)."""
+    import oracle as O
+    t = time.perf_counter()
+    if job[0] == "solve2d":
+        _, n, contrast, rule, loads, tol, crit = job
+        phases = H.two_phases(contrast)
+        cell = H.centred_disk_cell(n, vf=0.2, rule=rule, radius_px=1.0, subgrid=16)
+        fb = O.filter_build(cell, phases)
+        lam0, mu0 = H.mean_lame(phases)
+        r = O.solve(fb["ctilde"], 2, n, lam0, mu0, np.eye(3)[:loads], tol=tol, max_iter=MAX_ITER, criterion=crit)
+        its = [int(i) for i in r["iterations"]]
+        return {"job": list(job), "vi": float(n * n * sum(its)), "iterations": its, "seconds": time.perf_counter() - t}
+    _, n, iters = job
+    phases = H.two_phases(10.0)
+    fb = O.filter_build(H.laminate_cell(n, 3, 0.3), phases)
+    lam0, mu0 = H.mean_lame(phases)
+    t = time.perf_counter()
+    O.solve(fb["ctilde"], 3, n, lam0, mu0, np.eye(6)[:1], tol=-1.0, max_iter=iters)
+    return {"job": list(job), "vi": float(n ** 3 * iters), "seconds": time.perf_counter() - t}
+
+
+def cpu_baseline(args, pool=None):
+    """The FP64 oracle as it stands on this machine's host cores, on bounded samples of the workloads:
+    single core -- full solves of the 45^2 cell of the first configuration (one load, e < 1e-8), of
+    the sweep's eight 45^2 cells and of two of its 135^2 cells (3 loads, e_n < 1e-6);
+    all cores -- the sweep's eight 405^2 cells solved in parallel (one worker per cell, `pool`);
+    3D -- one fixed iteration of one load on a 135^3 cell (time per iteration).
+    The 1215^2 cells and full 3D solves take hours on a host core and are left out."""
+    import oracle as O
+    jobs1 = [("solve2d", 45, 10.0, H.RULE_VOIGT, 1, 1e-8, O.CRIT_E)]
+    jobs1 += [("solve2d", 45, c, r, 3, TOL, O.CRIT_EN) for c in CONTRASTS for r in RULES]
+    jobs1 += [("solve2d", 135, 10.0, H.RULE_VOIGT, 3, TOL, O.CRIT_EN), ("solve2d", 135, 0.1, H.RULE_REUSS, 3, TOL, O.CRIT_EN)]
+    all_core = third = None
+    pending = None
+    if pool is not None:
+        jobs_all = [("solve2d", 405, c, r, 3, TOL, O.CRIT_EN) for c in CONTRASTS for r in RULES]
+        t_all = time.perf_counter()
+        pending = pool.map_async(oracle_job, jobs_all)
+        pending3 = pool.apply_async(oracle_job, (("iter3d", 135, 1),))
+    t = time.perf_counter()
+    res1 = [oracle_job(j) for j in jobs1]
+    dt1 = time.perf_counter() - t
+    vi1 = sum(r["vi"] for r in res1)
+    per_filter = {}
+    for r in res1[1:]:
+        per_filter.setdefault(H.RULE_NAMES[r["job"][3]], []).extend(r["iterations"])
+    if pending is not None:
+        ra = pending.get()
+        dt_all = time.perf_counter() - t_all
+        for r in ra:
+            per_filter.setdefault(H.RULE_NAMES[r["job"][3]], []).extend(r["iterations"])
+        all_core = {"value": sum(r["vi"] for r in ra) / dt_all, "unit": UNIT, "cores": min(len(jobs_all), os.cpu_count() or 1),
+                    "sample": "the sweep's eight 405^2 cells (3 loads, e_n < %g), one worker per cell, %.1f s" % (TOL, dt_all)}
+        r3 = pending3.get()
+        third = {"n": 135, "seconds_per_iteration": r3["seconds"], "value": r3["vi"] / r3["seconds"], "unit": UNIT,
+                 "sample": "1 fixed iteration, one load, 135^3 laminate (iteration cost does not depend on geometry)"}
+    return {"value": vi1 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "full solves: 45^2 disk (1 load, e < 1e-8), the sweep's eight 45^2 cells and its 135^2 Voigt "
+                      "(contrast 10) and Reuss (0.1) cells (3 loads, e_n < %g), filter build included, %.1f s on one "
+                      "core" % (TOL, dt1),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(), "all_cores": all_core, "per_iteration_3d": third,
+            "iterations_per_filter": {k: {"median": float(np.median(v)), "max": int(max(v))} for k, v in per_filter.items()}}
+
+
+def reference_sample():
+    """One bounded step of the reference arm: the oracle's filter build and 2 fixed iterations of the
+    3 loads of the sweep's 405^2 Voigt cell (contrast 10), on one host core."""
     import oracle as O
     cells, phases, c0 = workload()
     idx = [i for i, c in enumerate(cells) if c.n == 405 and c.rule == H.RULE_VOIGT][0]
     cell = cells[idx]
     t = time.perf_counter()
     fb = O.filter_build(cell, phases)
-    O.solve(fb["ctilde"], 2, cell.n, c0[idx][0], c0[idx][1], np.eye(3), tol=-1.0, max_iter=iters)
-    dt = time.perf_counter() - t
-    vi = cell.n ** 2 * iters * 3
-    return {"value": vi / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "405^2 Voigt cell, contrast 10: filter build + 3 loads x %d iterations (%.1f s)" % (iters, dt)}
+    O.solve(fb["ctilde"], 2, cell.n, c0[idx][0], c0[idx][1], np.eye(3), tol=-1.0, max_iter=2)
+    return cell.n ** 2 * 2 * 3 / (time.perf_counter() - t)
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
-    import oracle as O  # noqa: F401
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload per step."""
     for _ in range(args.warmup):
-        cpu_baseline(args, iters=2)
+        reference_sample()
     t = time.perf_counter()
-    vals = []
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args, iters=2))
+    vals = [reference_sample() for _ in range(args.steps)]
     dt = time.perf_counter() - t
-    value = float(np.mean([v["value"] for v in vals]))
-    cb = dict(vals[-1])
-    cb["value"] = value
+    value = float(np.mean(vals))
+    sample = "405^2 Voigt cell of the sweep, contrast 10: oracle filter build + 3 loads x 2 iterations per step"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(),
-            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def profile_case(args):

@@ -336,7 +336,8 @@ def hom_solve_cg(material: Material, E, **kw) -> dict:
 
 def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_dsigma: Optional[torch.Tensor] = None,
                        want_ctilde: bool = True, want_frac: bool = True, precision: int = HOM_FP64,
-                       criterion: int = HOM_CRIT_E, tol: float = 1e-10, max_iter: int = 2000, stream=None) -> dict:
+                       criterion: int = HOM_CRIT_E, tol: float = 1e-10, max_iter: int = 2000,
+                       passes: int = HOM_PASSES_AUTO, stream=None) -> dict:
     """Adjoint derivative of L(C_eff, sigma) (see include/hom.h).  `forward` is the dict returned by
     hom_solve (with device fields); dL_dC is [ncells, nc, nc] (host), dL_dsigma a device tensor laid
     out like forward['sigma'].  Returns dctilde [sum voxels, ns] (device), dphase [nphase, 2],
@@ -368,7 +369,7 @@ def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_
     info = hom_result(iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
                       err_n=err_n.ctypes.data)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
-                          check_every=0, diverge_window=0, use_graph=0, passes=HOM_PASSES_AUTO, max_radix=0)
+                          check_every=0, diverge_window=0, use_graph=0, passes=int(passes), max_radix=0)
     with torch.cuda.device(device):
         code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                         c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),

@@ -54,8 +54,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
         common += ["-DHOM_GREEN_TW2=%d" % int(os.environ["HOM_GREEN_TW2"])]
     if os.environ.get("HOM_ROW_TW2"):  # row pass with a scalar twiddle table (tuning)
         common += ["-DHOM_ROW_TW2=%d" % int(os.environ["HOM_ROW_TW2"])]
-    if os.environ.get("HOM_ROW_U"):  # row-pass load batch (tuning)
-        common += ["-DHOM_ROW_U=%d" % int(os.environ["HOM_ROW_U"])]
     if os.environ.get("HOM_FAST3D_THREADS"):  # threads per CTA of the specialised 3D passes (tuning)
         common += ["-DHOM_FAST3D_THREADS=%d" % int(os.environ["HOM_FAST3D_THREADS"])]
     if os.environ.get("HOM_FAST_THREADS"):  # threads per CTA of the specialised 2D passes (tuning)

@@ -129,6 +129,7 @@ extern "C" void hom_release(void) {
   }
   g_cache.clear();
   release_backward_buffers();
+  release_graphs();
   fast2d_release();
   cudaSetDevice(cur);
 }

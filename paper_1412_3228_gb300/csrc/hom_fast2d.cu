@@ -23,6 +23,7 @@
 // Green pass keeps its displacement-like state g as [load][column pair][position][4 complex].
 // Both layouts are private to these passes: the initial state and the output fields are written
 // by the kernels here.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -41,9 +42,6 @@ namespace {
 #ifndef HOM_ROW_TW2
 #define HOM_ROW_TW2 1    // row pass with a scalar twiddle table (three CTAs per SM)
 #endif
-#ifndef HOM_ROW_U
-#define HOM_ROW_U (HOM_ROW_TW2 ? 1 : 4)  // row-pass load batch (items in flight per thread; 1 measured best at 80 registers)
-#endif
 constexpr int NP = 3;  // lane pairs per position (2D Mandel components)
 constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};  // sizes with specialised 2D passes
 
@@ -58,6 +56,12 @@ __device__ __forceinline__ size_t tile_index(const CellDev& c, int n, int l, int
 
 constexpr uint32_t kLabel8Mixed = 255;  // one-byte label of a mixed voxel
 
+constexpr int kRowSpare = 2 * NP * kFastRows;  // float4 entries of the row pass's spare landing area
+template <int N>
+__device__ __forceinline__ float4* row_slot(float4* s, float4* spare, int p, int k, int r) {
+  return row_slot_p<N, NP, NP>(s, spare, p, k, r);
+}
+
 // ------------------------------------------------------------------ row pass
 // eps (stored x half-spectra) -> inverse x-DFT -> tau = sigma - c0 : eps -> forward x-DFT -> tau.
 // OUT: the final fields eps and sigma of the returned iterate (real, solver output layout).
@@ -66,8 +70,8 @@ struct RowShared {
   float dc[kMaxLoads][2][kFastRows][NP];     // [load][eps row mean, tau row sum][row][comp]
 };
 
-template <int N, bool OUT>
-__device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, const CellDev& c,
+template <int N, bool OUT, bool SRC>
+__device__ __forceinline__ void row_body(const SolveArgs& A, int task, const TaskR& t, const CellDev& c,
                                          const FastPlanDev& fp, float4* s, RowShared& sh) {
   constexpr int H = (N + 1) / 2;
   constexpr int P = (H + 1) / 2;  // kx pairs holding data
@@ -104,12 +108,13 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
 #if HOM_ROW_TW2
   float2* tws = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16);
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT) cp16(tws + 2 * i, fp.tw2 + 2 * i);
-  float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + (N + 1) / 2);
+  float4* spare = s + N * NP + kFastRows * NL / 16 + (N + 1) / 2;
 #else
   float4* tws = s + N * NP + kFastRows * NL / 16;
   for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
-  float2* sph = reinterpret_cast<float2*>(s + N * NP + kFastRows * NL / 16 + N);
+  float4* spare = s + N * NP + kFastRows * NL / 16 + N;
 #endif
+  float2* sph = reinterpret_cast<float2*>(spare + kRowSpare);
   cp_commit();
   // per local phase (lam - lam0, 2 mu - 2 mu0) for the pure-voxel update (visible after the next barrier)
   for (int i = threadIdx.x; i < c.nph; i += kT) {
@@ -121,47 +126,54 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
     const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
-    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component; item
-    // (p, k) reads rows y0..y0+3 of pair p (U items per round: 4 U loads in flight per thread)
-    constexpr int U = HOM_ROW_U;
-    for (int f0 = threadIdx.x; f0 < P * NP; f0 += U * kT) {
-      float4 v[U][kFastRows];
+    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component.  Item
+    // (p, k) = kx pair p, component k: its four row values (one 16-byte lane pair each) land, by
+    // asynchronous copies all in flight at once, in the tile slots of the four line positions
+    // they produce (row_slot), and are turned into line values in place below.  Rows beyond the
+    // task (r >= nr) are zero-filled by the copy itself.
+    for (int f = threadIdx.x; f < P * NP; f += kT) {
+      const int p = f / NP, k = f - p * NP;
+      const float4* src = ein + tile_index(c, N, l, p, y0) + k;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int f = f0 + u * kT;
-        const int p = f / NP, k = f - p * NP;
-        const size_t b = tile_index(c, N, l, p, y0) + k;
+      for (int r = 0; r < kFastRows; ++r)
+        cp16z(row_slot<N>(s, spare, p, k, r), src + (size_t)(r < nr ? r : 0) * NP, r < nr ? 16u : 0u);
+    }
+    cp_commit();
+    // the next active load's rows of every pair (192 contiguous bytes each) -> L2, so that its
+    // copies above hit L2 while this load's transforms run
+    if (la + 1 < nal) {
+      const float4* nx = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + s_al[la + 1]] & 1) : (it & 1)]);
+      for (int p = threadIdx.x; p < P; p += kT)
+        prefetch_l2(nx + tile_index(c, N, s_al[la + 1], p, y0), (unsigned)(nr * NP * sizeof(float4)));
+    }
+    cp_wait_all();
+    __syncthreads();
+    for (int f = threadIdx.x; f < P * NP; f += kT) {
+      const int p = f / NP, k = f - p * NP;
+      float4 v[kFastRows];
 #pragma unroll
-        for (int r = 0; r < kFastRows; ++r) v[u][r] = (f < P * NP && r < nr) ? ein[b + (size_t)r * NP] : z4;
-      }
+      for (int r = 0; r < kFastRows; ++r) v[r] = *row_slot<N>(s, spare, p, k, r);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int f = f0 + u * kT;
-        if (f >= P * NP) continue;
-        const int p = f / NP, k = f - p * NP;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int kx = 2 * p + h;
-          if (kx >= H) break;
-          // row r at kx: (re, im) = lane h of v[u][r]
-          const float2 q0 = h ? make_float2(v[u][0].y, v[u][0].w) : make_float2(v[u][0].x, v[u][0].z);
-          const float2 q1 = h ? make_float2(v[u][1].y, v[u][1].w) : make_float2(v[u][1].x, v[u][1].z);
-          const float2 q2 = h ? make_float2(v[u][2].y, v[u][2].w) : make_float2(v[u][2].x, v[u][2].z);
-          const float2 q3 = h ? make_float2(v[u][3].y, v[u][3].w) : make_float2(v[u][3].x, v[u][3].z);
-          // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
-          s[kx * NP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
-          if (kx > 0) {
-            s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
-          } else {
-            s_dc[la][0][0][k] = q0.x;
-            s_dc[la][0][1][k] = q1.x;
-            s_dc[la][0][2][k] = q2.x;
-            s_dc[la][0][3][k] = q3.x;
-          }
+      for (int h = 0; h < 2; ++h) {
+        const int kx = 2 * p + h;
+        if (kx >= H) break;
+        // row r at kx: (re, im) = lane h of v[r]
+        const float2 q0 = h ? make_float2(v[0].y, v[0].w) : make_float2(v[0].x, v[0].z);
+        const float2 q1 = h ? make_float2(v[1].y, v[1].w) : make_float2(v[1].x, v[1].z);
+        const float2 q2 = h ? make_float2(v[2].y, v[2].w) : make_float2(v[2].x, v[2].z);
+        const float2 q3 = h ? make_float2(v[3].y, v[3].w) : make_float2(v[3].x, v[3].z);
+        // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
+        s[kx * NP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
+        if (kx > 0) {
+          s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
+        } else {
+          s_dc[la][0][0][k] = q0.x;
+          s_dc[la][0][1][k] = q1.x;
+          s_dc[la][0][2][k] = q2.x;
+          s_dc[la][0][3][k] = q3.x;
         }
       }
     }
-    cp_wait_all();
     __syncthreads();
     fft_dif_p<NP, N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
@@ -233,6 +245,30 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) o[k] = make_float4(out[k][0], out[k][2], out[k][1], out[k][3]);
+      }
+      if constexpr (SRC) {
+        // adjoint solve: the stiffness acts on w - S, so tau = (c~ - c0) : w - c~ : S, with the
+        // source S (real field, solver output layout) read at the rows' voxels
+        const int x = __ldg(fp.iperm + pos);
+        const float* S = static_cast<const float*>(A.src) + c.fld_off + (size_t)l * NP * c.nv + (size_t)y0 * N + x;
+        float cs[NP][kFastRows];
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+#pragma unroll
+          for (int k = 0; k < NP; ++k) cs[k][r] = 0.f;
+          if (r >= nr) continue;
+          const uint32_t L = mixed ? lab[r] : (uint32_t)__ldg(A.cell_phases + c.ph_off + lab[r]);
+          const float* C = (L & HOM_MIXED_BIT) ? A.mixed_c32 + (size_t)(L & ~HOM_MIXED_BIT) * 6 : A.phase_c32 + (size_t)L * 6;
+          float sv[NP];
+#pragma unroll
+          for (int k = 0; k < NP; ++k) sv[k] = __ldg(S + (size_t)k * c.nv + (size_t)r * N);
+          cs[0][r] = __ldg(C) * sv[0] + __ldg(C + 1) * sv[1] + __ldg(C + 2) * sv[2];
+          cs[1][r] = __ldg(C + 1) * sv[0] + __ldg(C + 3) * sv[1] + __ldg(C + 4) * sv[2];
+          cs[2][r] = __ldg(C + 2) * sv[0] + __ldg(C + 4) * sv[1] + __ldg(C + 5) * sv[2];
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+          o[k] = make_float4(o[k].x - cs[k][0], o[k].y - cs[k][2], o[k].z - cs[k][1], o[k].w - cs[k][3]);
       }
       if (OUT) {
         // real fields of rows y0 + r at x = iperm[pos]
@@ -316,28 +352,48 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, const TaskR& t, con
       const double se = (double)N * (2.0 * c.mu0 * (double)s_dc[la][0][r][k] + (k < 2 ? c.lam0 * tr : 0.0));
       acc += (double)s_dc[la][1][r][k] + se;
     }
-    A.partR[((size_t)blockIdx.x * A.L + s_al[la]) * NP + k] = acc;
+    A.partR[((size_t)task * A.L + s_al[la]) * NP + k] = acc;
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_ROW,
               (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N));
 }
 
+// L2 prefetch of the first active load of row task `task` (every pair's rows, 16 * 3 * nrows
+// contiguous bytes each), issued while the CTA still works on its current task.
 template <bool OUT>
-__global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A) {
+__device__ __forceinline__ void prefetch_row_task(const SolveArgs& A, int task) {
+  const TaskR t = A.tR[task];
+  const CellDev c = A.cells[t.cell];
+  int l = -1;
+  for (int q = 0; q < A.L && l < 0; ++q)
+    if (OUT || A.active[t.cell * A.L + q]) l = q;
+  if (l < 0) return;
+  const float4* e = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (*A.it_dev & 1)]);
+  const int P = (c.n / 2 + 2) / 2;
+  for (int p = threadIdx.x; p < P; p += kT)
+    prefetch_l2(e + tile_index(c, c.n, l, p, t.row0), (unsigned)(t.nrows * NP * sizeof(float4)));
+}
+
+// One CTA per task.  `ahead` is the number of CTAs resident on the device at once: task b + ahead
+// is about the one that starts when this CTA ends, so CTA b prefetches its first load into L2.
+template <bool OUT, bool SRC>
+__global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A, int ntasks, int ahead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
-  const TaskR t = A.tR[blockIdx.x];
+  const int task = blockIdx.x;
+  if (task + ahead < ntasks) prefetch_row_task<OUT>(A, task + ahead);
+  const TaskR t = A.tR[task];
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 45: row_body<45, OUT>(A, t, c, fp, s, sh); break;
-    case 75: row_body<75, OUT>(A, t, c, fp, s, sh); break;
-    case 135: row_body<135, OUT>(A, t, c, fp, s, sh); break;
-    case 225: row_body<225, OUT>(A, t, c, fp, s, sh); break;
-    case 405: row_body<405, OUT>(A, t, c, fp, s, sh); break;
-    case 1215: row_body<1215, OUT>(A, t, c, fp, s, sh); break;
+    case 45: row_body<45, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 75: row_body<75, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 135: row_body<135, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 225: row_body<225, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 405: row_body<405, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 1215: row_body<1215, OUT, SRC>(A, task, t, c, fp, s, sh); break;
     default: break;
   }
 }
@@ -361,7 +417,7 @@ __global__ void k_init_f2d(SolveArgs A, int ncells) {
 // ------------------------------------------------------------------ Green pass
 // tau (mixed domain) -> forward y-DFT -> Gamma0 and the residual on J (eq. 2) -> inverse y-DFT -> eps.
 template <int N>
-__device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, const CellDev& c,
+__device__ __forceinline__ void green_body(const SolveArgs& A, int task, const TaskL& t, const CellDev& c,
                                            const FastPlanDev& fp, float4* s) {
   constexpr int H = (N + 1) / 2;
   const int cl = t.cell * A.L + t.load;
@@ -495,8 +551,8 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
     double tot[2];
     block_sum<float, 2, kT>(vv, tot);  // contains the barrier before the inverse transform
     if (threadIdx.x == 0) {
-      A.partC[2 * (size_t)blockIdx.x] = tot[0];
-      A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
+      A.partC[2 * (size_t)task] = tot[0];
+      A.partC[2 * (size_t)task + 1] = tot[1];
     }
   }
   fft_dit_p<NP, N, false>(s, tws);  // inverse: natural order
@@ -508,19 +564,40 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, const TaskL& t, c
   }
 }
 
-__global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveArgs A) {
+// L2 prefetch of Green task `task`'s tau tile and g block (contiguous, in 4 KB pieces).
+__device__ __forceinline__ void prefetch_green_task(const SolveArgs& A, int task) {
+  const TaskL t = A.tC[task];
+  if (!A.active[t.cell * A.L + t.load]) return;
+  const CellDev c = A.cells[t.cell];
+  const char* tau = reinterpret_cast<const char*>(static_cast<const float4*>(A.tau) + tile_index(c, c.n, t.load, t.kx0 / 2, 0));
+  const char* g = reinterpret_cast<const char*>(static_cast<const float4*>(A.g) +
+                                                (c.g_off + ((size_t)t.load * (c.Hp / 2) + (size_t)(t.kx0 / 2)) * c.n * 4) / 2);
+  const unsigned bt = (unsigned)c.n * NP * sizeof(float4), bg = (unsigned)c.n * 2 * sizeof(float4);
+  constexpr unsigned kPiece = 4096;
+  const unsigned nt = (bt + kPiece - 1) / kPiece, ng = (bg + kPiece - 1) / kPiece;
+  for (unsigned i = threadIdx.x; i < nt + ng; i += kT) {
+    const bool on_t = i < nt;
+    const unsigned o = (on_t ? i : i - nt) * kPiece, b = on_t ? bt : bg;
+    prefetch_l2((on_t ? tau : g) + o, min(kPiece, b - o));
+  }
+}
+
+// One CTA per task; CTA b prefetches task b + ahead into L2 (see k_row_f2d).
+__global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveArgs A, int ntasks, int ahead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
-  const TaskL t = A.tC[blockIdx.x];
+  const int task = blockIdx.x;
+  if (task + ahead < ntasks) prefetch_green_task(A, task + ahead);
+  const TaskL t = A.tC[task];
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 45: green_body<45>(A, t, c, fp, s); break;
-    case 75: green_body<75>(A, t, c, fp, s); break;
-    case 135: green_body<135>(A, t, c, fp, s); break;
-    case 225: green_body<225>(A, t, c, fp, s); break;
-    case 405: green_body<405>(A, t, c, fp, s); break;
-    case 1215: green_body<1215>(A, t, c, fp, s); break;
+    case 45: green_body<45>(A, task, t, c, fp, s); break;
+    case 75: green_body<75>(A, task, t, c, fp, s); break;
+    case 135: green_body<135>(A, task, t, c, fp, s); break;
+    case 225: green_body<225>(A, task, t, c, fp, s); break;
+    case 405: green_body<405>(A, task, t, c, fp, s); break;
+    case 1215: green_body<1215>(A, task, t, c, fp, s); break;
     default: break;
   }
 }
@@ -668,12 +745,13 @@ void fast2d_release() {
   g_fast_cache.clear();
 }
 
-// row: tile | labels of 4 rows | twiddles;  Green: tile | twiddles | wave numbers
-// row: tile | one-byte labels of 4 rows | twiddles | per-phase update constants
+// row: tile | one-byte labels of 4 rows | twiddles | spare landing slots | per-phase update constants
+// Green: tile | twiddles | wave numbers
 size_t fast2d_smem_row(int nmax, int nphase_cell) {
   const size_t labels = (size_t)kFastRows * ((nmax + 15) / 16 * 16);
   const size_t tw = HOM_ROW_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
-  return (size_t)nmax * NP * sizeof(float4) + labels + tw + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
+  return (size_t)nmax * NP * sizeof(float4) + labels + tw + (size_t)kRowSpare * sizeof(float4) +
+         ((size_t)nphase_cell * 8 + 15) / 16 * 16;
 }
 size_t fast2d_smem_green(int nmax) {
   const size_t tw = HOM_GREEN_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
@@ -689,16 +767,22 @@ int opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
-  int rc = opt_in(k_row_f2d<false>, smem);
+  if (A.src) {  // adjoint solve: the constitutive step takes the source term
+    int rc = opt_in(k_row_f2d<false, true>, smem);
+    if (rc != HOM_OK) return rc;
+    k_row_f2d<false, true><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f2d<false, true>, kT, smem));
+    return HOM_OK;
+  }
+  int rc = opt_in(k_row_f2d<false, false>, smem);
   if (rc != HOM_OK) return rc;
-  k_row_f2d<false><<<ntasks, kT, smem, st>>>(A);
+  k_row_f2d<false, false><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f2d<false, false>, kT, smem));
   return HOM_OK;
 }
 
 int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
-  int rc = opt_in(k_row_f2d<true>, smem);
+  int rc = opt_in(k_row_f2d<true, false>, smem);
   if (rc != HOM_OK) return rc;
-  k_row_f2d<true><<<ntasks, kT, smem, st>>>(A);
+  k_row_f2d<true, false><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f2d<true, false>, kT, smem));
   return HOM_OK;
 }
 
@@ -711,7 +795,7 @@ int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st) {
 int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
   int rc = opt_in(k_green_f2d, smem);
   if (rc != HOM_OK) return rc;
-  k_green_f2d<<<ntasks, kT, smem, st>>>(A);
+  k_green_f2d<<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_green_f2d, kT, smem));
   return HOM_OK;
 }
 

@@ -48,8 +48,10 @@ struct RowShared3 {
   float dc[kMaxLoads][2][kFastRows][NP];  // [load][eps row mean, tau row sum][row][comp]
 };
 
-template <int N, bool OUT>
-__device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, const CellDev& c,
+constexpr int kRowSpare3 = 2 * NP * kFastRows;  // float4 entries of the row pass's spare landing area
+
+template <int N, bool OUT, bool SRC>
+__device__ __forceinline__ void row3_body(const SolveArgs& A, int task, const TaskR& t, const CellDev& c,
                                           const FastPlanDev& fp, float4* s, RowShared3& sh) {
   constexpr int H = (N + 1) / 2;
   constexpr int P = (H + 1) / 2;
@@ -77,7 +79,8 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
   }
   float2* tws = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16);
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
-  float2* sph = reinterpret_cast<float2*>(s + N * SP + kFastRows * NL / 16 + (N + 1) / 2);
+  float4* spare = s + N * SP + kFastRows * NL / 16 + (N + 1) / 2;
+  float2* sph = reinterpret_cast<float2*>(spare + kRowSpare3);
   cp_commit();
   for (int i = threadIdx.x; i < c.nph; i += kT3) {
     const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 21;
@@ -88,13 +91,30 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
   for (int la = 0; la < nal; ++la) {
     const int l = sh.al[la];
     const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
-    // 1. four half-spectrum rows -> two Hermitian-extended lines per component
+    // 1. four half-spectrum rows -> two Hermitian-extended lines per component: the row values of
+    // item (p, k) land by asynchronous copies in the slots of the line positions they produce
+    // (row_slot_p) and are expanded in place (see the 2D row pass)
     for (int f = threadIdx.x; f < P * NP; f += kT3) {
       const int p = f / NP, k = f - p * NP;
-      const size_t b = idx3(c, N, l, p, z, y0) + k;
+      const float4* src = ein + idx3(c, N, l, p, z, y0) + k;
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r)
+        cp16z(row_slot_p<N, NP, SP>(s, spare, p, k, r), src + (size_t)(r < nr ? r : 0) * NP, r < nr ? 16u : 0u);
+    }
+    cp_commit();
+    if (la + 1 < nal) {  // the next active load's rows -> L2
+      const int ln = sh.al[la + 1];
+      const float4* nx = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + ln] & 1) : (it & 1)]);
+      for (int p = threadIdx.x; p < P; p += kT3)
+        prefetch_l2(nx + idx3(c, N, ln, p, z, y0), (unsigned)(nr * NP * sizeof(float4)));
+    }
+    cp_wait_all();
+    __syncthreads();
+    for (int f = threadIdx.x; f < P * NP; f += kT3) {
+      const int p = f / NP, k = f - p * NP;
       float4 v[kFastRows];
 #pragma unroll
-      for (int r = 0; r < kFastRows; ++r) v[r] = r < nr ? ein[b + (size_t)r * NP] : z4;
+      for (int r = 0; r < kFastRows; ++r) v[r] = *row_slot_p<N, NP, SP>(s, spare, p, k, r);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int kx = 2 * p + h;
@@ -114,7 +134,6 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
         }
       }
     }
-    cp_wait_all();
     __syncthreads();
     fft_dif_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: eps at digit-reversed positions
 
@@ -176,6 +195,32 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) o[k] = make_float4(out[k][0], out[k][2], out[k][1], out[k][3]);
+      }
+      if constexpr (SRC) {
+        // adjoint solve: tau = (c~ - c0) : w - c~ : S, the source S (real field, solver output
+        // layout) read at the rows' voxels
+        const int x = __ldg(fp.iperm + pos);
+        const float* Sb = static_cast<const float*>(A.src) + c.fld_off + (size_t)l * NP * c.nv + (size_t)t.row0 * N + x;
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          if (r >= nr) break;
+          const uint32_t L = lab[r] == kLabel8Mixed ? __ldg(A.label + c.vox_off + (size_t)(t.row0 + r) * N + x)
+                                                    : (uint32_t)__ldg(A.cell_phases + c.ph_off + lab[r]);
+          const float* C = (L & HOM_MIXED_BIT) ? A.mixed_c32 + (size_t)(L & ~HOM_MIXED_BIT) * 21 : A.phase_c32 + (size_t)L * 21;
+          float sv[NP];
+#pragma unroll
+          for (int k = 0; k < NP; ++k) sv[k] = __ldg(Sb + (size_t)k * c.nv + (size_t)r * N);
+#pragma unroll
+          for (int I = 0; I < NP; ++I) {
+            float cs = 0.f;
+#pragma unroll
+            for (int J = 0; J < NP; ++J) cs = fmaf(__ldg(C + packed_index(NP, I, J)), sv[J], cs);
+            if (r == 0) o[I].x -= cs;
+            else if (r == 1) o[I].z -= cs;
+            else if (r == 2) o[I].y -= cs;
+            else o[I].w -= cs;
+          }
+        }
       }
       if (OUT) {
         const int x = __ldg(fp.iperm + pos);
@@ -256,27 +301,47 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, const TaskR& t, co
       const double se = (double)N * (2.0 * c.mu0 * (double)sh.dc[la][0][r][k] + (k < 3 ? c.lam0 * tr : 0.0));
       acc += (double)sh.dc[la][1][r][k] + se;
     }
-    A.partR[((size_t)blockIdx.x * A.L + sh.al[la]) * NP + k] = acc;
+    A.partR[((size_t)task * A.L + sh.al[la]) * NP + k] = acc;
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_ROW,
               (unsigned long long)(2 * (size_t)nr * nal * NP * H * sizeof(float2) + (size_t)nr * N));
 }
 
+// L2 prefetch of the first active load of row task `task` (every pair's rows, contiguous).
 template <bool OUT>
-__global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A) {
+__device__ __forceinline__ void prefetch_row3_task(const SolveArgs& A, int task) {
+  const TaskR t = A.tR[task];
+  const CellDev c = A.cells[t.cell];
+  int l = -1;
+  for (int q = 0; q < A.L && l < 0; ++q)
+    if (OUT || A.active[t.cell * A.L + q]) l = q;
+  if (l < 0) return;
+  const float4* e = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (*A.it_dev & 1)]);
+  const int z = t.row0 / c.n, y0 = t.row0 - z * c.n;
+  const int P = (c.n / 2 + 2) / 2;
+  for (int p = threadIdx.x; p < P; p += kT3)
+    prefetch_l2(e + idx3(c, c.n, l, p, z, y0), (unsigned)(t.nrows * NP * sizeof(float4)));
+}
+
+// One CTA per task; CTA b prefetches the first load of task b + ahead (about the task that starts
+// when this CTA ends: `ahead` CTAs are resident at once) into L2.
+template <bool OUT, bool SRC>
+__global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks, int ahead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared3 sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
-  const TaskR t = A.tR[blockIdx.x];
+  const int task = blockIdx.x;
+  if (task + ahead < ntasks) prefetch_row3_task<OUT>(A, task + ahead);
+  const TaskR t = A.tR[task];
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 27: row3_body<27, OUT>(A, t, c, fp, s, sh); break;
-    case 45: row3_body<45, OUT>(A, t, c, fp, s, sh); break;
-    case 81: row3_body<81, OUT>(A, t, c, fp, s, sh); break;
-    case 135: row3_body<135, OUT>(A, t, c, fp, s, sh); break;
-    case 243: row3_body<243, OUT>(A, t, c, fp, s, sh); break;
+    case 27: row3_body<27, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 45: row3_body<45, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 81: row3_body<81, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 135: row3_body<135, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 243: row3_body<243, OUT, SRC>(A, task, t, c, fp, s, sh); break;
     default: break;
   }
 }
@@ -524,11 +589,12 @@ bool fast3d_size(int n) {
   return false;
 }
 
-// row: tile | one-byte labels of 4 rows | twiddles | per-phase constants;  y: tile | twiddles;
+// row: tile | one-byte labels of 4 rows | twiddles | spare landing slots | per-phase constants;
+// y: tile | twiddles;
 // Green: tile | twiddles | wave numbers
 size_t fast3d_smem_row(int nmax, int nphase_cell) {
   return (size_t)nmax * SP * sizeof(float4) + (size_t)kFastRows * ((nmax + 15) / 16 * 16) +
-         ((size_t)nmax + 1) / 2 * 16 + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
+         ((size_t)nmax + 1) / 2 * 16 + (size_t)kRowSpare3 * sizeof(float4) + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
 }
 size_t fast3d_smem_y(int nmax) { return (size_t)nmax * SP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16; }
 size_t fast3d_smem_green(int nmax) {
@@ -538,11 +604,14 @@ size_t fast3d_smem_green(int nmax) {
 int fast3d_row(const SolveArgs& A, unsigned ntasks, size_t smem, bool out, cudaStream_t st) {
   int rc;
   if (out) {
-    if ((rc = opt_in3(k_row_f3d<true>, smem)) != HOM_OK) return rc;
-    k_row_f3d<true><<<ntasks, kT3, smem, st>>>(A);
+    if ((rc = opt_in3(k_row_f3d<true, false>, smem)) != HOM_OK) return rc;
+    k_row_f3d<true, false><<<ntasks, kT3, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f3d<true, false>, kT3, smem));
+  } else if (A.src) {  // adjoint solve: the constitutive step takes the source term
+    if ((rc = opt_in3(k_row_f3d<false, true>, smem)) != HOM_OK) return rc;
+    k_row_f3d<false, true><<<ntasks, kT3, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f3d<false, true>, kT3, smem));
   } else {
-    if ((rc = opt_in3(k_row_f3d<false>, smem)) != HOM_OK) return rc;
-    k_row_f3d<false><<<ntasks, kT3, smem, st>>>(A);
+    if ((rc = opt_in3(k_row_f3d<false, false>, smem)) != HOM_OK) return rc;
+    k_row_f3d<false, false><<<ntasks, kT3, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f3d<false, false>, kT3, smem));
   }
   return HOM_OK;
 }

@@ -7,7 +7,10 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hom_common.cuh"
+#include "hom_fast2d.h"
 
 namespace hom {
 namespace {
@@ -16,6 +19,29 @@ namespace {
 #define HOM_FAST_THREADS 256
 #endif
 constexpr int kT = HOM_FAST_THREADS;  // threads per CTA (a build-time tunable)
+
+// CTAs of `kernel` resident on the device at once (the prefetch distance of the passes), cached
+// per kernel for the last (device, shared-memory size) asked.
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem) {
+  struct Last { const void* k = nullptr; int dev = -1; size_t smem = 0; int val = 0; };
+  static thread_local Last last[4];
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  const void* kp = reinterpret_cast<const void*>(kernel);
+  for (const Last& e : last)
+    if (e.k == kp && e.dev == dev && e.smem == smem) return e.val;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  static thread_local int next = 0;
+  last[next] = Last{kp, dev, smem, std::max(sms, 1) * per_sm};
+  const int v = last[next].val;
+  next = (next + 1) & 3;
+  return v;
+}
 
 // ------------------------------------------------------------------ packed FP32x2 arithmetic
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -32,6 +58,35 @@ __device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// 16-byte asynchronous copy that reads `bytes` (16 or 0) from global memory and zero-fills the rest.
+__device__ __forceinline__ void cp16z(void* smem_dst, const void* gsrc, unsigned bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(bytes) : "memory");
+}
+
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2; no
+// completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* gsrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+
+// Landing slot of row r of kx pair p, component k, in a row pass (4 real rows = 2 complex lines).  A pair (kx = 2p, 2p + 1)
+// produces the line positions 2p, 2p + 1, N - 2p - 1 and N - 2p, so its four rows land in those
+// slots and the pair is expanded in place without touching another pair's data.  Pair 0 (kx = 0
+// maps to itself) and, when the half spectrum has an odd length H, the last pair (kx = H is
+// absent, so its positions collide) land in a spare area instead; the slots they produce (0, 1,
+// N - 1, and H - 1, H) are no other pair's landing slots.
+// (NC lane pairs per position, SP float4 between positions in shared memory; the spare area holds
+// 2 NC kFastRows float4.)
+template <int N, int NC, int SP>
+__device__ __forceinline__ float4* row_slot_p(float4* s, float4* spare, int p, int k, int r) {
+  constexpr int H = (N + 1) / 2, P = (H + 1) / 2;
+  if (p == 0) return spare + k * kFastRows + r;
+  if ((H & 1) && p == P - 1) return spare + (NC + k) * kFastRows + r;
+  const int pos = r < 2 ? 2 * p + r : N - 2 * p - (3 - r);  // 2p, 2p + 1, N - 2p - 1, N - 2p
+  return s + pos * SP + k;
+}
 
 // Two complex numbers, one per line: re = (re_A, re_B), im = (im_A, im_B).
 struct P2 {

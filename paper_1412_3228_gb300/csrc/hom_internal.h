@@ -47,6 +47,7 @@ inline void set_plan_pointers(Plan& p, unsigned char* base) {
 // Device scratch owned by the library (grown on demand, freed by hom_release).
 int get_workspace(size_t bytes, void** ptr);
 void release_backward_buffers();
+void release_graphs();  // cached whole-solve graphs
 
 // ------------------------------------------------------------------ validation
 bool grid_supported(int n);

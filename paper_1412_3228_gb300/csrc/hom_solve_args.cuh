@@ -54,6 +54,9 @@ struct SolveArgs {
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
   const uint8_t* label8;      // specialised row pass: local phase index (255: mixed), x in transform order
   const int* cell_phases;     // specialised row pass: per-cell lists of the phases of pure voxels
+  // whole-solve graph: the control kernel sets the WHILE condition of the graph's iteration loop
+  unsigned long long cond;    // cudaGraphConditionalHandle
+  int use_cond;
 };
 
 // Kahan-compensated accumulation in the field precision: the running sum s and the negated

@@ -20,6 +20,8 @@
 #include <cmath>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -620,6 +622,9 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
       *A.nactive = tot;
       *A.it_dev = it + 1;
       *A.done = 0u;
+      // whole-solve graph: run another iteration while a pair is active and the budget allows
+      // (the host loop's bound: at most max_iter + 1 iterations)
+      if (A.use_cond) cudaGraphSetConditional(A.cond, (tot > 0 && it + 1 <= A.max_iter) ? 1u : 0u);
     }
   }
 }
@@ -902,6 +907,39 @@ struct Timer {
   }
 };
 
+// Instantiated whole-solve graphs, kept across calls.  A graph bakes in the kernel arguments
+// (pointers into the workspace and the caller's material, sizes, options) and launch shapes, so
+// the key is those bytes; a call with the same key replays the cached graph.
+struct GraphEntry {
+  int dev;
+  std::string key;
+  cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;  // most recently used last
+constexpr size_t kMaxGraphs = 8;
+
+cudaGraphExec_t find_graph(int dev, const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size(); ++i)
+    if (g_graphs[i].dev == dev && g_graphs[i].key == key) {
+      GraphEntry e = g_graphs[i];
+      g_graphs.erase(g_graphs.begin() + i);
+      g_graphs.push_back(e);
+      return e.exec;
+    }
+  return nullptr;
+}
+
+void keep_graph(int dev, const std::string& key, cudaGraphExec_t exec) {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  if (g_graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  g_graphs.push_back(GraphEntry{dev, key, exec});
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a{};
@@ -941,7 +979,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     c0 = c0_cg.data();
   }
   // opts->passes == HOM_PASSES_GENERIC keeps every solve on the generic passes
-  lay.fast = std::is_same<T, float>::value && !adj && !cg && opts->passes != HOM_PASSES_GENERIC;
+  lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC;
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1066,7 +1104,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemsetAsync(ws + o_cgint, 0, (size_t)npairs * 2 * sizeof(int), st));
   }
 
-  SolveArgs A{};
+  SolveArgs A;
+  std::memset(&A, 0, sizeof(A));  // the bytes of A key the graph cache: no stray padding
   A.cells = reinterpret_cast<const CellDev*>(ws + o_cells);
   A.plans = reinterpret_cast<const Plan*>(ws + o_plans);
   A.label = mat->label;
@@ -1212,44 +1251,76 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     HOM_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  // Graphs are captured on a private stream (the legacy default stream cannot be captured) and
-  // launched on the caller's stream.
-  cudaGraphExec_t gexec = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  while (host_nactive > 0) {
+  if (opts->use_graph && !out->stats && !cg) {
+    // The whole solve as one graph launch: a conditional WHILE node whose body is one iteration
+    // (the passes and the control kernel); the control kernel clears the condition once no pair is
+    // active or max_iter + 1 iterations ran, so the host waits once instead of polling.  The body
+    // is captured on a private stream (the legacy default stream cannot be captured); the
+    // instantiated graph is cached across calls with the same arguments.
+    int dev = 0;
+    HOM_CUDA_TRY(cudaGetDevice(&dev));
+    SolveArgs K = A;  // the output buffers are not used by the iterations: not part of the key
+    K.out_eps = K.out_sig = nullptr;
+    std::string key(reinterpret_cast<const char*>(&K), sizeof(K));
+    const size_t dims[] = {nR, nC, nY, nCtl, lay.smem_row, lay.smem_green, lay.smem_y, smem_frow, smem_fgreen,
+                           smem_fy, (size_t)lay.fast, (size_t)DIM, sizeof(T), (size_t)MAXR};
+    key.append(reinterpret_cast<const char*>(dims), sizeof(dims));
+    cudaGraphExec_t gexec = find_graph(dev, key);
+    if (!gexec) {
+      cudaGraph_t graph = nullptr;
+      cudaStream_t cap = nullptr;
+      HOM_CUDA_TRY(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle h{};
+      cudaGraphNode_t node{};
+      cudaGraphNodeParams cp{};
+      cudaError_t ce = cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault);
+      if (ce == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+      }
+      if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      if (ce == cudaSuccess)
+        ce = cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        const cudaStream_t user = st;
+        st = cap;  // the launch lambdas use `st`
+        A.cond = h;
+        A.use_cond = 1;
+        one_iteration();
+        A.cond = 0;
+        A.use_cond = 0;
+        st = user;
+        cudaGraph_t body = nullptr;
+        ce = cudaStreamEndCapture(cap, &body);
+      }
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec, graph, 0);
+      if (cap) cudaStreamDestroy(cap);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(HOM_ERR_CUDA, "whole-solve graph: %s", cudaGetErrorString(ce));
+      }
+      keep_graph(dev, key, gexec);
+    }
+    HOM_CUDA_TRY(cudaGraphLaunch(gexec, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  while (host_nactive > 0 && !(opts->use_graph && !out->stats && !cg)) {
     // CG: a verification pass takes a launch without a step, and is followed by a step or a stop
     const int remaining = (cg ? 2 * opts->max_iter + 2 : opts->max_iter + 1) - launched;
     if (remaining <= 0) break;  // the control kernel has stopped every pair by now
     const int k = std::min(check, remaining);
-    if (opts->use_graph && !out->stats) {
-      if (!gexec) {
-        cudaGraph_t graph;
-        HOM_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-        const cudaStream_t user = st;
-        st = cap_stream;  // the launch lambdas and the timer use `st`
-        HOM_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < check; ++i) one_iteration();
-        const cudaError_t ce = cudaStreamEndCapture(cap_stream, &graph);
-        st = user;
-        if (ce != cudaSuccess) {
-          cudaStreamDestroy(cap_stream);
-          return set_error(HOM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-        }
-        HOM_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
-        cudaGraphDestroy(graph);
-      }
-      HOM_CUDA_TRY(cudaGraphLaunch(gexec, st));
-      launched += check;
-    } else {
-      for (int i = 0; i < k; ++i) one_iteration();
-      launched += k;
-    }
+    for (int i = 0; i < k; ++i) one_iteration();
+    launched += k;
     HOM_CUDA_TRY(cudaGetLastError());
     HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     HOM_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (cap_stream) cudaStreamDestroy(cap_stream);
   if (host_nactive > 0) return set_error(HOM_ERR_TIMEOUT, "iteration control did not terminate");
   if (cg) {
     // the returned iterate E + x, in the buffer the output pass reads for each pair
@@ -1301,6 +1372,13 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 }
 
 }  // namespace
+
+void release_graphs() {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& e : g_graphs) cudaGraphExecDestroy(e.exec);
+  g_graphs.clear();
+}
+
 }  // namespace hom
 
 using namespace hom;

@@ -325,6 +325,37 @@ def test_host_outputs_graphs_and_repeatability():
         assert torch.equal(r["sigma"].cpu(), a["sigma"].cpu())
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp64"])
+def test_whole_solve_graph_matches_host_loop(precision):
+    """use_graph runs the whole solve as one graph launch (a conditional WHILE node; the control
+    kernel ends the loop).  On an uneven batch whose pairs stop at different iterations -- some
+    converge, some reach max_iter -- it gives exactly the host loop's results, on repeated calls
+    (the second and third replay the cached graph), and with a different max_iter (another graph)."""
+    base = [(H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER), 10.0), (H.centred_disk_cell(27, rule=H.RULE_VOIGT), 100.0),
+            (H.centred_disk_cell(75, rule=H.RULE_REUSS), 0.1)]
+    phases, cells = [], []
+    for cell, contrast in base:
+        cells.append(H.remap_phases(cell, len(phases)))
+        phases.extend(H.two_phases(contrast))
+    c0 = [H.mean_lame(phases[2 * i:2 * i + 2]) for i in range(len(cells))]
+    mat = hom.hom_filter_build(cells, phases)
+    crit = hom.HOM_CRIT_EN if precision == hom.HOM_FP32 else hom.HOM_CRIT_E
+    for max_iter in (120, 33):
+        kw = dict(precision=precision, criterion=crit, tol=1e-6, max_iter=max_iter)
+        a = hom.hom_solve(mat, np.eye(3), c0, **kw)
+        if max_iter == 120:
+            assert len(np.unique(a["iterations"])) > 2
+        for _ in range(3):
+            g = hom.hom_solve(mat, np.eye(3), c0, use_graph=True, **kw)
+            assert g["code"] == a["code"]
+            assert np.array_equal(g["iterations"], a["iterations"])
+            assert np.array_equal(g["status"], a["status"])
+            assert np.array_equal(g["mean_sigma"], a["mean_sigma"])
+            assert torch.equal(g["eps"].cpu(), a["eps"].cpu())
+        if max_iter == 33:
+            assert (a["status"] == 1).any() and (a["iterations"] <= 33).all()
+
+
 def test_kernel_stats_count_the_work():
     cells = [H.centred_disk_cell(45, rule=H.RULE_VOIGT)]
     phases = H.two_phases(10.0)
