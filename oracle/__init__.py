@@ -153,13 +153,40 @@ def nyquist_mask(dim: int, n: int) -> np.ndarray:
     return out
 
 
-def wave_vectors(dim: int, n: int) -> np.ndarray:
-    """xi_k = 2 pi a for every DFT bin of an n^dim grid, numpy axis order (z,) y, x.
-    Returns [*grid, dim] with component 0 = x, 1 = y, 2 = z."""
-    a = 2.0 * math.pi * signed_frequencies(n).astype(np.float64)
+SCHEME_CONTINUOUS = 0  # eq. (2): the wave vector xi = 2 pi a of the continuous Green operator
+SCHEME_ROTATED = 1     # a modified discrete Green operator (the paper's second category, refs. [1, 11])
+
+
+def wave_vectors(dim: int, n: int, scheme: int = SCHEME_CONTINUOUS) -> np.ndarray:
+    """The wave vector the Green operator and the equilibrium check use at every DFT bin of an
+    n^dim grid, numpy axis order (z,) y, x.  Returns [*grid, dim] with component 0 = x, 1 = y, 2 = z.
+
+    SCHEME_CONTINUOUS: xi_k = 2 pi a (section 2, eq. 2).
+    SCHEME_ROTATED: the modified discrete Green operator of the "rotated" finite-difference scheme
+    (one of the modified operators the paper's introduction cites as the second way to improve the
+    method).  There, strains are symmetric finite-difference gradients of a displacement held at
+    the voxel corners, each derivative averaged over the 2^(d-1) cell edges along its axis, and
+    equilibrium is the adjoint difference of the stress.  The symbol of the derivative along axis
+    j is k_j = (1/(2^(d-1) h)) (e^(i t_j) - 1) prod_{m != j} (e^(i t_m) + 1), t = 2 pi a / n; all d
+    components share the phase i exp(i sum_m t_m / 2), which cancels in the operator, leaving the
+    real vector
+        q_j = (2/h) sin(t_j / 2) prod_{m != j} cos(t_m / 2)        (h = 1/n)
+    in place of xi everywhere: compatible fields are sym(q (x) u_hat), equilibrium is q . sigma_hat
+    = 0, and the Green operator is eq. (2)'s formula evaluated at q."""
+    a = signed_frequencies(n).astype(np.float64)
     grids = np.meshgrid(*([a] * dim), indexing="ij")  # axis order (z,) y, x
     comps = [grids[dim - 1 - c] for c in range(dim)]  # x is the last numpy axis
-    return np.stack(comps, axis=-1)
+    if scheme == SCHEME_CONTINUOUS:
+        return np.stack([2.0 * math.pi * g for g in comps], axis=-1)
+    half = [math.pi * g / n for g in comps]  # t_j / 2
+    out = []
+    for j in range(dim):
+        q = 2.0 * n * np.sin(half[j])
+        for m in range(dim):
+            if m != j:
+                q = q * np.cos(half[m])
+        out.append(q)
+    return np.stack(out, axis=-1)
 
 
 def gamma0_tensor(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
@@ -178,14 +205,14 @@ def gamma0_tensor(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
 
 
 def apply_gamma0(tau_hat: np.ndarray, dim: int, n: int, lam0: float, mu0: float,
-                 chunk: int = 1 << 17) -> np.ndarray:
-    """eq. (2): eps_hat(k) = -Gamma0(k) : tau_hat(k) for k != 0 on J.
+                 chunk: int = 1 << 17, scheme: int = SCHEME_CONTINUOUS) -> np.ndarray:
+    """eq. (2): eps_hat(k) = -Gamma0(k) : tau_hat(k) for k != 0 on J (at the scheme's wave vector).
     tau_hat: complex Mandel field [nc, *grid].  Returns -Gamma0:tau_hat with the k = 0 entry
     left at zero (the caller sets eps_hat(0))."""
     nc = nc_of(dim)
     shape = tau_hat.shape[1:]
     npts = int(np.prod(shape))
-    xi = wave_vectors(dim, n).reshape(npts, dim)
+    xi = wave_vectors(dim, n, scheme).reshape(npts, dim)
     t = mandel_to_tensor2(np.moveaxis(tau_hat.reshape(nc, npts), 0, -1), dim)  # [npts, d, d]
     out = np.zeros((npts, dim, dim), dtype=np.complex128)
     for s in range(0, npts, chunk):
@@ -220,15 +247,16 @@ def _ifft(f: np.ndarray, dim: int) -> np.ndarray:
     return np.fft.ifftn(f, axes=tuple(range(-dim, 0)))
 
 
-def equilibrium_errors(sig_hat: np.ndarray, dim: int, n: int) -> Tuple[float, float]:
+def equilibrium_errors(sig_hat: np.ndarray, dim: int, n: int, scheme: int = SCHEME_CONTINUOUS) -> Tuple[float, float]:
     """Stress-equilibrium criterion of Moulinec & Suquet (ref. [9] of the paper):
         e   = sqrt(sum_{k in J} |xi_k . sigma_hat(k)|^2) / ||sigma_hat(0)||
         e_n = sqrt(sum_{k in J, k != 0} |(xi_k/|xi_k|) . sigma_hat(k)|^2) / ||sigma_hat(0)||
+    with xi the scheme's wave vector (wave_vectors).
     sig_hat: complex Mandel field [nc, *grid] (unnormalised DFT)."""
     nc = nc_of(dim)
     shape = sig_hat.shape[1:]
     npts = int(np.prod(shape))
-    xi = wave_vectors(dim, n).reshape(npts, dim)
+    xi = wave_vectors(dim, n, scheme).reshape(npts, dim)
     t = mandel_to_tensor2(np.moveaxis(sig_hat.reshape(nc, npts), 0, -1), dim)  # [npts, d, d]
     div = np.einsum("pij,pj->pi", t, xi)
     q2 = np.sum(xi * xi, axis=-1)
@@ -254,7 +282,7 @@ def constitutive(ctilde: np.ndarray, eps: np.ndarray) -> np.ndarray:
 
 
 def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
-              tol: float, max_iter: int, criterion: int = CRIT_E) -> Dict:
+              tol: float, max_iter: int, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS) -> Dict:
     """Basic fixed-point scheme for one macroscopic strain E (Mandel [nc]):
         eps^0 = E
         repeat i = 0, 1, ...:
@@ -263,6 +291,7 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
             eps_hat^{i+1}(k) = -Gamma0(k) : tau_hat^i(k)   (k in J, k != 0)
             eps_hat^{i+1}(0) = E (times N_v for the unnormalised DFT)
             eps^{i+1} = inverse DFT
+    (Gamma0 and the error at the scheme's wave vector; SCHEME_CONTINUOUS is eq. 2 itself.)
     Returns the iterate that passed (iterations = number of Green-operator applications)."""
     nc = nc_of(dim)
     grid = (n,) * dim
@@ -276,7 +305,7 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
     it = 0
     while True:
         sigma = constitutive(ctilde, eps)
-        e, e_n = equilibrium_errors(_fft(sigma, dim), dim, n)
+        e, e_n = equilibrium_errors(_fft(sigma, dim), dim, n, scheme)
         errs.append(e)
         errs_n.append(e_n)
         err = e if criterion == CRIT_E else e_n
@@ -289,7 +318,7 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
         if it >= max_iter:
             break
         tau = sigma - constitutive(np.broadcast_to(C0, grid + (nc, nc)), eps)
-        eps_hat = apply_gamma0(_fft(tau, dim), dim, n, lam0, mu0)
+        eps_hat = apply_gamma0(_fft(tau, dim), dim, n, lam0, mu0, scheme=scheme)
         zero = (slice(None),) + (0,) * dim
         eps_hat[zero] = nv * np.asarray(E, dtype=np.float64)
         eps = np.real(_ifft(eps_hat, dim))
@@ -300,10 +329,10 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
 
 
 def solve(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
-          tol: float = 1e-8, max_iter: int = 1000, criterion: int = CRIT_E) -> Dict:
+          tol: float = 1e-8, max_iter: int = 1000, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS) -> Dict:
     """Solve every load case (rows of E, Mandel [L, nc]) independently."""
     E = np.atleast_2d(np.asarray(E, dtype=np.float64))
-    runs = [solve_one(ctilde, dim, n, lam0, mu0, E[l], tol, max_iter, criterion) for l in range(E.shape[0])]
+    runs = [solve_one(ctilde, dim, n, lam0, mu0, E[l], tol, max_iter, criterion, scheme) for l in range(E.shape[0])]
     return dict(eps=np.stack([r["eps"] for r in runs]), sigma=np.stack([r["sigma"] for r in runs]),
                 mean_sigma=np.stack([r["mean_sigma"] for r in runs]),
                 iterations=np.array([r["iterations"] for r in runs]),
