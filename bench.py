@@ -126,7 +126,7 @@ def measured_peak_hbm():
 # --set full capture of the profile case (--profile-case: two 1215^2 cells x 3 loads; traffic grows
 # with the tiles processed, so a launch's traffic is this ratio times its bytes).
 # Valid for the kernels as captured there; None for kernels without a capture.
-TRAFFIC_RATIO = {"row": (110.363 + 54.692) / 215.77, "green": (177.533 + 116.269) / 354.61}
+TRAFFIC_RATIO = {"row": (110.248 + 52.984) / 215.77, "green": (177.549 + 116.346) / 354.61}
 
 
 def golden_ceff():
@@ -271,6 +271,11 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.skip_ensemble:
         ensemble = ensemble_2d(hom, dev)
 
+    # ---- differentiation: FP32 forward + adjoint at 135^3 (von Mises + C_eff loss)
+    backward = None
+    if rank == 0 and not args.skip_3d:
+        backward = backward_135(hom, dev)
+
     # ---- accelerated scheme (conjugate gradients) against the basic scheme at high contrast
     cg = None
     if rank == 0 and not args.skip_cg:
@@ -307,7 +312,7 @@ def run_ours(args, rank, world):
             "fp32_vs_fp64_equal_error": (None if fp64 is None else {
                 "fp32_value": value, "fp64_value": fp64["batched_equal_error"]["value"],
                 "fp64_tol": fp64["batched_equal_error"]["tol"], "ratio": value / fp64["batched_equal_error"]["value"],
-                "fp32_ceff_err": fp32_err, "fp64_ceff_err": fp64["batched_equal_error"]["ceff_max_rel_err"]}), "cufft_comparison": comparison, "spheres3d_243": spheres, "spheres3d_135": spheres135,
+                "fp32_ceff_err": fp32_err, "fp64_ceff_err": fp64["batched_equal_error"]["ceff_max_rel_err"]}), "cufft_comparison": comparison, "spheres3d_243": spheres, "spheres3d_135": spheres135, "backward_135": backward,
             "ensemble2d_256": ensemble, "cg_vs_fixed_point": cg}
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args, pool)
@@ -495,6 +500,65 @@ def spheres_3d(hom, dev, n=243, contrasts=(10.0,), fp64_check=True):
             "iterations": [[int(i) for i in row] for row in r["iterations"]], "spheres": len(base.prims),
             "mixed_voxels": int(mat.mixed_count), "achieved_gbs": kb, "ceff_max_rel_err": err, "ceff_reference": ref,
             "passes": "specialised FP32 3D (row, y forward, Green along z, y inverse)"}
+
+
+def backward_135(hom, dev, n=135):
+    """The differentiation workload: one n^3 random-sphere cell (seed 3000, volume fraction 0.25,
+    radius U[0.05, 0.1], contrast 20, 2-layer filter r = 1 px, 8^3 subgrid), FP32 forward solve of the
+    6 unit loads (fields kept) and FP32 adjoint solve for L = sum_ij (C_ij - T_ij)^2 / |T|^2 +
+    <sigma_vm^2> / <sigma_vm^2>_0 (von Mises term on the xx load; T = C_eff (1 + 0.1 N(0, 1)) symmetrised,
+    seed 3001), both on the specialised 3D passes; e_n < 4e-6 (the FP32 floor at contrast 20 is
+    near 1.2e-6).  Reports the forward and backward times and the adjoint iterations."""
+    import torch
+    cell = H.rsa_spheres_cell(n, seed=3000, vf=0.25, rmin=0.05, rmax=0.1, rule=H.RULE_TWO_LAYER, radius_px=1.0,
+                              subgrid=8, gap_voxels=n / 243.0)
+    phases = H.two_phases(20.0)
+    c0 = H.mean_lame(phases)
+    st = torch.cuda.current_stream()
+    kw = dict(precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=4e-6, max_iter=MAX_ITER)
+
+    def forward():
+        mat = hom.hom_filter_build([cell], phases)
+        fwd = hom.hom_solve(mat, np.eye(6), c0, **kw)
+        return mat, fwd
+
+    def loss_grads(fwd, T=None, vm0=None):
+        C = hom.hom_effective_stiffness(np.eye(6), fwd["mean_sigma"], 3)[0]
+        s = fwd["sigma"].view(6, 6, -1)[0].double()
+        s = s - torch.cat([(s[:3].sum(0, keepdim=True) / 3.0).expand(3, -1), torch.zeros_like(s[3:])])
+        vm2 = float(1.5 * (s * s).sum(0).mean())
+        if T is None:
+            rng = np.random.default_rng(3001)
+            T = C * (1.0 + 0.1 * rng.standard_normal(C.shape))
+            T = 0.5 * (T + T.T)
+            vm0 = vm2
+        G = (2.0 * (C - T) / np.sum(T ** 2))[None]
+        S = torch.zeros((6, 6, n ** 3), dtype=torch.float32, device="cuda")
+        S[0] = (3.0 * s / (n ** 3 * vm0)).float()
+        loss = float(np.sum((C - T) ** 2) / np.sum(T ** 2) + vm2 / vm0)
+        return G, S, T, vm0, loss
+
+    mat, fwd = forward()  # warm-up, and the target of the loss
+    G, S, T, vm0, _ = loss_grads(fwd)
+    hom.hom_solve_backward(mat, fwd, c0, dL_dC=G, dL_dsigma=S, want_ctilde=True, want_frac=True, **kw)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(st)
+    mat, fwd = forward()
+    e[1].record(st)
+    G, S, _, _, loss = loss_grads(fwd, T, vm0)
+    b = hom.hom_solve_backward(mat, fwd, c0, dL_dC=G, dL_dsigma=S, want_ctilde=True, want_frac=True, **kw)
+    e[2].record(st)
+    torch.cuda.synchronize()
+    return {"n": n, "contrast": 20.0, "loads": 6, "forward_ms": round(e[0].elapsed_time(e[1]), 2),
+            "backward_ms": round(e[1].elapsed_time(e[2]), 2), "loss": loss,
+            "forward_iterations": [int(i) for i in fwd["iterations"][0]],
+            "adjoint_iterations": [int(i) for i in b["adjoint_iterations"][0]],
+            "adjoint_status": [int(i) for i in b["adjoint_status"][0]],
+            "dL_dphase": b["dphase"].tolist(), "tol": kw["tol"],
+            "note": "FP32 forward and adjoint on the specialised 3D passes; loss gradient w.r.t. sigma from torch "
+                    "on the returned fields (user side); tests/test_gpu_backward_vm.py checks the gradient "
+                    "against finite differences of the FP64 path at this size"}
 
 
 def cg_comparison(hom, dev, sizes=(135, 405), tol=1e-4):

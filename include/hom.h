@@ -74,6 +74,11 @@ extern "C" {
 #define HOM_PASSES_AUTO 0    /* specialised FP32 passes where a compiled plan exists, else generic */
 #define HOM_PASSES_GENERIC 1 /* generic passes for every cell (any supported grid and precision)   */
 
+/* Discrete Green operator (section 2, eq. 2, and the modified operators its introduction cites). */
+#define HOM_GREEN_CONTINUOUS 0 /* eq. (2) at xi = 2 pi a on J (the paper's operator)                 */
+#define HOM_GREEN_ROTATED 1    /* rotated finite-difference scheme: eq. (2)'s formula, and the       */
+                               /* equilibrium check, at q_j = 2n sin(pi a_j/n) prod_{m!=j} cos(pi a_m/n) */
+
 #define HOM_CRIT_E 0  /* e   = sqrt(sum_k |xi_k . sigma_hat(k)|^2) / ||sigma_hat(0)||          */
 #define HOM_CRIT_EN 1 /* e_n = sqrt(sum_{k!=0} |(xi_k/|xi_k|) . sigma_hat(k)|^2) / ||sigma_hat(0)|| */
 
@@ -156,6 +161,10 @@ typedef struct hom_solve_opts {
   int32_t passes;         /* HOM_PASSES_AUTO or HOM_PASSES_GENERIC                       */
   int32_t max_radix;      /* largest register radix of the generic FP32 FFT stages: 15, 27 or
                              45 (0 = 27; FP64 always uses 15)                             */
+  int32_t green;          /* HOM_GREEN_CONTINUOUS or HOM_GREEN_ROTATED (generic passes;   */
+                          /* not with hom_solve_cg)                                       */
+  int32_t tune;           /* 1: autotune the FFT plan of FP32 solves with passes = AUTO and */
+                          /* max_radix = 0 (see hom_autotune_report); 0: fixed defaults   */
 } hom_solve_opts;
 
 /* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every
@@ -332,6 +341,15 @@ int hom_fourier_extrapolate(const hom_cell* cells, int32_t ncells, const hom_mat
  * Returns HOM_ERR_INVALID_ARG if some E is singular.  Synchronous. */
 int hom_effective_stiffness(int32_t ncells, int32_t dim, const double* E, const double* mean_sigma,
                             double* C_out);
+
+/* The autotuner's record.  The first FP32 hom_solve of a batch shape (device, dimension, load count,
+ * Green operator, multiset of grid sizes) with opts->tune = 1 (passes = AUTO, max_radix = 0) times
+ * four candidate plans on that batch -- the specialised passes and the generic passes with register
+ * radices up to 15, 27 and 45 -- over 4 fixed iterations each (after one untimed call), and every
+ * later solve of the shape runs the fastest.  Writes one line per shape, "shape: timings -> choice",
+ * into buf (at most len bytes, NUL-terminated) and returns the full length.  The choice depends on
+ * measured times, so two processes may pick different plans (results then differ by FP32 rounding). */
+int32_t hom_autotune_report(char* buf, int32_t len);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char* hom_last_error(void);

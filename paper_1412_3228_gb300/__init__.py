@@ -32,13 +32,15 @@ HOM_ERR_CAPACITY = 8
 HOM_FP32, HOM_FP64 = 0, 1
 HOM_CRIT_E, HOM_CRIT_EN = 0, 1
 HOM_PASSES_AUTO, HOM_PASSES_GENERIC = 0, 1
+HOM_GREEN_CONTINUOUS, HOM_GREEN_ROTATED = 0, 1
 HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", -1: "active"}
 HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
 KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "init"]
 
-EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_solve_backward", "hom_effective_stiffness",
-            "hom_last_error", "hom_release", "hom_version"]
+EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_solve_cg", "hom_solve_backward",
+            "hom_effective_stiffness", "hom_fourier_extrapolate", "hom_autotune_report", "hom_last_error", "hom_release",
+            "hom_version"]
 
 
 class HomError(RuntimeError):
@@ -75,7 +77,7 @@ class hom_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("criterion", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("max_radix", ctypes.c_int32)]
+                ("max_radix", ctypes.c_int32), ("green", ctypes.c_int32), ("tune", ctypes.c_int32)]
 
 
 class hom_kernel_stats(ctypes.Structure):
@@ -118,6 +120,8 @@ def lib() -> ctypes.CDLL:
         h.hom_fourier_extrapolate.argtypes = [ctypes.POINTER(hom_cell), ctypes.c_int32, ctypes.POINTER(hom_material),
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p]
+        h.hom_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_int32]
+        h.hom_autotune_report.restype = ctypes.c_int32
         h.hom_last_error.restype = ctypes.c_char_p
         h.hom_version.restype = ctypes.c_int32
         _lib_handle = h
@@ -264,7 +268,8 @@ def hom_solve_noalloc(material: Material, E, c0, **kw) -> dict:
 def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: int = HOM_FP64,
               criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
-              passes: int = HOM_PASSES_AUTO, max_radix: int = 0, stats: bool = False, stream=None,
+              passes: int = HOM_PASSES_AUTO, max_radix: int = 0, green: int = HOM_GREEN_CONTINUOUS,
+              tune: bool = False, stats: bool = False, stream=None,
               allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
     """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
 
@@ -305,7 +310,8 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
                      err_n=err_n.ctypes.data, stats=ctypes.pointer(st) if st is not None else None)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=int(check_every), diverge_window=int(diverge_window),
-                          use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix))
+                          use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix),
+                          green=int(green), tune=int(bool(tune)))
     with torch.cuda.device(device):
         if _entry == "hom_solve_cg":
             code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
@@ -337,7 +343,7 @@ def hom_solve_cg(material: Material, E, **kw) -> dict:
 def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_dsigma: Optional[torch.Tensor] = None,
                        want_ctilde: bool = True, want_frac: bool = True, precision: int = HOM_FP64,
                        criterion: int = HOM_CRIT_E, tol: float = 1e-10, max_iter: int = 2000,
-                       passes: int = HOM_PASSES_AUTO, stream=None) -> dict:
+                       passes: int = HOM_PASSES_AUTO, green: int = HOM_GREEN_CONTINUOUS, stream=None) -> dict:
     """Adjoint derivative of L(C_eff, sigma) (see include/hom.h).  `forward` is the dict returned by
     hom_solve (with device fields); dL_dC is [ncells, nc, nc] (host), dL_dsigma a device tensor laid
     out like forward['sigma'].  Returns dctilde [sum voxels, ns] (device), dphase [nphase, 2],
@@ -369,7 +375,8 @@ def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_
     info = hom_result(iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
                       err_n=err_n.ctypes.data)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
-                          check_every=0, diverge_window=0, use_graph=0, passes=int(passes), max_radix=0)
+                          check_every=0, diverge_window=0, use_graph=0, passes=int(passes), max_radix=0,
+                          green=int(green), tune=0)
     with torch.cuda.device(device):
         code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                         c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),
@@ -417,6 +424,14 @@ class HomSolve(torch.autograd.Function):
                                criterion=st.get("criterion", HOM_CRIT_E), tol=st.get("tol", 1e-10),
                                max_iter=st.get("max_iter", 2000))
         return torch.from_numpy(g["dphase"]), None, None, None
+
+
+def hom_autotune_report() -> str:
+    """The autotuner's record: one line per batch shape, with the candidate timings and the choice."""
+    n = lib().hom_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().hom_autotune_report(buf, n + 1)
+    return buf.value.decode()
 
 
 def hom_effective_stiffness(E, mean_sigma, dim: int) -> np.ndarray:

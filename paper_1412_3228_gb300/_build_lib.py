@@ -58,6 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         common += ["-DHOM_FAST3D_THREADS=%d" % int(os.environ["HOM_FAST3D_THREADS"])]
     if os.environ.get("HOM_FAST_THREADS"):  # threads per CTA of the specialised 2D passes (tuning)
         common += ["-DHOM_FAST_THREADS=%d" % int(os.environ["HOM_FAST_THREADS"])]
+    for d in os.environ.get("HOM_EXTRA_DEFINES", "").split():  # other build-time tunables (-DNAME=VALUE)
+        if d.startswith("-D"):
+            common.append(d)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

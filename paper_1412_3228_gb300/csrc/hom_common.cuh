@@ -263,6 +263,8 @@ struct Plan {
   const double2* tw64;
   const float* xi32;      // 2 pi a(k): signed DFT frequency of bin k times 2 pi
   const double* xi64;
+  const float2* rot32;    // (2n sin(pi a/n), cos(pi a/n)): the rotated scheme's wave-vector factors
+  const double2* rot64;
 };
 
 // Fills the dividers of a plan whose n, nstage, radix and span are set.

@@ -42,6 +42,15 @@ namespace {
 #ifndef HOM_ROW_TW2
 #define HOM_ROW_TW2 1    // row pass with a scalar twiddle table (three CTAs per SM)
 #endif
+#ifndef HOM_ROW_LANDING
+#define HOM_ROW_LANDING 1  // row pass: rows land by cp.async in their line slots (0: register loads)
+#endif
+#ifndef HOM_ROW_PREFETCH
+#define HOM_ROW_PREFETCH 0  // row pass L2 prefetch: 1 = the next load, 2 = the next task (bit mask)
+#endif
+#ifndef HOM_GREEN_PREFETCH
+#define HOM_GREEN_PREFETCH 0  // Green pass: L2 prefetch of the task that starts next
+#endif
 constexpr int NP = 3;  // lane pairs per position (2D Mandel components)
 constexpr int kFastSizes[] = {45, 75, 135, 225, 405, 1215};  // sizes with specialised 2D passes
 
@@ -126,6 +135,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
   for (int la = 0; la < nal; ++la) {
     const int l = s_al[la];
     const float4* ein = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + l] & 1) : (it & 1)]);
+#if HOM_ROW_LANDING
     // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component.  Item
     // (p, k) = kx pair p, component k: its four row values (one 16-byte lane pair each) land, by
     // asynchronous copies all in flight at once, in the tile slots of the four line positions
@@ -141,7 +151,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
     cp_commit();
     // the next active load's rows of every pair (192 contiguous bytes each) -> L2, so that its
     // copies above hit L2 while this load's transforms run
-    if (la + 1 < nal) {
+    if ((HOM_ROW_PREFETCH & 1) && la + 1 < nal) {
       const float4* nx = static_cast<const float4*>(A.eps[OUT ? (A.iters[t.cell * A.L + s_al[la + 1]] & 1) : (it & 1)]);
       for (int p = threadIdx.x; p < P; p += kT)
         prefetch_l2(nx + tile_index(c, N, s_al[la + 1], p, y0), (unsigned)(nr * NP * sizeof(float4)));
@@ -175,6 +185,50 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
       }
     }
     __syncthreads();
+#else
+    // 1. four half-spectrum rows -> two Hermitian-extended complex lines per component; item
+    // (p, k) reads rows y0..y0+3 of pair p (U items per round: 4 U loads in flight per thread)
+    constexpr int U = 1;
+    for (int f0 = threadIdx.x; f0 < P * NP; f0 += U * kT) {
+      float4 v[U][kFastRows];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
+        const int p = f / NP, k = f - p * NP;
+        const size_t b = tile_index(c, N, l, p, y0) + k;
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) v[u][r] = (f < P * NP && r < nr) ? ein[b + (size_t)r * NP] : z4;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = f0 + u * kT;
+        if (f >= P * NP) continue;
+        const int p = f / NP, k = f - p * NP;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kx = 2 * p + h;
+          if (kx >= H) break;
+          // row r at kx: (re, im) = lane h of v[u][r]
+          const float2 q0 = h ? make_float2(v[u][0].y, v[u][0].w) : make_float2(v[u][0].x, v[u][0].z);
+          const float2 q1 = h ? make_float2(v[u][1].y, v[u][1].w) : make_float2(v[u][1].x, v[u][1].z);
+          const float2 q2 = h ? make_float2(v[u][2].y, v[u][2].w) : make_float2(v[u][2].x, v[u][2].z);
+          const float2 q3 = h ? make_float2(v[u][3].y, v[u][3].w) : make_float2(v[u][3].x, v[u][3].z);
+          // A + iB at kx and conj(A) + i conj(B) at n - kx, for (A, B) = (row 0, row 1) and (row 2, row 3)
+          s[kx * NP + k] = make_float4(q0.x - q1.y, q2.x - q3.y, q0.y + q1.x, q2.y + q3.x);
+          if (kx > 0) {
+            s[(N - kx) * NP + k] = make_float4(q0.x + q1.y, q2.x + q3.y, q1.x - q0.y, q3.x - q2.y);
+          } else {
+            s_dc[la][0][0][k] = q0.x;
+            s_dc[la][0][1][k] = q1.x;
+            s_dc[la][0][2][k] = q2.x;
+            s_dc[la][0][3][k] = q3.x;
+          }
+        }
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+#endif
     fft_dif_p<NP, N, false>(s, tws);  // inverse: eps at digit-reversed positions
 
     // 2. constitutive update: lanes (x, y, z, w) of a float4 are rows (0, 2, 1, 3).  A one-byte
@@ -383,7 +437,7 @@ __global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A
   __shared__ RowShared sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const int task = blockIdx.x;
-  if (task + ahead < ntasks) prefetch_row_task<OUT>(A, task + ahead);
+  if ((HOM_ROW_PREFETCH & 2) && task + ahead < ntasks) prefetch_row_task<OUT>(A, task + ahead);
   const TaskR t = A.tR[task];
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];
@@ -587,7 +641,7 @@ __global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveAr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const int task = blockIdx.x;
-  if (task + ahead < ntasks) prefetch_green_task(A, task + ahead);
+  if (HOM_GREEN_PREFETCH && task + ahead < ntasks) prefetch_green_task(A, task + ahead);
   const TaskL t = A.tC[task];
   const CellDev c = A.cells[t.cell];
   const FastPlanDev fp = A.fplans[c.fplan];

@@ -42,12 +42,17 @@ inline void set_plan_pointers(Plan& p, unsigned char* base) {
   p.xi32 = reinterpret_cast<const float*>(base);
   base += up(n * 4);
   p.xi64 = reinterpret_cast<const double*>(base);
+  base += up(n * 8);
+  p.rot32 = reinterpret_cast<const float2*>(base);
+  base += up(n * 8);
+  p.rot64 = reinterpret_cast<const double2*>(base);
 }
 
 // Device scratch owned by the library (grown on demand, freed by hom_release).
 int get_workspace(size_t bytes, void** ptr);
 void release_backward_buffers();
 void release_graphs();  // cached whole-solve graphs
+std::string tune_report();  // the autotuner's choices and timings, one line per batch shape
 
 // ------------------------------------------------------------------ validation
 bool grid_supported(int n);

@@ -19,6 +19,8 @@ struct HostPlan {
   std::vector<uint16_t> perm;   // position of index k in the digit-reversed layout
   std::vector<double> tw;       // interleaved (re, im) of exp(-2 pi i t / n)
   std::vector<double> xi;       // 2 pi a(k), a(k) the signed frequency of DFT bin k
+  std::vector<double> rot;      // interleaved (2n sin(pi a/n), cos(pi a/n)): factors of the rotated
+                                // scheme's wave vector q_j = 2n sin(pi a_j/n) prod_{m!=j} cos(pi a_m/n)
 };
 
 // Factor n into the register radices {2, 3, 4, 5, 7, 8, 9, 11, 13, 15, 16, 21, 25, 27, 35, 45, 49}
@@ -82,6 +84,12 @@ inline bool build_host_plan_radices(int n, const std::vector<int>& radix, HostPl
   p.xi.assign(n, 0.0);
   // signed frequency of bin k: k up to n / 2 (the Nyquist bin of an even grid counts as +n/2), else k - n
   for (int k = 0; k < n; ++k) p.xi[k] = 6.28318530717958647692528676656 * (double)(k <= n / 2 ? k : k - n);
+  p.rot.assign(2 * (size_t)n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double h = 3.14159265358979323846264338328 * (double)(k <= n / 2 ? k : k - n) / (double)n;
+    p.rot[2 * k] = 2.0 * n * std::sin(h);
+    p.rot[2 * k + 1] = std::cos(h);
+  }
   p.tw.assign(2 * (size_t)n, 0.0);
   const double two_pi = 6.28318530717958647692528676656;
   for (int t = 0; t < n; ++t) {
@@ -100,10 +108,12 @@ inline bool build_host_plan(int n, HostPlan& p, int max_radix = 45) {
 }
 
 // Device layout of a plan's tables (each block 256-byte aligned): permutation (uint16),
-// FP32 twiddles, FP64 twiddles, FP32 wave numbers, FP64 wave numbers.
+// FP32 twiddles, FP64 twiddles, FP32 wave numbers, FP64 wave numbers, FP32 and FP64 factors of the
+// rotated scheme's wave vector.
 inline size_t plan_table_bytes(int n) {
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up((size_t)n * 2) + up((size_t)n * 8) + up((size_t)n * 16) + up((size_t)n * 4) + up((size_t)n * 8);
+  return up((size_t)n * 2) + up((size_t)n * 8) + up((size_t)n * 16) + up((size_t)n * 4) + up((size_t)n * 8) +
+         up((size_t)n * 8) + up((size_t)n * 16);
 }
 
 inline void fill_plan_tables(const HostPlan& hp, unsigned char* dst) {
@@ -121,6 +131,11 @@ inline void fill_plan_tables(const HostPlan& hp, unsigned char* dst) {
   for (size_t k = 0; k < n; ++k) x32[k] = (float)hp.xi[k];
   q += up(n * 4);
   std::memcpy(q, hp.xi.data(), n * 8);
+  q += up(n * 8);
+  float* r32 = reinterpret_cast<float*>(q);
+  for (size_t k = 0; k < 2 * n; ++k) r32[k] = (float)hp.rot[k];
+  q += up(n * 8);
+  std::memcpy(q, hp.rot.data(), n * 16);
 }
 
 }  // namespace hom

@@ -46,6 +46,7 @@ struct SolveArgs {
   unsigned int* done;
   unsigned long long* bytes;  // [HOM_NKERNEL]
   int L, criterion, max_iter, diverge_window;
+  int green;  // HOM_GREEN_CONTINUOUS or HOM_GREEN_ROTATED
   double tol;
   void* out_eps;
   void* out_sig;

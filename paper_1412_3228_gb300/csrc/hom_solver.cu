@@ -18,6 +18,7 @@
 // (cell, load), applies the stopping rule and deactivates finished load cases; later passes
 // skip inactive ones.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <algorithm>
 #include <mutex>
@@ -63,6 +64,9 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 template <typename T> __device__ __forceinline__ const T* xi_table(const Plan& p);
 template <> __device__ __forceinline__ const float* xi_table<float>(const Plan& p) { return p.xi32; }
 template <> __device__ __forceinline__ const double* xi_table<double>(const Plan& p) { return p.xi64; }
+template <typename V> __device__ __forceinline__ const V* rot_table(const Plan& p);
+template <> __device__ __forceinline__ const float2* rot_table<float2>(const Plan& p) { return p.rot32; }
+template <> __device__ __forceinline__ const double2* rot_table<double2>(const Plan& p) { return p.rot64; }
 
 // ------------------------------------------------------------------ row pass
 // OUT = false: one iteration's row pass (eps -> tau).  OUT = true: final fields of the returned
@@ -345,11 +349,20 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const T ratio = cc.ratio;
   const T inv_nv = cc.inv_nv;
   const T inv_mu0 = cc.inv_mu0;
-  // 2 pi a(k) of the transformed axis, one entry per bin (after the lines in shared memory)
+  // 2 pi a(k) of the transformed axis, one entry per bin (after the lines in shared memory); the
+  // rotated scheme takes the factors (2n sin(pi a/n), cos(pi a/n)) of its wave vector instead
+  const bool rotated = A.green == HOM_GREEN_ROTATED;
   T* xi_tab = reinterpret_cast<T*>(s + (size_t)nl * n);
+  V* rot_tab = reinterpret_cast<V*>(s + (size_t)nl * n);
   const T* xi_src = xi_table<T>(sp);
-  for (int k = threadIdx.x; k < n; k += kThreads) xi_tab[k] = xi_src[k];
+  const V* rot_src = rot_table<V>(sp);
+  if (rotated) {
+    for (int k = threadIdx.x; k < n; k += kThreads) rot_tab[k] = rot_src[k];
+  } else {
+    for (int k = threadIdx.x; k < n; k += kThreads) xi_tab[k] = xi_src[k];
+  }
   const T xi_fixed = DIM == 3 ? xi_src[t.fixed] : T(0);
+  const V rot_fixed = DIM == 3 ? rot_src[t.fixed] : mk(T(0), T(1));
   __syncthreads();
   const T rs2 = T(0.707106781186547524400844362105);
   const double* Eld = A.E + ((size_t)t.cell * A.L + t.load) * NC;
@@ -384,12 +397,24 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     for (int k = 0; k < NC; ++k) tv[k] = s + (size_t)(kxl * NC + k) * n + pos;
     V* gp = gbuf + gbase + gfix + (size_t)kk * grow_stride + (size_t)kxl * DIM;
     T xi[DIM];
-    xi[0] = xi_tab[kx];  // kx <= (n-1)/2: the table entry is 2 pi kx
-    if (DIM == 2) {
-      xi[1] = xi_tab[kk];
+    if (rotated) {  // q_j = 2n sin(pi a_j / n) prod_{m != j} cos(pi a_m / n)
+      const V fx = rot_tab[kx], fl = rot_tab[kk];
+      if (DIM == 2) {
+        xi[0] = fx.x * fl.y;
+        xi[1] = fx.y * fl.x;
+      } else {
+        xi[0] = fx.x * rot_fixed.y * fl.y;
+        xi[1] = fx.y * rot_fixed.x * fl.y;
+        xi[DIM - 1] = fx.y * rot_fixed.y * fl.x;
+      }
     } else {
-      xi[1] = xi_fixed;
-      xi[DIM - 1] = xi_tab[kk];
+      xi[0] = xi_tab[kx];  // kx <= (n-1)/2: the table entry is 2 pi kx
+      if (DIM == 2) {
+        xi[1] = xi_tab[kk];
+      } else {
+        xi[1] = xi_fixed;
+        xi[DIM - 1] = xi_tab[kk];
+      }
     }
     const bool k0 = kx == 0 && kk == 0 && (DIM == 2 || t.fixed == 0);
     // even grids: a wave vector with a Nyquist component (n/2) has no conjugate partner in the
@@ -940,6 +965,34 @@ void keep_graph(int dev, const std::string& key, cudaGraphExec_t exec) {
   g_graphs.push_back(GraphEntry{dev, key, exec});
 }
 
+// Autotuner choices per batch shape (device, dimension, loads, Green operator, grid sizes), with the
+// timings that decided them.
+struct TuneChoice {
+  int passes, radix;
+};
+struct TuneEntry {
+  std::string key;
+  TuneChoice choice;
+  std::string report;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tuned;
+
+bool find_tuned(const std::string& key, TuneChoice* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& e : g_tuned)
+    if (e.key == key) {
+      *out = e.choice;
+      return true;
+    }
+  return false;
+}
+
+void keep_tuned(const std::string& key, TuneChoice c, const std::string& report) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.push_back(TuneEntry{key, c, report});
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a{};
@@ -979,7 +1032,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     c0 = c0_cg.data();
   }
   // opts->passes == HOM_PASSES_GENERIC keeps every solve on the generic passes
-  lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC;
+  lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC &&
+             opts->green == HOM_GREEN_CONTINUOUS;
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1142,6 +1196,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.L = L;
   A.criterion = opts->criterion;
   A.max_iter = opts->max_iter;
+  A.green = opts->green;
   A.diverge_window = opts->diverge_window;
   A.tol = opts->tol;
   A.out_eps = out->eps ? (eps_dev ? out->eps : (void*)(ws + o_stage_e)) : nullptr;
@@ -1373,6 +1428,18 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
 }  // namespace
 
+std::string tune_report() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string r;
+  for (const auto& e : g_tuned) {
+    char c[96];
+    std::snprintf(c, sizeof(c), " -> %s r%d", e.choice.passes == HOM_PASSES_AUTO ? "specialised" : "generic",
+                  e.choice.radix);
+    r += e.key + ": " + e.report + c + "\n";
+  }
+  return r;
+}
+
 void release_graphs() {
   std::lock_guard<std::mutex> lk(g_graph_mu);
   for (auto& e : g_graphs) cudaGraphExecDestroy(e.exec);
@@ -1401,6 +1468,10 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown passes option %d", opts->passes);
   if (opts->max_radix != 0 && opts->max_radix != 15 && opts->max_radix != 27 && opts->max_radix != 45)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: max_radix must be 0, 15, 27 or 45");
+  if (opts->green != HOM_GREEN_CONTINUOUS && opts->green != HOM_GREEN_ROTATED)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown Green operator %d", opts->green);
+  if (cg && opts->green != HOM_GREEN_CONTINUOUS)
+    return set_error(HOM_ERR_NOT_IMPL, "hom_solve_cg: only the continuous Green operator");
   if (!mat->label || !mat->phase_c32 || !mat->phase_c64)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material not built");
   const int dim = cells[0].dim;
@@ -1417,19 +1488,82 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Largest register radix of the generic FFT stages: FP32 kernels are compiled for 15, 27 and 45
   // (opts->max_radix; 0 = 27), FP64 ones for 15.
-  const int r32 = opts->max_radix > 0 ? opts->max_radix : 27;
-  if (opts->precision == HOM_FP32) {
-    if (r32 >= 45)
-      return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
-                      : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
-    if (r32 <= 15)
-      return dim == 2 ? run_solve<float, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
-                      : run_solve<float, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
-    return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
-                    : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
+  auto dispatch = [&](const hom_solve_opts* op, hom_result* res) -> int {
+    const int r32 = op->max_radix > 0 ? op->max_radix : 27;
+    if (op->precision == HOM_FP32) {
+      if (r32 >= 45)
+        return dim == 2 ? run_solve<float, 2, 45>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg)
+                        : run_solve<float, 3, 45>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg);
+      if (r32 <= 15)
+        return dim == 2 ? run_solve<float, 2, 15>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg)
+                        : run_solve<float, 3, 15>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg);
+      return dim == 2 ? run_solve<float, 2, 27>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg)
+                      : run_solve<float, 3, 27>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg);
+    }
+    return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg)
+                    : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, op, res, st, ext, adj, cg);
+  };
+  hom_solve_opts o = *opts;
+  if (opts->tune && opts->precision == HOM_FP32 && !ext && !adj && !cg && opts->passes == HOM_PASSES_AUTO &&
+      opts->max_radix == 0) {
+    // Autotuner: the first solve of a batch shape times every candidate plan -- the specialised
+    // passes (where every size has one) and the generic passes with register radices up to 15, 27
+    // and 45 -- over a few fixed iterations of this very batch, and keeps the fastest for the shape.
+    int dev = 0;
+    HOM_CUDA_TRY(cudaGetDevice(&dev));
+    std::vector<int> ns;
+    for (int c = 0; c < ncells; ++c) ns.push_back(cells[c].n);
+    std::sort(ns.begin(), ns.end());
+    std::string key = "dev" + std::to_string(dev) + " dim" + std::to_string(dim) + " L" + std::to_string(L) +
+                      " green" + std::to_string(opts->green) + " n";
+    for (size_t i = 0; i < ns.size(); ++i) {
+      size_t j = i;
+      while (j + 1 < ns.size() && ns[j + 1] == ns[i]) ++j;
+      key += " " + std::to_string(ns[i]) + "x" + std::to_string(j - i + 1);
+      i = j;
+    }
+    TuneChoice choice{};
+    if (!find_tuned(key, &choice)) {
+      struct Cand { int passes, radix; };
+      const Cand cands[] = {{HOM_PASSES_AUTO, 27}, {HOM_PASSES_GENERIC, 15}, {HOM_PASSES_GENERIC, 27},
+                            {HOM_PASSES_GENERIC, 45}};
+      std::vector<double> ms_sigma((size_t)ncells * L * nc_of(dim));
+      std::string report;
+      double best = 1e300;
+      for (const Cand& cd : cands) {
+        hom_solve_opts t = *opts;
+        t.passes = cd.passes;
+        t.max_radix = cd.radix;
+        t.tol = -1.0;  // a fixed number of iterations, no early stop
+        t.max_iter = 4;
+        t.use_graph = 0;
+        t.tune = 0;
+        double ms = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {  // the first call builds plans and workspace
+          hom_kernel_stats ks{};
+          hom_result tr{};
+          tr.mean_sigma = ms_sigma.data();
+          tr.stats = &ks;
+          const int rc = dispatch(&t, &tr);
+          if (rc != HOM_OK && rc != HOM_ERR_NOT_CONVERGED && rc != HOM_ERR_DIVERGED) return rc;
+          ms = 0.0;
+          for (int k = HOM_K_ROW; k <= HOM_K_CONTROL; ++k) ms += ks.ms[k];
+        }
+        char line[160];
+        std::snprintf(line, sizeof(line), "%s%s r%d %.3f ms", report.empty() ? "" : " | ",
+                      cd.passes == HOM_PASSES_AUTO ? "specialised" : "generic", cd.radix, ms / 5.0);
+        report += line;
+        if (ms < best) {
+          best = ms;
+          choice = TuneChoice{cd.passes, cd.radix};
+        }
+      }
+      keep_tuned(key, choice, report);
+    }
+    o.passes = choice.passes;
+    o.max_radix = choice.radix;
   }
-  return dim == 2 ? run_solve<double, 2, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg)
-                  : run_solve<double, 3, 15>(cells, ncells, mat, E, L, c0, opts, out, st, ext, adj, cg);
+  return dispatch(&o, out);
 }
 
 }  // namespace hom
@@ -1437,6 +1571,16 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
 extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                          const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
   return solve_entry(cells, ncells, mat, E, L, c0, opts, out, stream, nullptr);
+}
+
+extern "C" int32_t hom_autotune_report(char* buf, int32_t len) {
+  const std::string r = hom::tune_report();
+  if (buf && len > 0) {
+    const size_t k = std::min<size_t>(r.size(), (size_t)len - 1);
+    std::memcpy(buf, r.data(), k);
+    buf[k] = 0;
+  }
+  return (int32_t)r.size();
 }
 
 extern "C" int hom_solve_cg(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E,

@@ -116,20 +116,21 @@ def test_fast_adjoint_matches_generic(case):
     phases = H.two_phases(10.0)
     c0 = H.mean_lame(phases)
     mat = hom.hom_filter_build([cell], phases)
-    fwd = hom.hom_solve(mat, np.eye(nc), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-7,
+    fwd = hom.hom_solve(mat, np.eye(nc), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-6,
                         max_iter=3000)
+    assert (fwd["status"] == 0).all()
     rng = np.random.default_rng(17)
     G = rng.standard_normal((1, nc, nc))
     S = torch.tensor(rng.standard_normal(fwd["sigma"].numel()) / cell.n ** cell.dim, dtype=torch.float32, device="cuda")
     out = {}
     for passes in (hom.HOM_PASSES_AUTO, hom.HOM_PASSES_GENERIC):
         out[passes] = hom.hom_solve_backward(mat, fwd, c0, dL_dC=G, dL_dsigma=S, precision=hom.HOM_FP32,
-                                             criterion=hom.HOM_CRIT_EN, tol=1e-7, max_iter=3000, passes=passes)
+                                             criterion=hom.HOM_CRIT_EN, tol=1e-6, max_iter=3000, passes=passes)
         assert (out[passes]["adjoint_status"] == 0).all()
     a, g = out[hom.HOM_PASSES_AUTO], out[hom.HOM_PASSES_GENERIC]
-    np.testing.assert_allclose(a["dphase"], g["dphase"], rtol=0, atol=1e-5 * np.abs(g["dphase"]).max())
+    np.testing.assert_allclose(a["dphase"], g["dphase"], rtol=0, atol=2e-5 * np.abs(g["dphase"]).max())
     da, dg = a["dctilde"].double(), g["dctilde"].double()
-    assert float((da - dg).pow(2).mean().sqrt() / dg.pow(2).mean().sqrt()) < 1e-5
+    assert float((da - dg).pow(2).mean().sqrt() / dg.pow(2).mean().sqrt()) < 2e-5
 
 
 def test_backward_135_fp32_matches_fp64_fd():
@@ -152,12 +153,13 @@ def test_backward_135_fp32_matches_fp64_fd():
     T = _target(C0, 3001)
     vm0 = _vm2_mean(s0)
     mat = hom.hom_filter_build([cell], phases)
-    fwd = hom.hom_solve(mat, np.eye(6), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-7, max_iter=5000)
+    # FP32 at contrast 20: e_n bottoms out near contrast x 6e-8 (about 1.2e-6), so stop at 4e-6
+    fwd = hom.hom_solve(mat, np.eye(6), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=4e-6, max_iter=5000)
     assert (fwd["status"] == 0).all()
     C = hom.hom_effective_stiffness(np.eye(6), fwd["mean_sigma"], 3)[0]
     G, S = _loss_grads(C, fwd["sigma"].view(6, 6, -1).cpu().numpy().astype(np.float64), T, vm0, n ** 3, torch.float32)
     b = hom.hom_solve_backward(mat, fwd, c0, dL_dC=G, dL_dsigma=S, precision=hom.HOM_FP32,
-                               criterion=hom.HOM_CRIT_EN, tol=1e-7, max_iter=5000)
+                               criterion=hom.HOM_CRIT_EN, tol=4e-6, max_iter=5000)
     assert (b["adjoint_status"] == 0).all()
     big = np.abs(b["dphase"]).max()
     for p in range(2):
