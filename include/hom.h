@@ -85,6 +85,7 @@ extern "C" {
 #define HOM_STATUS_CONVERGED 0
 #define HOM_STATUS_MAX_ITER 1
 #define HOM_STATUS_DIVERGED 2
+#define HOM_STATUS_STALLED 3   /* no new smallest error for opts->stall_window iterations       */
 
 #define HOM_MIXED_BIT 0x80000000u /* label bit: the voxel's stiffness is in the mixed table   */
 
@@ -165,6 +166,9 @@ typedef struct hom_solve_opts {
                           /* not with hom_solve_cg)                                       */
   int32_t tune;           /* 1: autotune the FFT plan of FP32 solves with passes = AUTO and */
                           /* max_radix = 0 (see hom_autotune_report); 0: fixed defaults   */
+  int32_t stall_window;   /* > 0: stop a load case whose error has not reached a new minimum */
+                          /* for this many iterations (HOM_STATUS_STALLED: FP32 rounding  */
+                          /* floor above tol); 0 = off                                    */
 } hom_solve_opts;
 
 /* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every
@@ -228,8 +232,12 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
  * Per (cell, load) the iteration starts from eps = E and stops at the first iterate whose
  * equilibrium error (opts->criterion) is below opts->tol, after opts->max_iter Green-operator
  * applications, or on divergence; the returned fields and <sigma> are those of that iterate.
- * Returns HOM_OK when every load case converged, HOM_ERR_NOT_CONVERGED / HOM_ERR_DIVERGED
- * otherwise (all outputs still written).  Synchronises the stream before returning. */
+ * Returns HOM_OK when every load case converged, HOM_ERR_NOT_CONVERGED (max_iter or stalled) /
+ * HOM_ERR_DIVERGED otherwise (all outputs still written).  Synchronises the stream before returning.
+ * With opts->use_graph = 1 (and out->stats = NULL) the iterations run as one launch of a CUDA graph
+ * whose conditional WHILE node repeats one iteration until the control kernel finds no active load
+ * case or the iteration budget spent; the instantiated graph is kept for later calls with the same
+ * arguments (same material, workspace, sizes and options; outputs may differ). */
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 

@@ -33,7 +33,7 @@ HOM_FP32, HOM_FP64 = 0, 1
 HOM_CRIT_E, HOM_CRIT_EN = 0, 1
 HOM_PASSES_AUTO, HOM_PASSES_GENERIC = 0, 1
 HOM_GREEN_CONTINUOUS, HOM_GREEN_ROTATED = 0, 1
-HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", -1: "active"}
+HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", 3: "stalled", -1: "active"}
 HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
 KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "init"]
@@ -77,7 +77,8 @@ class hom_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("criterion", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("passes", ctypes.c_int32),
-                ("max_radix", ctypes.c_int32), ("green", ctypes.c_int32), ("tune", ctypes.c_int32)]
+                ("max_radix", ctypes.c_int32), ("green", ctypes.c_int32), ("tune", ctypes.c_int32),
+                ("stall_window", ctypes.c_int32)]
 
 
 class hom_kernel_stats(ctypes.Structure):
@@ -269,7 +270,7 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
               criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
               passes: int = HOM_PASSES_AUTO, max_radix: int = 0, green: int = HOM_GREEN_CONTINUOUS,
-              tune: bool = False, stats: bool = False, stream=None,
+              tune: bool = False, stall_window: int = 0, stats: bool = False, stream=None,
               allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
     """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
 
@@ -311,7 +312,7 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=int(check_every), diverge_window=int(diverge_window),
                           use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix),
-                          green=int(green), tune=int(bool(tune)))
+                          green=int(green), tune=int(bool(tune)), stall_window=int(stall_window))
     with torch.cuda.device(device):
         if _entry == "hom_solve_cg":
             code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
@@ -376,7 +377,7 @@ def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_
                       err_n=err_n.ctypes.data)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=0, diverge_window=0, use_graph=0, passes=int(passes), max_radix=0,
-                          green=int(green), tune=0)
+                          green=int(green), tune=0, stall_window=0)
     with torch.cuda.device(device):
         code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                         c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),

@@ -41,11 +41,13 @@ struct SolveArgs {
   double* mean_sigma;  // [npairs][nc]
   double* last_err;
   int* grow;
+  double* best_err;  // stagnation check: smallest error so far and its iteration
+  int* best_it;
   int* it_dev;
   int* nactive;
   unsigned int* done;
   unsigned long long* bytes;  // [HOM_NKERNEL]
-  int L, criterion, max_iter, diverge_window;
+  int L, criterion, max_iter, diverge_window, stall_window;
   int green;  // HOM_GREEN_CONTINUOUS or HOM_GREEN_ROTATED
   double tol;
   void* out_eps;

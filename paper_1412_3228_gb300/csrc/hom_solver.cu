@@ -614,10 +614,21 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
       if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
       else if (crit < A.tol) st = HOM_STATUS_CONVERGED;
       else if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
-      else if (A.diverge_window > 0) {
-        int gcount = crit > A.last_err[pair] ? A.grow[pair] + 1 : 0;
-        A.grow[pair] = gcount;
-        if (gcount >= A.diverge_window) st = HOM_STATUS_DIVERGED;
+      else {
+        if (A.diverge_window > 0) {
+          int gcount = crit > A.last_err[pair] ? A.grow[pair] + 1 : 0;
+          A.grow[pair] = gcount;
+          if (gcount >= A.diverge_window) st = HOM_STATUS_DIVERGED;
+        }
+        // stagnation: no new smallest error for stall_window iterations (the FP32 floor)
+        if (st < 0 && A.stall_window > 0) {
+          if (crit < A.best_err[pair]) {
+            A.best_err[pair] = crit;
+            A.best_it[pair] = it;
+          } else if (it - A.best_it[pair] >= A.stall_window) {
+            st = HOM_STATUS_STALLED;
+          }
+        }
       }
       A.last_err[pair] = crit;
       if (st >= 0) {
@@ -682,6 +693,8 @@ __global__ void k_init_pairs(SolveArgs A) {
     A.status[p] = -1;
     A.grow[p] = 0;
     A.last_err[p] = INFINITY;
+    A.best_err[p] = INFINITY;
+    A.best_it[p] = 0;
   }
   if (p == 0) {
     *A.it_dev = 0;
@@ -1057,8 +1070,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
                o_tY = take(std::max<size_t>(1, lay.tY.size()) * sizeof(TaskL));
   const size_t o_pairs = take(lay.pairs.size() * sizeof(PairDev));
   const size_t o_E = take((size_t)npairs * nc * sizeof(double));
-  const size_t o_int = take((size_t)npairs * 4 * sizeof(int) + 64);
-  const size_t o_dbl = take((size_t)npairs * (3 + nc) * sizeof(double));
+  const size_t o_int = take((size_t)npairs * 5 * sizeof(int) + 64);
+  const size_t o_dbl = take((size_t)npairs * (4 + nc) * sizeof(double));
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
   int cg_nchunk = 1;
@@ -1184,20 +1197,23 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.iters = ib + npairs;
   A.status = ib + 2 * npairs;
   A.grow = ib + 3 * npairs;
-  A.it_dev = ib + 4 * npairs;
-  A.nactive = ib + 4 * npairs + 1;
-  A.done = reinterpret_cast<unsigned int*>(ib + 4 * npairs + 2);
+  A.best_it = ib + 4 * npairs;
+  A.it_dev = ib + 5 * npairs;
+  A.nactive = ib + 5 * npairs + 1;
+  A.done = reinterpret_cast<unsigned int*>(ib + 5 * npairs + 2);
   double* db = reinterpret_cast<double*>(ws + o_dbl);
   A.err = db;
   A.errn = db + npairs;
   A.last_err = db + 2 * npairs;
-  A.mean_sigma = db + 3 * npairs;
+  A.best_err = db + 3 * npairs;
+  A.mean_sigma = db + 4 * npairs;
   A.bytes = reinterpret_cast<unsigned long long*>(ws + o_bytes);
   A.L = L;
   A.criterion = opts->criterion;
   A.max_iter = opts->max_iter;
   A.green = opts->green;
   A.diverge_window = opts->diverge_window;
+  A.stall_window = opts->stall_window;
   A.tol = opts->tol;
   A.out_eps = out->eps ? (eps_dev ? out->eps : (void*)(ws + o_stage_e)) : nullptr;
   A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
@@ -1419,10 +1435,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   int worst = HOM_OK;
   for (int p = 0; p < npairs; ++p) {
     if (h_st[p] == HOM_STATUS_DIVERGED) worst = HOM_ERR_DIVERGED;
-    else if (h_st[p] == HOM_STATUS_MAX_ITER && worst == HOM_OK) worst = HOM_ERR_NOT_CONVERGED;
+    else if ((h_st[p] == HOM_STATUS_MAX_ITER || h_st[p] == HOM_STATUS_STALLED) && worst == HOM_OK)
+      worst = HOM_ERR_NOT_CONVERGED;
   }
   if (worst == HOM_ERR_DIVERGED) set_error(worst, "a load case diverged");
-  if (worst == HOM_ERR_NOT_CONVERGED) set_error(worst, "a load case reached max_iter");
+  if (worst == HOM_ERR_NOT_CONVERGED) set_error(worst, "a load case reached max_iter or stalled");
   return worst;
 }
 
@@ -1462,7 +1479,7 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown precision");
   if (opts->criterion != HOM_CRIT_E && opts->criterion != HOM_CRIT_EN)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown criterion");
-  if (opts->max_iter < 0 || opts->check_every < 0 || opts->diverge_window < 0)
+  if (opts->max_iter < 0 || opts->check_every < 0 || opts->diverge_window < 0 || opts->stall_window < 0)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: negative option");
   if (opts->passes != HOM_PASSES_AUTO && opts->passes != HOM_PASSES_GENERIC)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown passes option %d", opts->passes);

@@ -371,3 +371,26 @@ def test_kernel_stats_count_the_work():
     per_it = 2 * 45 * H_ * (3 + 2) * 8
     assert st["green"]["bytes"] == per_it * (total_it + 3)
     assert r["voxel_iterations"] == n * n * total_it
+
+
+def test_stagnation_stop():
+    """stall_window: an FP32 load case whose error floor (FP32 rounding, about 9e-8 x contrast) lies
+    above the tolerance stops as HOM_STATUS_STALLED long before max_iter; a case that converges is
+    unaffected, and the stalled pair's returned iterate is as accurate as the floor allows."""
+    base = [(H.centred_disk_cell(45, rule=H.RULE_VOIGT), 100.0), (H.centred_disk_cell(45, rule=H.RULE_REUSS), 2.0)]
+    phases, cells = [], []
+    for cell, contrast in base:
+        cells.append(H.remap_phases(cell, len(phases)))
+        phases.extend(H.two_phases(contrast))
+    c0 = [H.mean_lame(phases[0:2]), H.mean_lame(phases[2:4])]
+    mat = hom.hom_filter_build(cells, phases)
+    r = hom.hom_solve(mat, np.eye(3), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-8,
+                      max_iter=5000, stall_window=40)
+    assert r["code"] == hom.HOM_ERR_NOT_CONVERGED
+    assert (r["status"][0] == 3).all() and (r["iterations"][0] < 5000).all()
+    assert (r["err_n"][0] < 1e-4).all()
+    easy = hom.hom_solve(mat, np.eye(3), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-5,
+                         max_iter=5000, stall_window=40)
+    ref = hom.hom_solve(mat, np.eye(3), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-5, max_iter=5000)
+    assert (easy["status"][1] == 0).all()
+    np.testing.assert_array_equal(easy["iterations"][1], ref["iterations"][1])
