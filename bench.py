@@ -684,11 +684,19 @@ def ensemble_2d(hom, dev, count=256):
 
 
 def cpu_model():
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu, e.g. on Arm hosts)."""
     try:
         for line in open("/proc/cpuinfo"):
-            if line.lower().startswith(("model name", "cpu part", "hardware")):
+            if line.lower().startswith("model name"):
                 return line.split(":", 1)[1].strip()
     except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
         pass
     import platform
     return platform.processor() or platform.machine()
