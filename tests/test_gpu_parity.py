@@ -394,3 +394,23 @@ def test_stagnation_stop():
     ref = hom.hom_solve(mat, np.eye(3), c0, precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-5, max_iter=5000)
     assert (easy["status"][1] == 0).all()
     np.testing.assert_array_equal(easy["iterations"][1], ref["iterations"][1])
+
+
+@pytest.mark.parametrize("contrast", [100.0, 0.01])
+def test_fp32_high_contrast_ceff_matches_oracle(contrast):
+    """FP32 at the ends of the ensemble's contrast range: the solve stops at e_n < 1e-6 or, where the
+    FP32 floor lies above that, at the stagnation stop; either way C_eff is within 1e-5 of the
+    oracle's (converged to e < 1e-10)."""
+    cells = [H.centred_disk_cell(45, rule=H.RULE_VOIGT), H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER)]
+    phases = H.two_phases(contrast)
+    c0 = H.mean_lame(phases)
+    mat = hom.hom_filter_build(cells, phases)
+    r = hom.hom_solve(mat, np.eye(3), [c0, c0], precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=1e-6,
+                      max_iter=5000, stall_window=50)
+    assert np.isin(r["status"], (0, 3)).all()
+    C = hom.hom_effective_stiffness(np.eye(3), r["mean_sigma"], 2)
+    for i, cell in enumerate(cells):
+        fb = O.filter_build(cell, phases)
+        ref = O.solve(fb["ctilde"], 2, 45, c0[0], c0[1], np.eye(3), tol=1e-10, max_iter=20000)
+        Cr = O.effective_stiffness(ref["mean_sigma"], np.eye(3))
+        assert _rel(C[i], Cr) < 1e-5
