@@ -340,6 +340,66 @@ def solve(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.n
                 errors_n=[r["errors_n"] for r in runs])
 
 
+def fixed_point_map(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
+                    eps: np.ndarray) -> np.ndarray:
+    """F(eps) = E - Gamma0 * ((c - c0) : eps), the map the basic scheme iterates (eqs. 1-a, 1-b, 2):
+    eps_hat(k) = -Gamma0(k) : tau_hat(k) for k != 0, eps_hat(0) = E, tau = (c - c0) : eps."""
+    nc = nc_of(dim)
+    grid = (n,) * dim
+    C0 = isotropic_mandel(lam0, mu0, dim)
+    tau = constitutive(ctilde, eps) - constitutive(np.broadcast_to(C0, grid + (nc, nc)), eps)
+    eps_hat = apply_gamma0(_fft(tau, dim), dim, n, lam0, mu0)
+    zero = (slice(None),) + (0,) * dim
+    eps_hat[zero] = n ** dim * np.asarray(E, dtype=np.float64)
+    return np.real(_ifft(eps_hat, dim))
+
+
+def solve_refined_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
+                      tol: float, start: np.ndarray, inner_iters: int, max_outer: int,
+                      criterion: int = CRIT_EN, inner_dtype=np.float64) -> Dict:
+    """Defect correction of the fixed point of section 2 (mixed-precision iterative refinement; the
+    paper works in one precision, this is how a low-precision iteration reaches a high-precision
+    tolerance).  The discrete problem is eps = F(eps) with F the affine map of eqs. 1-a, 1-b, 2
+    (fixed_point_map).  From a start eps_0 (an iterate of the basic scheme), for m = 0, 1, ...:
+        evaluate the equilibrium error of eps_m (FP64); stop if below tol;
+        r_m = F(eps_m) - eps_m                                  (FP64 residual)
+        delta^0 = r_m;  delta^{k+1} = r_m - Gamma0 * ((c - c0) : delta^k), k < inner_iters
+                                                                (the same fixed point for the
+                                                                 correction, zero mean strain)
+        eps_{m+1} = eps_m + delta                               (FP64 update)
+    Since F is affine, the exact correction solves delta = F(eps_m + delta) - eps_m, i.e. that inner
+    fixed point, so each outer step shrinks the error by the inner iteration's contraction (to the
+    inner precision's rounding floor relative to |delta|, not to |eps|).  inner_dtype = float32
+    rounds the inner fields to FP32 after every step (an emulation of FP32 storage).
+    Returns the final iterate, its errors, the outer steps and the inner iterations performed."""
+    nc = nc_of(dim)
+    E = np.asarray(E, dtype=np.float64)
+    zeroE = np.zeros(nc)
+    eps = np.array(start, dtype=np.float64)
+    outer = inner = 0
+    hist = []
+    while True:
+        sigma = constitutive(ctilde, eps)
+        e, e_n = equilibrium_errors(_fft(sigma, dim), dim, n)
+        hist.append((e, e_n))
+        err = e if criterion == CRIT_E else e_n
+        if err < tol or outer >= max_outer:
+            break
+        r = fixed_point_map(ctilde, dim, n, lam0, mu0, E, eps) - eps
+        r_low = r.astype(inner_dtype).astype(np.float64)
+        delta = r_low
+        for _ in range(inner_iters):
+            delta = (r_low + (fixed_point_map(ctilde, dim, n, lam0, mu0, zeroE, delta))).astype(inner_dtype)
+            delta = delta.astype(np.float64)
+            inner += 1
+        eps = eps + delta
+        outer += 1
+    mean_sigma = np.array([math.fsum(sigma[I].ravel()) for I in range(nc)]) / n ** dim
+    return dict(eps=eps, sigma=sigma, mean_sigma=mean_sigma, outer=outer, inner=inner,
+                status="converged" if hist[-1][1 if criterion == CRIT_EN else 0] < tol else "max_outer",
+                errors=np.array([h[0] for h in hist]), errors_n=np.array([h[1] for h in hist]))
+
+
 def effective_stiffness(mean_sigma: np.ndarray, E: np.ndarray) -> np.ndarray:
     """C_eff from the mean stresses of linearly independent load cases:
     <sigma^(l)> = C_eff E^(l) for every l, i.e. C_eff = S^T (E^T)^-1 with rows of S, E per load."""
