@@ -169,6 +169,15 @@ typedef struct hom_solve_opts {
   int32_t stall_window;   /* > 0: stop a load case whose error has not reached a new minimum */
                           /* for this many iterations (HOM_STATUS_STALLED: FP32 rounding  */
                           /* floor above tol); 0 = off                                    */
+  int32_t refine;         /* FP32 only: > 0 = up to this many defect corrections of the load */
+                          /* cases that stall (or reach max_iter): an FP64 iteration gives  */
+                          /* their error and the residual r = F(eps) - eps, and FP32       */
+                          /* iterations of the correction's fixed point (source r, zero    */
+                          /* mean strain) update eps in FP64.  Generic passes; the stall   */
+                          /* window defaults to 30.  0 = off                               */
+  int32_t refine_inner;   /* FP32 iterations per correction (0: from the FP32 iteration's */
+                          /* observed contraction, enough for one correction to bring the */
+                          /* error to tol / 5)                                            */
 } hom_solve_opts;
 
 /* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every

@@ -78,7 +78,7 @@ class hom_solve_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("max_radix", ctypes.c_int32), ("green", ctypes.c_int32), ("tune", ctypes.c_int32),
-                ("stall_window", ctypes.c_int32)]
+                ("stall_window", ctypes.c_int32), ("refine", ctypes.c_int32), ("refine_inner", ctypes.c_int32)]
 
 
 class hom_kernel_stats(ctypes.Structure):
@@ -270,7 +270,8 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
               criterion: int = HOM_CRIT_E, tol: float = 1e-8, max_iter: int = 1000, fields: bool = True,
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
               passes: int = HOM_PASSES_AUTO, max_radix: int = 0, green: int = HOM_GREEN_CONTINUOUS,
-              tune: bool = False, stall_window: int = 0, stats: bool = False, stream=None,
+              tune: bool = False, stall_window: int = 0, refine: int = 0, refine_inner: int = 0,
+              stats: bool = False, stream=None,
               allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
     """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
 
@@ -312,7 +313,8 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=int(check_every), diverge_window=int(diverge_window),
                           use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix),
-                          green=int(green), tune=int(bool(tune)), stall_window=int(stall_window))
+                          green=int(green), tune=int(bool(tune)), stall_window=int(stall_window),
+                          refine=int(refine), refine_inner=int(refine_inner))
     with torch.cuda.device(device):
         if _entry == "hom_solve_cg":
             code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
@@ -377,7 +379,7 @@ def hom_solve_backward(material: Material, forward: dict, c0, *, dL_dC=None, dL_
                       err_n=err_n.ctypes.data)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=0, diverge_window=0, use_graph=0, passes=int(passes), max_radix=0,
-                          green=int(green), tune=0, stall_window=0)
+                          green=int(green), tune=0, stall_window=0, refine=0, refine_inner=0)
     with torch.cuda.device(device):
         code = lib().hom_solve_backward(material.marshalled.cells, ncells, ctypes.byref(material.struct),
                                         c0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), L, ctypes.byref(opts),

@@ -49,10 +49,13 @@ struct SolveArgs {
   unsigned long long* bytes;  // [HOM_NKERNEL]
   int L, criterion, max_iter, diverge_window, stall_window;
   int green;  // HOM_GREEN_CONTINUOUS or HOM_GREEN_ROTATED
+  int inner;  // defect-correction inner solve: the control kernel only counts iterations
+  const int* kinner;  // inner solve: per-pair iteration count (the pair stops at kinner[p])
   double tol;
   void* out_eps;
   void* out_sig;
   const void* src;  // adjoint source S (nullptr for the forward solve)
+  const void* src_mixed;  // defect correction: a strain added to every new iterate (mixed domain, layout of eps)
   double* res0;     // adjoint: residual sums (e, e_n) of the first iterate per pair
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
   const uint8_t* label8;      // specialised row pass: local phase index (255: mixed), x in transform order

@@ -500,9 +500,12 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     }
   }
   fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+  // defect correction (2D): the new iterate takes the fixed source strain (3D: in the inverse y pass)
+  const V* srcm = DIM == 2 ? static_cast<const V*>(A.src_mixed) : nullptr;
   for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
-    out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + j];
+    const size_t ad = base + (size_t)j * rowstride + w;
+    out[ad] = srcm ? s[(size_t)w * n + j] + srcm[ad] : s[(size_t)w * n + j];
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_GREEN,
@@ -538,10 +541,12 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
   __syncthreads();
   if (FWD) fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
   else fft_dit<false, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
+  const V* srcm = FWD ? nullptr : static_cast<const V*>(A.src_mixed);  // defect correction (3D)
   for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     const int pos = FWD ? HOM_LDG(sp.perm + j) : j;
-    out[base + (size_t)j * rowstride + w] = s[(size_t)w * n + pos];
+    const size_t ad = base + (size_t)j * rowstride + w;
+    out[ad] = srcm ? s[(size_t)w * n + pos] + srcm[ad] : s[(size_t)w * n + pos];
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)n * nl * sizeof(V)));
@@ -611,7 +616,9 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
       A.errn[pair] = en;
       const double crit = A.criterion == HOM_CRIT_E ? e : en;
       int st = -1;
-      if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
+      if (A.inner) {  // defect-correction inner solve: a fixed number of iterations, no error test
+        if (it >= A.kinner[pair]) st = HOM_STATUS_MAX_ITER;
+      } else if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
       else if (crit < A.tol) st = HOM_STATUS_CONVERGED;
       else if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
       else {
@@ -682,6 +689,94 @@ __global__ void k_init(SolveArgs A, int ncells, int nc) {
       const size_t ad = c.ws_off + ((size_t)l * c.nrows + row) * c.Hp * nc + comp;
       static_cast<V*>(A.eps[0])[ad] = mk((T)A.E[((size_t)cell * A.L + l) * nc + comp], T(0));
     }
+  }
+}
+
+// ------------------------------------------------------------------ defect correction
+// Element ranges of pair p's strain state (ε layout) and displacement-like state (g layout).
+__device__ __forceinline__ void pair_ranges(const SolveArgs& A, int p, size_t& e0, size_t& ne, size_t& g0, size_t& ng) {
+  const PairDev pd = A.pairs[p];
+  const CellDev c = A.cells[pd.cell];
+  ne = (size_t)c.nrows * c.Hp * c.nc;
+  e0 = c.ws_off + (size_t)pd.load * ne;
+  ng = (size_t)c.nrows * c.Hp * c.dim;
+  g0 = c.g_off + (size_t)pd.load * ng;
+}
+
+enum RefineOp {
+  kRefStart,   // eps64 = eps32[(iters + 1) & 1], g64 = g32  (the last FP32 iterate and its g)
+  kRefResid,   // r32 = eps64[1] - eps64[0]                   (F(eps) - eps, rounded to FP32)
+  kRefUpdate,  // eps64[0] += eps32[(k + 1) & 1], g64 += g32  (the correction after k inner steps)
+  kRefFinal    // eps32[iters & 1] = eps64[0]                 (the returned iterate, for the output pass)
+};
+
+// One element-wise step of the defect correction over the pairs with mask[p] != 0; blockIdx.y = pair.
+template <int OP>
+__global__ void k_refine(SolveArgs A, const int* mask, const float2* eps32a, const float2* eps32b, float2* g32,
+                         double2* eps64a, const double2* eps64b, double2* g64, float2* r32, int kinner) {
+  const int p = blockIdx.y;
+  if (!mask[p]) return;
+  size_t e0, ne, g0, ng;
+  pair_ranges(A, p, e0, ne, g0, ng);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (OP == kRefStart) {
+    const float2* e32 = ((A.iters[p] + 1) & 1) ? eps32b : eps32a;
+    for (size_t i = i0; i < ne; i += stride) eps64a[e0 + i] = make_double2(e32[e0 + i].x, e32[e0 + i].y);
+    for (size_t i = i0; i < ng; i += stride) g64[g0 + i] = make_double2(g32[g0 + i].x, g32[g0 + i].y);
+  } else if (OP == kRefResid) {
+    for (size_t i = i0; i < ne; i += stride) {
+      const double2 a = eps64b[e0 + i], b = eps64a[e0 + i];
+      r32[e0 + i] = make_float2((float)(a.x - b.x), (float)(a.y - b.y));
+    }
+  } else if (OP == kRefUpdate) {
+    const float2* d32 = ((A.kinner[p] + 1) & 1) ? eps32b : eps32a;
+    for (size_t i = i0; i < ne; i += stride) {
+      double2 a = eps64a[e0 + i];
+      a.x += d32[e0 + i].x;
+      a.y += d32[e0 + i].y;
+      eps64a[e0 + i] = a;
+    }
+    for (size_t i = i0; i < ng; i += stride) {
+      double2 a = g64[g0 + i];
+      a.x += g32[g0 + i].x;
+      a.y += g32[g0 + i].y;
+      g64[g0 + i] = a;
+    }
+  } else {
+    float2* e32 = const_cast<float2*>((A.iters[p] & 1) ? eps32b : eps32a);
+    for (size_t i = i0; i < ne; i += stride) e32[e0 + i] = make_float2((float)eps64a[e0 + i].x, (float)eps64a[e0 + i].y);
+  }
+}
+
+// The start of the inner solve of pair p: delta^0 = r (in eps32[0]), bookkeeping of pair p reset.
+__global__ void k_refine_inner_start(SolveArgs A, const int* mask, const float2* r32, float2* eps32a) {
+  const int p = blockIdx.y;
+  if (!mask[p]) return;
+  size_t e0, ne, g0, ng;
+  pair_ranges(A, p, e0, ne, g0, ng);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (size_t)gridDim.x * blockDim.x)
+    eps32a[e0 + i] = r32[e0 + i];
+}
+
+// Bookkeeping of a refinement phase: pairs with mask[p] start active, the others stay inactive.
+__global__ void k_init_pairs_masked(SolveArgs A, const int* mask) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < A.npairs) {
+    A.active[p] = mask[p] ? 1 : 0;
+    A.iters[p] = 0;
+    A.status[p] = -1;
+    A.grow[p] = 0;
+    A.last_err[p] = INFINITY;
+    A.best_err[p] = INFINITY;
+    A.best_it[p] = 0;
+  }
+  if (p == 0) {
+    int cnt = 0;
+    for (int q = 0; q < A.npairs; ++q) cnt += mask[q] ? 1 : 0;
+    *A.it_dev = 0;
+    *A.nactive = cnt;
+    *A.done = 0u;
   }
 }
 
@@ -1016,6 +1111,194 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Defect correction of the pairs the FP32 iteration left stalled (or at max_iter): from their last
+// FP32 iterate eps (and its g), repeat up to opts->refine times
+//   one FP64 iteration of the basic scheme on eps: its equilibrium error (FP64; the pair stops
+//     when it passes opts->tol) and F(eps);
+//   r = F(eps) - eps, rounded to FP32;
+//   K + 1 FP32 iterations of the correction's fixed point delta <- r + F0(delta), delta^0 = r
+//     (F0: the map with zero mean strain; the Green pass adds r to every new iterate);
+//   eps <- eps + delta and g <- g(F(eps)) + g', in FP64.
+// FP32 rounding then acts on the correction, not on the strain, so the FP32 iteration's floor no
+// longer limits the attainable error.  On return the refined pairs' results (mean stress, errors,
+// status, Green-operator applications) replace the FP32 ones and their iterate, rounded to FP32,
+// sits where the output pass reads it.
+template <typename T, int DIM, int MAXR>
+int refine_solve(SolveArgs& A, unsigned char* ws, int npairs, int nc, const hom_solve_opts* opts, const Layout& lay,
+                 size_t o_e64a, size_t o_e64b, size_t o_t64, size_t o_g64, size_t o_r32, size_t o_int2, size_t o_dbl2,
+                 size_t o_mask, size_t o_plans64, size_t o_E0, cudaStream_t st) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return HOM_OK;
+  } else {
+    std::vector<int> h_st(npairs), h_it(npairs), mask(npairs, 0);
+    HOM_CUDA_TRY(cudaMemcpyAsync(h_st.data(), A.status, npairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(h_it.data(), A.iters, npairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> h_e(npairs);
+    HOM_CUDA_TRY(cudaMemcpyAsync(h_e.data(), opts->criterion == HOM_CRIT_E ? A.err : A.errn, npairs * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+    // inner iterations: the FP32 iteration took it_p steps to bring the error from about 1 to e_p,
+    // a contraction of e_p^(1/it_p) per step; one correction should shrink the error to a fifth of
+    // tol, i.e. by f_p = tol / (5 e_p): K_p = it_p ln f_p / ln e_p (the largest over the pairs)
+    int nref = 0, K = 0;
+    std::vector<int> kin(npairs, 0);
+    for (int p = 0; p < npairs; ++p)
+      if (h_st[p] == HOM_STATUS_STALLED || h_st[p] == HOM_STATUS_MAX_ITER) {
+        mask[p] = 1;
+        ++nref;
+        const double e = h_e[p], f = opts->tol / (5.0 * e);
+        double kd = h_it[p];
+        if (e > 0.0 && e < 0.5 && f < 1.0 && f > 0.0) kd = h_it[p] * std::log(f) / std::log(e);
+        kin[p] = opts->refine_inner > 0 ? opts->refine_inner
+                                        : (int)std::ceil(std::min(std::max(kd, 10.0), 2.0 * std::max(h_it[p], 5)));
+        K = std::max(K, kin[p]);
+      }
+    if (nref == 0) return HOM_OK;
+    int* d_mask = reinterpret_cast<int*>(ws + o_mask);
+    int* d_kin = d_mask + npairs;
+    HOM_CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(d_kin, kin.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+    auto book = [&](SolveArgs& X, int which) {  // bookkeeping block `which` (0: FP64 checks, 1: inner solves)
+      int* ib = reinterpret_cast<int*>(ws + o_int2 + (size_t)which * ((size_t)npairs * 5 * sizeof(int) + 64));
+      X.active = ib;
+      X.iters = ib + npairs;
+      X.status = ib + 2 * npairs;
+      X.grow = ib + 3 * npairs;
+      X.best_it = ib + 4 * npairs;
+      X.it_dev = ib + 5 * npairs;
+      X.nactive = ib + 5 * npairs + 1;
+      X.done = reinterpret_cast<unsigned int*>(ib + 5 * npairs + 2);
+      double* db = reinterpret_cast<double*>(ws + o_dbl2) + (size_t)which * npairs * (4 + nc);
+      X.err = db;
+      X.errn = db + npairs;
+      X.last_err = db + 2 * (size_t)npairs;
+      X.best_err = db + 3 * (size_t)npairs;
+      X.mean_sigma = db + 4 * (size_t)npairs;
+      X.diverge_window = 0;
+      X.stall_window = 0;
+      X.cond = 0;
+      X.use_cond = 0;
+    };
+    SolveArgs A64 = A;  // FP64 checks: eps[0] = eps, eps[1] = F(eps)
+    book(A64, 0);
+    A64.plans = reinterpret_cast<const Plan*>(ws + o_plans64);
+    A64.eps[0] = ws + o_e64a;
+    A64.eps[1] = ws + o_e64b;
+    A64.tau = ws + o_t64;
+    A64.g = ws + o_g64;
+    A64.max_iter = 1 << 30;
+    A64.inner = 0;
+    SolveArgs Ain = A;  // inner solves: FP32 buffers of the forward solve, zero mean strain, source r
+    book(Ain, 1);
+    Ain.E = reinterpret_cast<const double*>(ws + o_E0);
+    Ain.src_mixed = ws + o_r32;
+    Ain.tol = -1.0;
+    Ain.max_iter = K;
+    Ain.inner = 1;
+    Ain.kinner = d_kin;
+    A.kinner = d_kin;  // read by the update step
+    const size_t smem_row64 = 2 * lay.smem_row, smem_green64 = 2 * lay.smem_green, smem_y64 = 2 * lay.smem_y;
+    int rc;
+    if ((rc = allow_smem(k_row<double, DIM, false, 15>, smem_row64)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_green<double, DIM, 15>, smem_green64)) != HOM_OK) return rc;
+    if (DIM == 3) {
+      if ((rc = allow_smem(k_ypass<double, true, 15>, smem_y64)) != HOM_OK) return rc;
+      if ((rc = allow_smem(k_ypass<double, false, 15>, smem_y64)) != HOM_OK) return rc;
+    }
+    const unsigned nR = (unsigned)lay.tR.size(), nC = (unsigned)lay.tC.size(), nY = (unsigned)lay.tY.size();
+    auto iter64 = [&]() {
+      k_row<double, DIM, false, 15><<<nR, kThreads, smem_row64, st>>>(A64);
+      if (DIM == 3) k_ypass<double, true, 15><<<nY, kThreads, smem_y64, st>>>(A64);
+      k_green<double, DIM, 15><<<nC, kThreads, smem_green64, st>>>(A64);
+      if (DIM == 3) k_ypass<double, false, 15><<<nY, kThreads, smem_y64, st>>>(A64);
+      k_control<<<(unsigned)npairs, kCtlThreads, 0, st>>>(A64, nc);
+    };
+    auto iter32 = [&]() {
+      k_row<float, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(Ain);
+      if (DIM == 3) k_ypass<float, true, MAXR><<<nY, kThreads, lay.smem_y, st>>>(Ain);
+      k_green<float, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(Ain);
+      if (DIM == 3) k_ypass<float, false, MAXR><<<nY, kThreads, lay.smem_y, st>>>(Ain);
+      k_control<<<(unsigned)npairs, kCtlThreads, 0, st>>>(Ain, nc);
+    };
+    const dim3 eg(64, (unsigned)npairs);
+    float2* e32a = static_cast<float2*>(A.eps[0]);
+    float2* e32b = static_cast<float2*>(A.eps[1]);
+    float2* g32 = static_cast<float2*>(A.g);
+    double2* e64a = reinterpret_cast<double2*>(ws + o_e64a);
+    double2* e64b = reinterpret_cast<double2*>(ws + o_e64b);
+    double2* g64 = reinterpret_cast<double2*>(ws + o_g64);
+    float2* r32 = reinterpret_cast<float2*>(ws + o_r32);
+    k_refine<kRefStart><<<eg, 256, 0, st>>>(A, d_mask, e32a, e32b, g32, e64a, e64b, g64, r32, 0);
+    std::vector<int> h_st64(npairs), extra(npairs, 0), conv(npairs, 0);
+    int steps = 0;
+    for (;;) {
+      // FP64 check of the current iterate (and F of it)
+      k_init_pairs_masked<<<(npairs + 255) / 256, 256, 0, st>>>(A64, d_mask);
+      iter64();
+      HOM_CUDA_TRY(cudaGetLastError());
+      HOM_CUDA_TRY(cudaMemcpyAsync(h_st64.data(), A64.status, npairs * sizeof(int), cudaMemcpyDeviceToHost, st));
+      HOM_CUDA_TRY(cudaStreamSynchronize(st));
+      int left = 0;
+      for (int p = 0; p < npairs; ++p)
+        if (mask[p]) {
+          extra[p] += 1;
+          if (h_st64[p] == HOM_STATUS_CONVERGED) {
+            mask[p] = 0;
+            conv[p] = 1;  // its FP64 results stay in the check's arrays: later checks skip it
+          } else {
+            ++left;
+          }
+        }
+      if (left == 0 || steps >= opts->refine) break;
+      HOM_CUDA_TRY(cudaMemcpyAsync(d_mask, mask.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+      // the correction: K + 1 FP32 iterations of delta <- r + F0(delta) from delta = r
+      k_refine<kRefResid><<<eg, 256, 0, st>>>(A, d_mask, e32a, e32b, g32, e64a, e64b, g64, r32, 0);
+      k_refine_inner_start<<<eg, 256, 0, st>>>(A, d_mask, r32, e32a);
+      k_init_pairs_masked<<<(npairs + 255) / 256, 256, 0, st>>>(Ain, d_mask);
+      for (int k = 0; k <= K; ++k) iter32();
+      k_refine<kRefUpdate><<<eg, 256, 0, st>>>(A, d_mask, e32a, e32b, g32, e64a, e64b, g64, r32, K);
+      HOM_CUDA_TRY(cudaGetLastError());
+      for (int p = 0; p < npairs; ++p)
+        if (mask[p]) extra[p] += kin[p] + 1;
+      ++steps;
+    }
+    // results of the refined pairs: the FP64 check's mean stress and errors, the iterate rounded to
+    // FP32 in the buffer the output pass reads, status converged or (after opts->refine corrections)
+    // the one the FP32 iteration had
+    std::vector<int> all(npairs, 0);
+    for (int p = 0; p < npairs; ++p)
+      if (h_st[p] == HOM_STATUS_STALLED || h_st[p] == HOM_STATUS_MAX_ITER) all[p] = 1;
+    HOM_CUDA_TRY(cudaMemcpyAsync(d_mask, all.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<double> ms((size_t)npairs * nc), err(npairs), errn(npairs), ms64((size_t)npairs * nc), e64(npairs),
+        en64(npairs);
+    HOM_CUDA_TRY(cudaMemcpyAsync(ms.data(), A.mean_sigma, ms.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(err.data(), A.err, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(errn.data(), A.errn, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(ms64.data(), A64.mean_sigma, ms64.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(e64.data(), A64.err, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(en64.data(), A64.errn, npairs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int p = 0; p < npairs; ++p)
+      if (all[p]) {
+        for (int k = 0; k < nc; ++k) ms[(size_t)p * nc + k] = ms64[(size_t)p * nc + k];
+        err[p] = e64[p];
+        errn[p] = en64[p];
+        if (conv[p]) h_st[p] = HOM_STATUS_CONVERGED;
+        h_it[p] += extra[p];
+      }
+    HOM_CUDA_TRY(cudaMemcpyAsync(A.mean_sigma, ms.data(), ms.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(A.err, err.data(), npairs * sizeof(double), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(A.errn, errn.data(), npairs * sizeof(double), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(A.status, h_st.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaMemcpyAsync(A.iters, h_it.data(), npairs * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_refine<kRefFinal><<<eg, 256, 0, st>>>(A, d_mask, e32a, e32b, g32, e64a, e64b, g64, r32, 0);
+    HOM_CUDA_TRY(cudaGetLastError());
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+    return HOM_OK;
+  }
+}
+
 template <typename T, int DIM, int MAXR>
 int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const double* E, int L, const double* c0,
               const hom_solve_opts* opts, hom_result* out, cudaStream_t st, const ExternalWorkspace* ext,
@@ -1045,8 +1328,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     c0 = c0_cg.data();
   }
   // opts->passes == HOM_PASSES_GENERIC keeps every solve on the generic passes
+  // defect correction (FP32 with FP64 residuals) runs on the generic passes: FP32 and FP64 states
+  // then share one layout
+  const bool refine = std::is_same<T, float>::value && opts->refine > 0 && !cg && !adj && !ext;
   lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC &&
-             opts->green == HOM_GREEN_CONTINUOUS;
+             opts->green == HOM_GREEN_CONTINUOUS && !refine;
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1082,7 +1368,18 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_cgpart = cg ? take((size_t)npairs * cg_nchunk * sizeof(double)) : 0;
   const size_t o_cgsc = cg ? take((size_t)npairs * (3 + nc) * sizeof(double)) : 0;
   const size_t o_cgint = cg ? take((size_t)npairs * 2 * sizeof(int)) : 0;
-  const size_t o_E0 = cg ? take((size_t)npairs * nc * sizeof(double)) : 0;
+  const size_t o_E0 = cg || refine ? take((size_t)npairs * nc * sizeof(double)) : 0;
+  // defect correction: FP64 strain state (current and F of it), FP64 tau and g, the FP32 residual,
+  // FP64 plans (register radix 15), and bookkeeping of the FP64 checks and of the inner solves
+  const size_t o_e64a = refine ? take(lay.ws_elems * sizeof(double2)) : 0;
+  const size_t o_e64b = refine ? take(lay.ws_elems * sizeof(double2)) : 0;
+  const size_t o_t64 = refine ? take(lay.ws_elems * sizeof(double2)) : 0;
+  const size_t o_g64 = refine ? take(lay.g_elems * sizeof(double2)) : 0;
+  const size_t o_r32 = refine ? take(lay.ws_elems * sizeof(V)) : 0;
+  const size_t o_int2 = refine ? take(2 * ((size_t)npairs * 5 * sizeof(int) + 64)) : 0;
+  const size_t o_dbl2 = refine ? take(2 * (size_t)npairs * (4 + nc) * sizeof(double)) : 0;
+  const size_t o_mask = refine ? take(2 * (size_t)npairs * sizeof(int)) : 0;
+  const size_t o_plans64 = refine ? take(lay.plans.size() * sizeof(Plan)) : 0;
   long long nv_all = 0, nv_max = 0;
   for (CellDev& c : lay.cells) {
     c.lp_off = nv_all;  // one-byte labels, rows padded to 16 bytes
@@ -1166,6 +1463,14 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_eps0, 0, lay.ws_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_g, 0, lay.g_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_bytes, 0, HOM_NKERNEL * sizeof(unsigned long long), st));
+  if (refine) {
+    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_E0, 0, (size_t)npairs * nc * sizeof(double), st));
+    std::vector<Plan> p64(lay.plans.size());
+    for (size_t i = 0; i < lay.plans.size(); ++i)
+      if ((rc = get_plan(lay.plans[i].n, 15, &p64[i])) != HOM_OK) return rc;
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_plans64, p64.data(), p64.size() * sizeof(Plan), cudaMemcpyHostToDevice, st));
+    HOM_CUDA_TRY(cudaStreamSynchronize(st));  // p64 goes out of scope
+  }
   if (cg) {
     HOM_CUDA_TRY(cudaMemsetAsync(ws + o_E0, 0, (size_t)npairs * nc * sizeof(double), st));
     HOM_CUDA_TRY(cudaMemsetAsync(ws + o_cgint, 0, (size_t)npairs * 2 * sizeof(int), st));
@@ -1213,7 +1518,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.max_iter = opts->max_iter;
   A.green = opts->green;
   A.diverge_window = opts->diverge_window;
-  A.stall_window = opts->stall_window;
+  // defect correction starts from where the FP32 iteration stagnates (30 iterations by default)
+  A.stall_window = opts->stall_window > 0 ? opts->stall_window : (refine ? 30 : 0);
   A.tol = opts->tol;
   A.out_eps = out->eps ? (eps_dev ? out->eps : (void*)(ws + o_stage_e)) : nullptr;
   A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
@@ -1399,6 +1705,12 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaGetLastError());
   }
 
+  if (refine) {
+    rc = refine_solve<T, DIM, MAXR>(A, ws, npairs, nc, opts, lay, o_e64a, o_e64b, o_t64, o_g64, o_r32, o_int2, o_dbl2,
+                                    o_mask, o_plans64, o_E0, st);
+    if (rc != HOM_OK) return rc;
+  }
+
   if (want_fields) {
     tm.begin(HOM_K_OUTPUT);
     if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, true, st);
@@ -1489,6 +1801,9 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown Green operator %d", opts->green);
   if (cg && opts->green != HOM_GREEN_CONTINUOUS)
     return set_error(HOM_ERR_NOT_IMPL, "hom_solve_cg: only the continuous Green operator");
+  if (opts->refine < 0 || opts->refine_inner < 0) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: negative refine option");
+  if (opts->refine > 0 && (opts->precision != HOM_FP32 || cg || adj || ext))
+    return set_error(HOM_ERR_NOT_IMPL, "hom_solve: defect correction is for FP32 forward solves of hom_solve");
   if (!mat->label || !mat->phase_c32 || !mat->phase_c64)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material not built");
   const int dim = cells[0].dim;
