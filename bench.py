@@ -566,11 +566,12 @@ def backward_135(hom, dev, n=135):
 
 
 def cg_comparison(hom, dev, sizes=(135, 405), tol=1e-4):
-    """Accelerated scheme against the basic one on the paper's high-contrast cases (section 5): the
+    """Accelerated schemes against the basic one on the paper's high-contrast cases (section 5): the
     centred disk of radius pi/15 at contrasts 1e3 and 1e-3, n in `sizes`, Voigt and 2-layer filters
     (r = 1 px, S = 16), 3 loads, FP64 (FP32 CG stalls near 1e-2 at contrast 1e3).  The basic scheme
-    stops at e_n < tol, conjugate gradients at e_G < tol (e_G >= e_n: at least as strict), each one
-    batched solve timed with CUDA events after a short warm-up solve; reports the times, the
+    stops at e_n < tol, conjugate gradients at e_G < tol (e_G >= e_n: at least as strict), the
+    Eyre-Milton scheme (reference medium: geometric means of the phase moduli) at max(e_n, e_c) < tol,
+    each one batched solve timed with CUDA events after a short warm-up solve; reports the times, the
     iteration counts and the C_eff agreement."""
     import torch
     cells, phases = [], []
@@ -581,33 +582,40 @@ def cg_comparison(hom, dev, sizes=(135, 405), tol=1e-4):
                 cells.append(H.remap_phases(cell, len(phases)))
                 phases.extend(H.two_phases(contrast))
     c0 = np.array([H.mean_lame(phases[2 * i:2 * i + 2]) for i in range(len(cells))])
+    c0_em = np.array([H.geometric_lame(phases[2 * i:2 * i + 2], 2) for i in range(len(cells))])
     mat = hom.hom_filter_build(cells, phases)
     E = np.eye(3)
     st = torch.cuda.current_stream()
     out = {}
-    for name in ("fixed_point", "cg"):
+    for name in ("fixed_point", "cg", "eyre_milton"):
         def solve(max_iter):
             if name == "cg":
                 return hom.hom_solve_cg(mat, E, precision=hom.HOM_FP64, tol=tol, max_iter=max_iter, fields=False)
+            if name == "eyre_milton":
+                return hom.hom_solve(mat, E, c0_em, precision=hom.HOM_FP64, criterion=hom.HOM_CRIT_EN, tol=tol,
+                                     max_iter=max_iter, fields=False, scheme=hom.HOM_SCHEME_EYRE_MILTON)
             return hom.hom_solve(mat, E, c0, precision=hom.HOM_FP64, criterion=hom.HOM_CRIT_EN, tol=tol,
                                  max_iter=max_iter, fields=False)
         solve(20)  # warm-up: plans and workspace
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(st)
-        r = solve(4000 if name == "cg" else 30000)
+        r = solve(4000 if name != "fixed_point" else 30000)
         t1.record(st)
         torch.cuda.synchronize()
         out[name] = dict(ms=round(t0.elapsed_time(t1), 2), iterations_max=int(r["iterations"].max()),
                          iterations_median=float(np.median(r["iterations"])),
                          status_counts={str(k): int(v) for k, v in zip(*np.unique(r["status"], return_counts=True))},
                          C=hom.hom_effective_stiffness(E, r["mean_sigma"], 2))
-    Cf, Cc = out["fixed_point"].pop("C"), out["cg"].pop("C")
+    Cf, Cc, Ce = out["fixed_point"].pop("C"), out["cg"].pop("C"), out["eyre_milton"].pop("C")
     diff = max(float(np.abs(Cf[i] - Cc[i]).max() / np.abs(Cf[i]).max()) for i in range(len(cells)))
+    diff_em = max(float(np.abs(Cf[i] - Ce[i]).max() / np.abs(Cf[i]).max()) for i in range(len(cells)))
     return {"workload": "disk r = pi/15, contrasts 1e3 and 1e-3, n in %s, Voigt and 2-layer, 3 loads, FP64, "
                         "e_n (fixed point) / e_G (CG) < %g" % (list(sizes), tol),
-            "cells": len(cells), "fixed_point": out["fixed_point"], "cg": out["cg"],
-            "speedup": round(out["fixed_point"]["ms"] / out["cg"]["ms"], 2), "ceff_max_rel_diff": diff}
+            "cells": len(cells), "fixed_point": out["fixed_point"], "cg": out["cg"], "eyre_milton": out["eyre_milton"],
+            "speedup": round(out["fixed_point"]["ms"] / out["cg"]["ms"], 2),
+            "speedup_eyre_milton": round(out["fixed_point"]["ms"] / out["eyre_milton"]["ms"], 2),
+            "ceff_max_rel_diff": diff, "ceff_max_rel_diff_eyre_milton": diff_em}
 
 
 def ensemble_2d(hom, dev, count=256):

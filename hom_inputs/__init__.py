@@ -80,6 +80,16 @@ def mean_lame(phases: Sequence[Tuple[float, float]]) -> Tuple[float, float]:
     return 0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus))
 
 
+def geometric_lame(phases: Sequence[Tuple[float, float]], dim: int) -> Tuple[float, float]:
+    """Reference medium for the Eyre-Milton scheme: geometric means of the extreme phase shear
+    moduli and bulk moduli lambda + 2 mu / dim, returned as a Lame pair."""
+    mus = [p[1] for p in phases]
+    ks = [p[0] + 2.0 * p[1] / dim for p in phases]
+    mu0 = math.sqrt(min(mus) * max(mus))
+    k0 = math.sqrt(min(ks) * max(ks))
+    return k0 - 2.0 * mu0 / dim, mu0
+
+
 def ncomp(dim: int) -> int:
     """Number of independent strain components (Mandel vector length)."""
     return 3 if dim == 2 else 6

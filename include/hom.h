@@ -56,6 +56,9 @@ extern "C" {
 #define HOM_ERR_OOM 7               /* workspace allocation failed                            */
 #define HOM_ERR_CAPACITY 8          /* mixed-voxel table too small; mixed_count = needed size */
 #define HOM_ERR_NOT_IMPL 9          /* requested combination is not implemented               */
+#define HOM_ERR_BOUNDS 10           /* bounds-checked build (HOM_BUILD_DEBUG): a kernel found an
+                                       index outside its array and skipped the access; the
+                                       message names the source file id and line              */
 
 /* ------------------------------------------------------------------ enumerations */
 #define HOM_PRIM_DISK 0    /* 2D disk: centre[0..1], radius                                     */
@@ -78,6 +81,13 @@ extern "C" {
 #define HOM_GREEN_CONTINUOUS 0 /* eq. (2) at xi = 2 pi a on J (the paper's operator)                 */
 #define HOM_GREEN_ROTATED 1    /* rotated finite-difference scheme: eq. (2)'s formula, and the       */
                                /* equilibrium check, at q_j = 2n sin(pi a_j/n) prod_{m!=j} cos(pi a_m/n) */
+
+/* Iteration scheme of hom_solve (the basic scheme of section 2, or an accelerated scheme of the
+ * kind its introduction and section 5 cite as complementary to filtering). */
+#define HOM_SCHEME_BASIC 0       /* eqs. 1-a, 1-b, 2: eps <- E - Gamma0 * ((c~ - c0) : eps)          */
+#define HOM_SCHEME_EYRE_MILTON 1 /* u = sigma + c0 : eps, u <- (I - 2 c0 Gamma0)(W u + 2 c0 : E),     */
+                                 /* W = (c~ - c0)(c~ + c0)^-1: contraction (sqrt(k) - 1)/(sqrt(k) + 1) */
+                                 /* for a contrast k with c0 the geometric mean of the phase moduli   */
 
 #define HOM_CRIT_E 0  /* e   = sqrt(sum_k |xi_k . sigma_hat(k)|^2) / ||sigma_hat(0)||          */
 #define HOM_CRIT_EN 1 /* e_n = sqrt(sum_{k!=0} |(xi_k/|xi_k|) . sigma_hat(k)|^2) / ||sigma_hat(0)|| */
@@ -178,6 +188,15 @@ typedef struct hom_solve_opts {
   int32_t refine_inner;   /* FP32 iterations per correction (0: from the FP32 iteration's */
                           /* observed contraction, enough for one correction to bring the */
                           /* error to tol / 5)                                            */
+  int32_t scheme;         /* HOM_SCHEME_BASIC (0) or HOM_SCHEME_EYRE_MILTON: generic passes,  */
+                          /* FP32 or FP64, continuous Green operator, hom_solve only, no   */
+                          /* refine                                                        */
+  int32_t warm_start;     /* 1: hom_result.eps (device, field type) holds the initial strain */
+                          /* field of every load case on entry (state in / out: the returned */
+                          /* fields overwrite it).  It need not be compatible: iterate 0 is */
+                          /* neither checked nor returned, the first Green-operator         */
+                          /* application makes it compatible with mean E.  Basic scheme of   */
+                          /* hom_solve, generic passes, no refine.  0 = start from eps = E   */
 } hom_solve_opts;
 
 /* Per-kernel timing, filled when hom_result.stats is non-NULL (adds CUDA events around every
@@ -209,6 +228,15 @@ typedef struct hom_result {
   double* err;          /* optional host [ncells*L]: e of the returned iterate                  */
   double* err_n;        /* optional host [ncells*L]: e_n of the returned iterate                */
   hom_kernel_stats* stats; /* optional host: per-kernel timing                                  */
+  double* err_c;        /* optional host [ncells*L]: Eyre-Milton scheme only, the compatibility
+                           error e_c = RMS(eps - P eps) / |E| of the returned iterate (P: the
+                           projection onto compatible fields of mean E, orthogonal for c0);
+                           0 for the basic scheme, whose iterates are compatible by construction */
+  double* history;      /* optional, host or device [ncells*L][max_iter + 1]: entry i of a load
+                           case is the stopping quantity of its iterate i (the chosen error, for the
+                           Eyre-Milton scheme the larger of it and e_c; NaN for the unchecked iterate
+                           0 of a warm start), written for i = 0 .. iterations (the rest untouched);
+                           the FP32 iteration only when opts->refine > 0.  hom_solve only      */
 } hom_result;
 
 /* ------------------------------------------------------------------ entry points */
@@ -246,7 +274,17 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
  * With opts->use_graph = 1 (and out->stats = NULL) the iterations run as one launch of a CUDA graph
  * whose conditional WHILE node repeats one iteration until the control kernel finds no active load
  * case or the iteration budget spent; the instantiated graph is kept for later calls with the same
- * arguments (same material, workspace, sizes and options; outputs may differ). */
+ * arguments (same material, workspace, sizes and options; outputs may differ).
+ * opts->scheme = HOM_SCHEME_EYRE_MILTON iterates u = sigma + c0 : eps instead, from u = 2 c0 : E:
+ *   eps = (c~ + c0)^-1 : u per voxel (pure voxels in closed form, mixed ones through a per-call
+ *   table of (c~ + c0)^-1), tau = c~ : eps - c0 : eps, and the new u_hat = tau_hat - 2 c0 :
+ *   Gamma0(k) : tau_hat (k != 0; Gamma0 is left out at Nyquist bins of even grids, as in the basic
+ *   scheme), u_hat(0) = tau_hat(0) + 2 c0 : E.  The iterates are not compatible before convergence,
+ *   so a load case stops only when both its equilibrium error (opts->criterion) and its
+ *   compatibility error e_c (hom_result.err_c) are below opts->tol.  Any positive-definite c0
+ *   converges; the geometric means of the extreme phase moduli (bulk and shear) give the fastest
+ *   contraction.  Generic passes only (opts->passes is ignored), continuous Green operator; returns
+ *   HOM_ERR_NOT_IMPL with opts->green = HOM_GREEN_ROTATED or opts->refine > 0. */
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 
@@ -376,6 +414,13 @@ void hom_release(void);
 
 /* Library version, major * 10000 + minor * 100 + patch. */
 int32_t hom_version(void);
+
+/* Build flags of the loaded library: HOM_BUILD_DEBUG when it was compiled with -DHOM_DEBUG, whose
+ * solver kernels check their global indices (state, g, output fields, labels) and their task
+ * descriptors against the arrays' extents, record the first failure and skip the access (the call
+ * then returns HOM_ERR_BOUNDS), and fill their dynamic shared memory with NaN bytes before use. */
+#define HOM_BUILD_DEBUG 1
+int32_t hom_build_flags(void);
 
 #ifdef __cplusplus
 }

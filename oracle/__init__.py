@@ -282,11 +282,14 @@ def constitutive(ctilde: np.ndarray, eps: np.ndarray) -> np.ndarray:
 
 
 def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
-              tol: float, max_iter: int, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS) -> Dict:
+              tol: float, max_iter: int, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS,
+              eps0: np.ndarray = None) -> Dict:
     """Basic fixed-point scheme for one macroscopic strain E (Mandel [nc]):
-        eps^0 = E
+        eps^0 = E  (or the given field eps0 [nc, *grid]: a warm start)
         repeat i = 0, 1, ...:
             sigma^i = c : eps^i ; evaluate the equilibrium error of sigma^i; stop if < tol
+                (a warm start's eps^0 need not be compatible, so iterate 0 is then never returned:
+                the first Green-operator application makes the iterate compatible with mean E)
             tau^i = sigma^i - c0 : eps^i
             eps_hat^{i+1}(k) = -Gamma0(k) : tau_hat^i(k)   (k in J, k != 0)
             eps_hat^{i+1}(0) = E (times N_v for the unnormalised DFT)
@@ -300,6 +303,8 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
     eps = np.empty((nc,) + grid)
     for I in range(nc):
         eps[I] = E[I]
+    if eps0 is not None:
+        eps = np.array(eps0, dtype=np.float64).reshape((nc,) + grid)
     errs, errs_n = [], []
     status = "max_iter"
     it = 0
@@ -312,7 +317,7 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
         if not math.isfinite(err):
             status = "diverged"
             break
-        if err < tol:
+        if err < tol and not (eps0 is not None and it == 0):
             status = "converged"
             break
         if it >= max_iter:
@@ -329,10 +334,13 @@ def solve_one(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: 
 
 
 def solve(ctilde: np.ndarray, dim: int, n: int, lam0: float, mu0: float, E: np.ndarray,
-          tol: float = 1e-8, max_iter: int = 1000, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS) -> Dict:
-    """Solve every load case (rows of E, Mandel [L, nc]) independently."""
+          tol: float = 1e-8, max_iter: int = 1000, criterion: int = CRIT_E, scheme: int = SCHEME_CONTINUOUS,
+          eps0: np.ndarray = None) -> Dict:
+    """Solve every load case (rows of E, Mandel [L, nc]) independently; eps0 [L, nc, *grid]
+    optionally warm-starts each."""
     E = np.atleast_2d(np.asarray(E, dtype=np.float64))
-    runs = [solve_one(ctilde, dim, n, lam0, mu0, E[l], tol, max_iter, criterion, scheme) for l in range(E.shape[0])]
+    runs = [solve_one(ctilde, dim, n, lam0, mu0, E[l], tol, max_iter, criterion, scheme,
+                      None if eps0 is None else eps0[l]) for l in range(E.shape[0])]
     return dict(eps=np.stack([r["eps"] for r in runs]), sigma=np.stack([r["sigma"] for r in runs]),
                 mean_sigma=np.stack([r["mean_sigma"] for r in runs]),
                 iterations=np.array([r["iterations"] for r in runs]),

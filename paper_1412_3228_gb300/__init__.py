@@ -29,10 +29,13 @@ HOM_OK = 0
 HOM_ERR_NOT_CONVERGED = 3
 HOM_ERR_DIVERGED = 4
 HOM_ERR_CAPACITY = 8
+HOM_ERR_NOT_IMPL = 9
+HOM_ERR_BOUNDS = 10
 HOM_FP32, HOM_FP64 = 0, 1
 HOM_CRIT_E, HOM_CRIT_EN = 0, 1
 HOM_PASSES_AUTO, HOM_PASSES_GENERIC = 0, 1
 HOM_GREEN_CONTINUOUS, HOM_GREEN_ROTATED = 0, 1
+HOM_SCHEME_BASIC, HOM_SCHEME_EYRE_MILTON = 0, 1
 HOM_STATUS = {0: "converged", 1: "max_iter", 2: "diverged", 3: "stalled", -1: "active"}
 HOM_MIXED_BIT = 0x80000000
 HOM_NKERNEL = 8
@@ -40,7 +43,7 @@ KERNEL_NAMES = ["filter", "row", "yfwd", "green", "yinv", "control", "output", "
 
 EXPORTED = ["hom_filter_build", "hom_solve", "hom_solve_noalloc", "hom_solve_cg", "hom_solve_backward",
             "hom_effective_stiffness", "hom_fourier_extrapolate", "hom_autotune_report", "hom_last_error", "hom_release",
-            "hom_version"]
+            "hom_version", "hom_build_flags"]
 
 
 class HomError(RuntimeError):
@@ -78,7 +81,8 @@ class hom_solve_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("diverge_window", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("max_radix", ctypes.c_int32), ("green", ctypes.c_int32), ("tune", ctypes.c_int32),
-                ("stall_window", ctypes.c_int32), ("refine", ctypes.c_int32), ("refine_inner", ctypes.c_int32)]
+                ("stall_window", ctypes.c_int32), ("refine", ctypes.c_int32), ("refine_inner", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("warm_start", ctypes.c_int32)]
 
 
 class hom_kernel_stats(ctypes.Structure):
@@ -89,7 +93,8 @@ class hom_kernel_stats(ctypes.Structure):
 class hom_result(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("mean_sigma", ctypes.c_void_p),
                 ("iterations", ctypes.c_void_p), ("status", ctypes.c_void_p), ("err", ctypes.c_void_p),
-                ("err_n", ctypes.c_void_p), ("stats", ctypes.POINTER(hom_kernel_stats))]
+                ("err_n", ctypes.c_void_p), ("stats", ctypes.POINTER(hom_kernel_stats)), ("err_c", ctypes.c_void_p),
+                ("history", ctypes.c_void_p)]
 
 
 _lib_handle = None
@@ -125,8 +130,20 @@ def lib() -> ctypes.CDLL:
         h.hom_autotune_report.restype = ctypes.c_int32
         h.hom_last_error.restype = ctypes.c_char_p
         h.hom_version.restype = ctypes.c_int32
+        h.hom_build_flags.restype = ctypes.c_int32
         _lib_handle = h
     return _lib_handle
+
+
+def use_debug_library() -> str:
+    """Load the bounds-checked build of the library (-DHOM_DEBUG, built on first use) instead of the
+    release one.  Call before the first call into the library; returns its path."""
+    global LIB_PATH
+    if _lib_handle is not None:
+        raise RuntimeError("libhom.so is already loaded in this process")
+    from . import _build_lib
+    LIB_PATH = _build_lib.build(debug=True)
+    return LIB_PATH
 
 
 def _check(code: int, allow=(HOM_OK,)) -> int:
@@ -271,15 +288,21 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
               host_fields: bool = False, check_every: int = 0, diverge_window: int = 0, use_graph: bool = False,
               passes: int = HOM_PASSES_AUTO, max_radix: int = 0, green: int = HOM_GREEN_CONTINUOUS,
               tune: bool = False, stall_window: int = 0, refine: int = 0, refine_inner: int = 0,
+              scheme: int = HOM_SCHEME_BASIC, eps0: Optional[torch.Tensor] = None, history: bool = False,
               stats: bool = False, stream=None,
               allow_not_converged: bool = True, _entry: str = "hom_solve") -> dict:
-    """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2).
+    """Basic fixed-point scheme for every cell x load case (section 2, eqs. 1-a, 1-b, 2), or the
+    Eyre-Milton scheme with scheme=HOM_SCHEME_EYRE_MILTON.
 
     E: [ncells, L, nc] (or [L, nc], shared by every cell) Mandel macroscopic strains.
     c0: [ncells, 2] (or [2]) Lamé constants of the reference medium.
     Returns a dict with eps / sigma fields ([sum over cells of L*nc*n^dim], flat, cell-major),
-    mean_sigma [ncells, L, nc], iterations / status / err / err_n [ncells, L] and the kernel
-    statistics when stats=True."""
+    mean_sigma [ncells, L, nc], iterations / status / err / err_n / err_c [ncells, L] and the
+    kernel statistics when stats=True.
+    eps0: warm start, a device tensor laid out like the returned eps (field precision); the solve
+    reads it through the returned eps buffer, which starts as a copy of it.
+    history=True adds "history" [ncells, L, max_iter + 1]: the stopping quantity of every
+    iterate (NaN where not written)."""
     cells = material.cells
     ncells = len(cells)
     dim = material.dim
@@ -294,6 +317,9 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
     ftype = torch.float32 if precision == HOM_FP32 else torch.float64
     nfield = sum(L * nc * c.n ** c.dim for c in cells)
     eps = sig = None
+    if eps0 is not None:
+        fields = True
+        host_fields = False
     if fields:
         if host_fields:
             eps = torch.empty(nfield, dtype=ftype, pin_memory=True)
@@ -301,20 +327,28 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
         else:
             eps = torch.empty(nfield, dtype=ftype, device=device)
             sig = torch.empty(nfield, dtype=ftype, device=device)
+            if eps0 is not None:
+                if eps0.numel() != nfield or eps0.dtype != ftype:
+                    raise ValueError("eps0 must hold %d values of %s" % (nfield, ftype))
+                eps.copy_(eps0.reshape(-1))
     mean_sigma = np.zeros((ncells, L, nc))
     iters = np.zeros((ncells, L), dtype=np.int32)
     status = np.zeros((ncells, L), dtype=np.int32)
     err = np.zeros((ncells, L))
     err_n = np.zeros((ncells, L))
+    err_c = np.zeros((ncells, L))
+    hist = np.full((ncells, L, int(max_iter) + 1), np.nan) if history else None
     st = hom_kernel_stats() if stats else None
     res = hom_result(eps=_ptr(eps), sigma=_ptr(sig), mean_sigma=mean_sigma.ctypes.data,
                      iterations=iters.ctypes.data, status=status.ctypes.data, err=err.ctypes.data,
-                     err_n=err_n.ctypes.data, stats=ctypes.pointer(st) if st is not None else None)
+                     err_n=err_n.ctypes.data, stats=ctypes.pointer(st) if st is not None else None,
+                     err_c=err_c.ctypes.data, history=hist.ctypes.data if hist is not None else None)
     opts = hom_solve_opts(precision=precision, criterion=criterion, tol=float(tol), max_iter=int(max_iter),
                           check_every=int(check_every), diverge_window=int(diverge_window),
                           use_graph=int(bool(use_graph)), passes=int(passes), max_radix=int(max_radix),
                           green=int(green), tune=int(bool(tune)), stall_window=int(stall_window),
-                          refine=int(refine), refine_inner=int(refine_inner))
+                          refine=int(refine), refine_inner=int(refine_inner), scheme=int(scheme),
+                          warm_start=int(eps0 is not None))
     with torch.cuda.device(device):
         if _entry == "hom_solve_cg":
             code = lib().hom_solve_cg(material.marshalled.cells, ncells, ctypes.byref(material.struct),
@@ -328,7 +362,9 @@ def hom_solve(material: Material, E, c0, *, L: Optional[int] = None, precision: 
     allowed = (HOM_OK, HOM_ERR_NOT_CONVERGED, HOM_ERR_DIVERGED) if allow_not_converged else (HOM_OK,)
     _check(code, allowed)
     out = dict(eps=eps, sigma=sig, mean_sigma=mean_sigma, iterations=iters, status=status, err=err,
-               err_n=err_n, code=code, E=E, L=L)
+               err_n=err_n, err_c=err_c, code=code, E=E, L=L)
+    if hist is not None:
+        out["history"] = hist
     if st is not None:
         out["stats"] = {KERNEL_NAMES[k]: dict(launches=int(st.launches[k]), ms=float(st.ms[k]),
                                               bytes=float(st.bytes[k])) for k in range(HOM_NKERNEL)}

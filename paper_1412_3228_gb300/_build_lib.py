@@ -4,7 +4,8 @@
 
 builds paper_1412_3228_gb300/_build/libhom.so with nvcc: each translation unit is compiled in
 parallel for `-gencode arch=compute_103a,code=sm_103a` and linked with the static CUDA runtime.
-The build is skipped when the library is newer than every source file.
+The build is skipped when the library is newer than every source file.  build(debug=True) makes
+the bounds-checked variant (-DHOM_DEBUG) in paper_1412_3228_gb300/_build_debug/libhom.so.
 """
 from __future__ import annotations
 
@@ -18,6 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhom.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libhom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["hom_capi.cu", "hom_filter.cu", "hom_solver.cu", "hom_fast2d.cu", "hom_fast3d.cu", "hom_noalloc.cu", "hom_backward.cu", "hom_extrap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -30,22 +33,25 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhom.so")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build libhom.so if needed and return its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build libhom.so (or its bounds-checked variant) if needed and return its path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH
+    if debug:
+        common.append("-DHOM_DEBUG")
     if os.environ.get("HOM_PTXAS_VERBOSE"):
         common += ["-Xptxas", "-v"]
     if os.environ.get("HOM_THREADS"):  # threads per CTA of the solver passes (tuning)
@@ -63,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             common.append(d)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -74,14 +80,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

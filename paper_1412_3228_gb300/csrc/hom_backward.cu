@@ -224,6 +224,7 @@ extern "C" int hom_solve_backward(const hom_cell* cells, int32_t ncells, const h
                                   int32_t L, const hom_solve_opts* opts, const void* eps, const double* dL_dC,
                                   const void* dL_dsigma, void* dL_dctilde, double* dL_dphase, double* dL_dfrac,
                                   hom_result* adjoint_info, void* stream) {
+  ::hom::NvtxRange nvtx_range_("hom_solve_backward");
   cudaGetLastError();  // do not report an error left behind by an unrelated earlier call
   if (!cells || ncells <= 0 || !mat || !c0 || !opts || !eps || !dL_dphase)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve_backward: null argument");

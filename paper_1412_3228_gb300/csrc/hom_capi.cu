@@ -117,6 +117,14 @@ extern "C" const char* hom_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int32_t hom_version(void) { return 100; }
 
+extern "C" int32_t hom_build_flags(void) {
+#ifdef HOM_DEBUG
+  return HOM_BUILD_DEBUG;
+#else
+  return 0;
+#endif
+}
+
 extern "C" void hom_release(void) {
   std::lock_guard<std::mutex> lk(g_mutex);
   int cur = 0;

@@ -71,6 +71,7 @@ unsigned blocks_for(int64_t count) { return (unsigned)((count + kT - 1) / kT); }
 
 extern "C" int hom_fourier_extrapolate(const hom_cell* cells, int32_t ncells, const hom_material* mat, int32_t cell,
                                        int32_t comp, int32_t m, double* out, void* stream) {
+  ::hom::NvtxRange nvtx_range_("hom_fourier_extrapolate");
   using namespace hom;
   if (!cells || ncells <= 0 || !mat || !mat->label || !mat->phase_c64 || !out)
     return set_error(HOM_ERR_INVALID_ARG, "hom_fourier_extrapolate: null or empty argument");

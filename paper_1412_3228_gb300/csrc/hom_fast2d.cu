@@ -23,6 +23,7 @@
 // Green pass keeps its displacement-like state g as [load][column pair][position][4 complex].
 // Both layouts are private to these passes: the initial state and the output fields are written
 // by the kernels here.
+#define HOM_FILE_ID 2
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -433,6 +434,7 @@ __device__ __forceinline__ void prefetch_row_task(const SolveArgs& A, int task) 
 // is about the one that starts when this CTA ends, so CTA b prefetches its first load into L2.
 template <bool OUT, bool SRC>
 __global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A, int ntasks, int ahead) {
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
@@ -440,6 +442,10 @@ __global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A
   if ((HOM_ROW_PREFETCH & 2) && task + ahead < ntasks) prefetch_row_task<OUT>(A, task + ahead);
   const TaskR t = A.tR[task];
   const CellDev c = A.cells[t.cell];
+  // debug builds: the task's rows lie in the cell (the CTA skips a bad task as a whole)
+  if (!HOM_CHECK(A, t.row0 >= 0 && t.nrows >= 1 && t.nrows <= kFastRows && t.row0 + t.nrows <= c.nrows &&
+                        t.load < A.L, (size_t)task))
+    return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
     case 45: row_body<45, OUT, SRC>(A, task, t, c, fp, s, sh); break;
@@ -638,12 +644,16 @@ __device__ __forceinline__ void prefetch_green_task(const SolveArgs& A, int task
 
 // One CTA per task; CTA b prefetches task b + ahead into L2 (see k_row_f2d).
 __global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveArgs A, int ntasks, int ahead) {
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const int task = blockIdx.x;
   if (HOM_GREEN_PREFETCH && task + ahead < ntasks) prefetch_green_task(A, task + ahead);
   const TaskL t = A.tC[task];
   const CellDev c = A.cells[t.cell];
+  // debug builds: an even kx pair start inside the half spectrum, a valid load
+  if (!HOM_CHECK(A, t.kx0 >= 0 && (t.kx0 & 1) == 0 && t.kx0 < c.H && t.load >= 0 && t.load < A.L, (size_t)task))
+    return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
     case 45: green_body<45>(A, task, t, c, fp, s); break;

@@ -17,6 +17,7 @@
 // task reads 4 x 96 contiguous bytes per pair and a y task one contiguous tile; the Green pass
 // gathers 96-byte pieces with 16-byte asynchronous copies.  The displacement-like state g of the
 // Green pass is private: [load][kx pair][y position][z position][3 lane pairs].
+#define HOM_FILE_ID 3
 #include <algorithm>
 
 #include "hom_fast2d.h"
@@ -328,6 +329,7 @@ __device__ __forceinline__ void prefetch_row3_task(const SolveArgs& A, int task)
 // when this CTA ends: `ahead` CTAs are resident at once) into L2.
 template <bool OUT, bool SRC>
 __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks, int ahead) {
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowShared3 sh;
   float4* s = reinterpret_cast<float4*>(smem_raw);
@@ -335,6 +337,10 @@ __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks
   if (task + ahead < ntasks) prefetch_row3_task<OUT>(A, task + ahead);
   const TaskR t = A.tR[task];
   const CellDev c = A.cells[t.cell];
+  // debug builds: the task's rows lie in one z plane of the cell
+  if (!HOM_CHECK(A, t.row0 >= 0 && t.nrows >= 1 && t.row0 + t.nrows <= c.nrows &&
+                        t.row0 / c.n == (t.row0 + t.nrows - 1) / c.n && t.load < A.L, (size_t)task))
+    return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
     case 27: row3_body<27, OUT, SRC>(A, task, t, c, fp, s, sh); break;
@@ -374,10 +380,14 @@ __device__ __forceinline__ void ypass3_body(const SolveArgs& A, const TaskL& t, 
 
 template <bool FWD>
 __global__ void __launch_bounds__(kT3, 1024 / kT3) k_ypass_f3d(SolveArgs A) {
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const TaskL t = A.tY[blockIdx.x];
   const CellDev c = A.cells[t.cell];
+  if (!HOM_CHECK(A, t.kx0 >= 0 && (t.kx0 & 1) == 0 && t.kx0 < c.H && t.fixed >= 0 && t.fixed < c.n &&
+                        t.load >= 0 && t.load < A.L, (size_t)blockIdx.x))
+    return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
     case 27: ypass3_body<27, FWD>(A, t, c, fp, s); break;
@@ -543,10 +553,14 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
 }
 
 __global__ void __launch_bounds__(kT3, kMinB3) k_green_f3d(SolveArgs A) {
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4* s = reinterpret_cast<float4*>(smem_raw);
   const TaskL t = A.tC[blockIdx.x];
   const CellDev c = A.cells[t.cell];
+  if (!HOM_CHECK(A, t.kx0 >= 0 && (t.kx0 & 1) == 0 && t.kx0 < c.H && t.fixed >= 0 && t.fixed < c.n &&
+                        t.load >= 0 && t.load < A.L, (size_t)blockIdx.x))
+    return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
     case 27: green3_body<27>(A, t, c, fp, s); break;

@@ -218,6 +218,30 @@ template <> struct Radix<27> { static constexpr int m = 2, r0 = 3, r1 = 9, r2 = 
 template <> struct Radix<81> { static constexpr int m = 2, r0 = 9, r1 = 9, r2 = 1; };
 template <> struct Radix<243> { static constexpr int m = 3, r0 = 3, r1 = 9, r2 = 9; };
 
+// Radix-9 stages with HOM_TW_POW: of the eight twiddles w^q (q = 1..8) of a butterfly only w and
+// w^4 are read from the table; the others are products of at most three of them (w^2 = w w,
+// w^3 = w^2 w, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3, w^8 = w^4 w^4), so each carries at most three
+// extra roundings, in exchange for six fewer shared-memory reads per butterfly.
+#ifndef HOM_TW_POW
+#define HOM_TW_POW 0
+#endif
+__device__ __forceinline__ float2 cmul1(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 tw_scalar(const float4& t) { return make_float2(t.x, t.z); }
+__device__ __forceinline__ float2 tw_scalar(const float2& t) { return t; }
+template <typename TW>
+__device__ __forceinline__ void tw_pow9(const TW* tw, int L, int j, float2 (&w)[9]) {
+  w[1] = tw_scalar(tw[j]);
+  w[4] = tw_scalar(tw[3 * L + j]);
+  w[2] = cmul1(w[1], w[1]);
+  w[3] = cmul1(w[2], w[1]);
+  w[5] = cmul1(w[4], w[1]);
+  w[6] = cmul1(w[4], w[2]);
+  w[7] = cmul1(w[4], w[3]);
+  w[8] = cmul1(w[4], w[4]);
+}
+
 // One stage over the NP pairs of every position; thread t takes the butterflies t, t + kT, ...
 // (pair-major, so neighbouring threads take neighbouring butterflies of one pair).
 // Twiddles of a stage with span L > 1 come from its own table, tw[(q - 1) L + j] = w^(j q n / (L R))
@@ -232,12 +256,16 @@ __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
     const int j = b - blk * L;
     float4* base = s + (blk * B + j) * SP + cc;
     P2 v[R];
+    constexpr bool kPow = HOM_TW_POW && R == 9 && L > 1;
+    float2 wp[9];
+    if constexpr (kPow) tw_pow9(tw, L, j, wp);
     if (DIT) {
       v[0] = ldp(base[0]);
 #pragma unroll
       for (int q = 1; q < R; ++q) {
         P2 x = ldp(base[q * L * SP]);
-        if (L > 1) x = twmul<FWD>(x, tw[(q - 1) * L + j]);
+        if constexpr (kPow) x = twmul<FWD>(x, wp[q]);
+        else if (L > 1) x = twmul<FWD>(x, tw[(q - 1) * L + j]);
         v[q] = x;
       }
       dftp<R, FWD>(v);
@@ -251,7 +279,8 @@ __device__ __forceinline__ void stage_p(float4* s, const TW* tw) {
 #pragma unroll
       for (int p = 1; p < R; ++p) {
         P2 x = v[out_pos<R>(p)];
-        if (L > 1) x = twmul<FWD>(x, tw[(p - 1) * L + j]);
+        if constexpr (kPow) x = twmul<FWD>(x, wp[p]);
+        else if (L > 1) x = twmul<FWD>(x, tw[(p - 1) * L + j]);
         base[p * L * SP] = stp(x);
       }
     }

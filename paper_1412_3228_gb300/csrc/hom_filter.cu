@@ -449,6 +449,7 @@ using namespace hom;
 
 extern "C" int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* phases, int32_t nphase,
                                 hom_material* mat, void* stream) {
+  ::hom::NvtxRange nvtx_range_("hom_filter_build");
   if (!cells || ncells <= 0 || !phases || nphase <= 0 || !mat)
     return set_error(HOM_ERR_INVALID_ARG, "hom_filter_build: null or empty argument");
   if (mat->nphase != nphase || !mat->label || !mat->phase_c64 || !mat->phase_c32)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -13,6 +14,23 @@
 #include "hom_common.cuh"
 
 namespace hom {
+
+// ------------------------------------------------------------------ tracing
+// NVTX range for the lifetime of the object (entry points, solve phases, pass launches); costs a
+// few nanoseconds when no profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { end(); }
+  void end() {  // close early (once); the destructor closes it on every other path
+    if (open_) nvtxRangePop();
+    open_ = false;
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+
+ private:
+  bool open_ = true;
+};
 
 // ------------------------------------------------------------------ errors
 int set_error(int code, const char* fmt, ...);

@@ -36,6 +36,7 @@ int scratch_address(void** out) {
 extern "C" int hom_solve_noalloc(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E,
                                  int32_t L, const double* c0, const hom_solve_opts* opts, hom_result* out,
                                  void* stream) {
+  ::hom::NvtxRange nvtx_range_("hom_solve_noalloc");
   cudaGetLastError();  // do not report an error left behind by an unrelated earlier call
   if (!opts || !out)
     return hom::set_error(HOM_ERR_INVALID_ARG, "hom_solve_noalloc: null argument");

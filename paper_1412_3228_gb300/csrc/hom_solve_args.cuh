@@ -60,10 +60,61 @@ struct SolveArgs {
   const FastPlanDev* fplans;  // specialised passes: per-size tables (indexed by CellDev::fplan)
   const uint8_t* label8;      // specialised row pass: local phase index (255: mixed), x in transform order
   const int* cell_phases;     // specialised row pass: per-cell lists of the phases of pure voxels
+  // Eyre-Milton scheme: per-task sums of the compatibility residual |eps_hat - P eps_hat|^2 of the
+  // Green pass, the compatibility error per pair, and (c~ + c0)^-1 of every mixed voxel (packed, in
+  // the field precision, indexed like the mixed stiffness table)
+  int scheme;
+  double* partE;    // [ntaskC]
+  double* errc;     // [npairs]
+  const void* em_minv;
+  // warm start: iterate 0 is the caller's field, whose g is unknown: it is neither checked nor returned
+  int warm;
+  // residual history: the stopping quantity of iterate i of pair p at hist[p * (max_iter + 1) + i]
+  double* hist;
   // whole-solve graph: the control kernel sets the WHILE condition of the graph's iteration loop
   unsigned long long cond;    // cudaGraphConditionalHandle
   int use_cond;
+  // bounds-checked builds (-DHOM_DEBUG): the first failed check's (line, file, index) and the
+  // extents it is checked against (complex elements of the state and g arrays, real elements of
+  // the output fields, voxels)
+  unsigned int* dbg;
+  size_t n_ws, n_g, n_fld, n_lab;
 };
+
+#ifndef HOM_FILE_ID
+#define HOM_FILE_ID 0
+#endif
+
+// Records the first failed check (line, file, index) in w and returns false, so that the caller
+// skips the access: a debug build never traps and never touches memory outside an array.
+__device__ __forceinline__ bool dbg_ok(unsigned int* w, bool ok, unsigned file, unsigned line, size_t idx) {
+  if (ok) return true;
+  if (w && atomicCAS(w, 0u, line) == 0u) {
+    w[1] = file;
+    w[2] = (unsigned)(idx >> 32);
+    w[3] = (unsigned)idx;
+  }
+  return false;
+}
+
+// Debug builds fill a pass kernel's dynamic shared memory with all-ones bytes (NaN in FP32 and
+// FP64) before use, so a read of an element nobody wrote shows up as a NaN result.
+__device__ __forceinline__ void dbg_poison_smem() {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned int bytes;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(bytes));
+  uint32_t* p = reinterpret_cast<uint32_t*>(smem_raw);
+  for (unsigned i = threadIdx.x; i < bytes / 4; i += blockDim.x) p[i] = 0xFFFFFFFFu;
+  __syncthreads();
+}
+
+#ifdef HOM_DEBUG
+#define HOM_CHECK(A, cond, idx) ::hom::dbg_ok((A).dbg, (cond), HOM_FILE_ID, __LINE__, (size_t)(idx))
+#define HOM_DBG_POISON() ::hom::dbg_poison_smem()
+#else
+#define HOM_CHECK(A, cond, idx) true
+#define HOM_DBG_POISON() ((void)0)
+#endif
 
 // Kahan-compensated accumulation in the field precision: the running sum s and the negated
 // lost low part c (the represented value is s - c).

@@ -17,6 +17,7 @@
 // z-direction Green pass).  A small control kernel reduces the FP64 partial sums per
 // (cell, load), applies the stopping rule and deactivates finished load cases; later passes
 // skip inactive ones.
+#define HOM_FILE_ID 1
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,11 +72,14 @@ template <> __device__ __forceinline__ const double2* rot_table<double2>(const P
 // ------------------------------------------------------------------ row pass
 // OUT = false: one iteration's row pass (eps -> tau).  OUT = true: final fields of the returned
 // iterate (eps and sigma real, written to the output arrays), no forward transform.
-template <typename T, int DIM, bool OUT, int MAXR>
+// EM: the stored state is u = sigma + c0 : eps of the Eyre-Milton scheme; each voxel first solves
+// (c~ + c0) : eps = u, and the row sums of sigma are (tau + u) / 2.
+template <typename T, int DIM, bool OUT, int MAXR, bool EM = false>
 __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
   using V = typename Cx<T>::V;
   constexpr int NC = DIM == 2 ? 3 : 6;
   constexpr int NS = DIM == 2 ? 6 : 21;
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Plan sp;
   __shared__ int s_al[kMaxLoads], s_par[kMaxLoads], s_nal;
@@ -138,10 +142,12 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         if (it.a < nlines) {
           const int q0 = 2 * it.a, q1 = q0 + 1;
           const long long b0 = qbase[q0];
-          a[u] = static_cast<const V*>(A.eps[b0 >> 62])[(b0 & kOffMask) + (size_t)it.b * NC];
+          const size_t i0 = (b0 & kOffMask) + (size_t)it.b * NC;
+          if (HOM_CHECK(A, i0 < A.n_ws, i0)) a[u] = static_cast<const V*>(A.eps[b0 >> 62])[i0];
           if (q1 < nreal) {
             const long long b1 = qbase[q1];
-            b[u] = static_cast<const V*>(A.eps[b1 >> 62])[(b1 & kOffMask) + (size_t)it.b * NC];
+            const size_t i1 = (b1 & kOffMask) + (size_t)it.b * NC;
+            if (HOM_CHECK(A, i1 < A.n_ws, i1)) b[u] = static_cast<const V*>(A.eps[b1 >> 62])[i1];
           }
         }
         it.next();
@@ -175,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
     const int rl = it.a, x = it.b;
     const int pos = HOM_LDG(sp.perm + x);
     const size_t vox = (size_t)(t.row0 + rl) * n + x;
+    if (!HOM_CHECK(A, c.vox_off + vox < A.n_lab, c.vox_off + vox)) continue;
     const uint32_t lab = HOM_LDG(A.label + c.vox_off + vox);
     const bool mixed = (lab & HOM_MIXED_BIT) != 0;
     T C[NS];
@@ -188,6 +195,18 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
       lam = HOM_LDG(src + 1);                 // c_01 = lambda
       mu2 = HOM_LDG(src) - lam;               // c_00 - c_01 = 2 mu
     }
+    // EM, pure voxel: (c + c0)^-1 u = (u - a tr(u) I) / (2 mu + 2 mu0), a = lam_s / (2 mu_s + DIM lam_s)
+    T em_inv2 = T(0), em_a = T(0);
+    const T* em_m = nullptr;
+    if (EM) {
+      if (mixed) {
+        em_m = static_cast<const T*>(A.em_minv) + (size_t)(lab & ~HOM_MIXED_BIT) * NS;
+      } else {
+        const T ls = lam + lam0, ms2 = mu2 + mu2_0;
+        em_inv2 = T(1) / ms2;
+        em_a = ls / (ms2 + T(DIM) * ls);
+      }
+    }
     for (int la = 0; la < nal; ++la) {
       const int l = s_al[la];
       T e[NC];
@@ -197,6 +216,27 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         const int q = q0 + k;
         const V zz = s[(size_t)(q >> 1) * n + pos];
         e[k] = (q & 1) ? zz.y : zz.x;
+      }
+      if (EM) {  // e holds u: the strain of the iterate is (c~ + c0)^-1 : u
+        T u[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) u[k] = e[k];
+        if (mixed) {
+#pragma unroll
+          for (int I = 0; I < NC; ++I) {
+            T acc_i = T(0);
+#pragma unroll
+            for (int J = 0; J < NC; ++J) acc_i += HOM_LDG(em_m + packed_index(NC, I, J)) * u[J];
+            e[I] = acc_i;
+          }
+        } else {
+          T tr = T(0);
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) tr += u[k];
+          const T atr = em_a * tr;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) e[k] = em_inv2 * (u[k] - (k < DIM ? atr : T(0)));
+        }
       }
       T ee[NC];  // strain the stiffness acts on: eps, or w - S in the adjoint solve
 #pragma unroll
@@ -227,11 +267,12 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
         const size_t base = c.fld_off + (size_t)l * NC * c.nv + vox;
         T* oe = static_cast<T*>(A.out_eps);
         T* os = static_cast<T*>(A.out_sig);
+        if (HOM_CHECK(A, base + (size_t)(NC - 1) * c.nv < A.n_fld, base + (size_t)(NC - 1) * c.nv))
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          if (oe) oe[base + (size_t)k * c.nv] = e[k];
-          if (os) os[base + (size_t)k * c.nv] = sg[k];
-        }
+          for (int k = 0; k < NC; ++k) {
+            if (oe) oe[base + (size_t)k * c.nv] = e[k];
+            if (os) os[base + (size_t)k * c.nv] = sg[k];
+          }
       } else {
         T tr = T(0);
 #pragma unroll
@@ -267,8 +308,12 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
     const V a = mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));   // (Z[k] + conj Z[n-k]) / 2
     const V b = mk(T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x));   // (Z[k] - conj Z[n-k]) / 2i
     const int q0 = 2 * line;
-    tau[(qbase[q0] & kOffMask) + (size_t)kx * NC] = a;
-    if (q0 + 1 < nreal) tau[(qbase[q0 + 1] & kOffMask) + (size_t)kx * NC] = b;
+    const size_t i0 = (qbase[q0] & kOffMask) + (size_t)kx * NC;
+    if (HOM_CHECK(A, i0 < A.n_ws, i0)) tau[i0] = a;
+    if (q0 + 1 < nreal) {
+      const size_t i1 = (qbase[q0 + 1] & kOffMask) + (size_t)kx * NC;
+      if (HOM_CHECK(A, i1 < A.n_ws, i1)) tau[i1] = b;
+    }
     if (kx == 0) {
       dc_tau[q0] = a.x;
       if (q0 + 1 < nreal) dc_tau[q0 + 1] = b.x;
@@ -283,6 +328,10 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
     double acc = 0.0;
     for (int rl = 0; rl < t.nrows; ++rl) {
       const int q0 = (rl * nal + la) * NC;
+      if (EM) {  // sigma = (tau + u) / 2, sum_x u = n times the stored row mean of u
+        acc += 0.5 * ((double)dc_tau[q0 + k] + (double)n * (double)dc_eps[q0 + k]);
+        continue;
+      }
       double tr = 0.0;
 #pragma unroll
       for (int j = 0; j < DIM; ++j) tr += (double)dc_eps[q0 + j];
@@ -297,11 +346,167 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
 }
 
 // ------------------------------------------------------------------ Green pass
+// Mandel vector (nc complex entries) <-> symmetric tensor; the shear entries carry sqrt(2).
+template <typename T, int DIM, typename V>
+__device__ __forceinline__ void mandel_tensor(const V* m, V (&t)[DIM][DIM]) {
+  const T rs2 = T(0.707106781186547524400844362105);
+  if (DIM == 2) {
+    t[0][0] = m[0];
+    t[1][1] = m[1];
+    t[0][1] = t[1][0] = rs2 * m[2];
+  } else {
+    t[0][0] = m[0];
+    t[1][1] = m[1];
+    t[DIM - 1][DIM - 1] = m[2];
+    t[1][DIM - 1] = t[DIM - 1][1] = rs2 * m[3];
+    t[0][DIM - 1] = t[DIM - 1][0] = rs2 * m[4];
+    t[0][1] = t[1][0] = rs2 * m[5];
+  }
+}
+// sym(xi (x) w) in Mandel form
+template <typename T, int DIM, typename V>
+__device__ __forceinline__ void sym_xi_w(const T* xi, const V* w, V* out) {
+  const T rs2 = T(0.707106781186547524400844362105);
+  out[0] = xi[0] * w[0];
+  out[1] = xi[1] * w[1];
+  if (DIM == 2) {
+    out[2] = rs2 * (xi[0] * w[1] + xi[1] * w[0]);
+  } else {
+    out[2] = xi[2] * w[2];
+    out[3] = rs2 * (xi[1] * w[2] + xi[2] * w[1]);
+    out[4] = rs2 * (xi[0] * w[2] + xi[2] * w[0]);
+    out[5] = rs2 * (xi[0] * w[1] + xi[1] * w[0]);
+  }
+}
+// K0(xi)^-1 (s . xi) for a symmetric tensor s: the displacement-like vector whose symmetric
+// gradient sym(xi (x) w) is Gamma0(xi) : s (eq. 2)
+template <typename T, int DIM, typename V>
+__device__ __forceinline__ void kinv_div(const V (&s)[DIM][DIM], const T* xi, T inv_mq, T rq, V* w) {
+  V v[DIM];
+  V xv = mk(T(0), T(0));
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    V acc = mk(T(0), T(0));
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) acc = acc + xi[b] * s[a][b];
+    v[a] = acc;
+    xv = xv + xi[a] * acc;
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) w[a] = inv_mq * (v[a] - (rq * xi[a]) * xv);
+}
+
+// One wave vector of the Eyre-Milton Green pass (see k_green).  tv: the nc entries of tau_hat
+// (overwritten by the new u_hat, 1/N_v-scaled, for the inverse transform), uh / up: the stored u_hat
+// of the current iterate (read / overwritten with the new one).  Accumulates (weight 2 for kx > 0
+// columns other than the Nyquist column, whose conjugates are not stored) |sigma_hat . xi|^2,
+// |sigma_hat . xi|^2 / |xi|^2 and the compatibility residual's |.|^2.
+template <typename T, int DIM, typename V>
+__device__ __forceinline__ void em_point(V* const (&tv)[DIM == 2 ? 3 : 6], const V* uh, V* up, const T* xi, bool k0,
+                                         bool nyq, bool self_conj, T nvT, T inv_nv, T lam0, T mu2_0, T a0,
+                                         T inv_mu2_0, T mu0, T lpm, T inv_mu0, T ratio, const double* Eld,
+                                         Acc<T>& r2acc, Acc<T>& rnacc, Acc<T>& c2acc) {
+  constexpr int NC = DIM == 2 ? 3 : 6;
+  V th[NC], sh[NC], ce[NC], eh[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    th[k] = *tv[k];
+    const V nu = nvT * uh[k];
+    sh[k] = T(0.5) * (nu + th[k]);  // sigma_hat
+    ce[k] = T(0.5) * (nu - th[k]);  // c0 : eps_hat
+  }
+  {  // eps_hat = c0^-1 : (c0 : eps_hat)
+    V tr = mk(T(0), T(0));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) tr = tr + ce[k];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) eh[k] = inv_mu2_0 * (k < DIM ? ce[k] - a0 * tr : ce[k]);
+  }
+  const T wgt = self_conj ? T(1) : T(2);
+  V un[NC];  // new u_hat, 1/N_v-scaled
+  if (k0 || nyq) {
+    // k = 0: compatibility residual eps_hat(0) - N_v E, new state tau_hat(0) / N_v + 2 c0 : E.
+    // Nyquist bins: Gamma0 is left out: residual eps_hat, new state tau_hat / N_v.
+    T c2 = T(0);
+    T trE = T(0);
+    if (k0)
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) trE += (T)Eld[k];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const V r = k0 ? eh[k] - mk(nvT * (T)Eld[k], T(0)) : eh[k];
+      c2 += r.x * r.x + r.y * r.y;
+      un[k] = inv_nv * th[k];
+      if (k0) un[k].x += T(2) * (mu2_0 * (T)Eld[k] + (k < DIM ? lam0 * trE : T(0)));
+    }
+    c2acc.add(wgt * c2);
+  } else {
+    T q2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) q2 += xi[a] * xi[a];
+    const T inv_q2 = recip(q2);
+    const T inv_mq = inv_mu0 * inv_q2;
+    const T rq = ratio * inv_q2;
+    // equilibrium residual of the current iterate: sigma_hat . xi
+    V st[DIM][DIM];
+    mandel_tensor<T, DIM>(sh, st);
+    T r2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      V r = mk(T(0), T(0));
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) r = r + xi[b] * st[a][b];
+      r2 += r.x * r.x + r.y * r.y;
+    }
+    r2acc.add(wgt * r2);
+    rnacc.add(wgt * r2 * inv_q2);
+    // compatibility residual: eps_hat - Gamma0 : (c0 : eps_hat)
+    V ct[DIM][DIM], w[DIM], pc[NC];
+    mandel_tensor<T, DIM>(ce, ct);
+    kinv_div<T, DIM>(ct, xi, inv_mq, rq, w);
+    sym_xi_w<T, DIM>(xi, w, pc);
+    T c2 = T(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const V r = eh[k] - pc[k];
+      c2 += r.x * r.x + r.y * r.y;
+    }
+    c2acc.add(wgt * c2);
+    // new state: tau_hat - 2 c0 : Gamma0 : tau_hat, scaled by 1/N_v
+    V tt[DIM][DIM], gt[NC];
+    mandel_tensor<T, DIM>(th, tt);
+    kinv_div<T, DIM>(tt, xi, inv_mq, rq, w);
+    sym_xi_w<T, DIM>(xi, w, gt);  // Gamma0 : tau_hat
+    V tr = mk(T(0), T(0));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) tr = tr + gt[k];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      const V c0g = mu2_0 * gt[k] + (k < DIM ? lam0 * tr : mk(T(0), T(0)));
+      un[k] = inv_nv * (th[k] - T(2) * c0g);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    *tv[k] = un[k];
+    up[k] = un[k];
+  }
+  (void)mu0;
+  (void)lpm;
+}
+
 // Lines along the last axis (y in 2D, z in 3D with ky fixed) for a tile of kx and one load.
-template <typename T, int DIM, int MAXR>
+// EM (Eyre-Milton): the private state beside the lines is u_hat of the current iterate (nc
+// components per wave vector, 1/N_v-scaled) instead of g.  With tau_hat of the row pass,
+// sigma_hat = (N_v u_hat + tau_hat) / 2 and c0 : eps_hat = (N_v u_hat - tau_hat) / 2 give the
+// equilibrium residual sigma_hat . xi and the compatibility residual eps_hat - Gamma0 c0 eps_hat of
+// the current iterate; the new state is tau_hat - 2 c0 Gamma0 tau_hat (k != 0), tau_hat(0) + 2 c0 E.
+template <typename T, int DIM, int MAXR, bool EM = false>
 __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   using V = typename Cx<T>::V;
   constexpr int NC = DIM == 2 ? 3 : 6;
+  constexpr int GC = EM ? NC : DIM;  // components of the private state per wave vector
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Plan sp;
   const TaskL t = A.tC[blockIdx.x];
@@ -330,7 +535,10 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       for (int u = 0; u < U; ++u) {
         jj[u] = it.a;
         ww[u] = it.b;
-        if (it.a < n) v[u] = in[base + (size_t)it.a * rowstride + it.b];
+        if (it.a < n) {
+          const size_t i0 = base + (size_t)it.a * rowstride + it.b;
+          v[u] = HOM_CHECK(A, i0 < A.n_ws, i0) ? in[i0] : mk(T(0), T(0));
+        }
         it.next();
       }
 #pragma unroll
@@ -367,35 +575,43 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   const T rs2 = T(0.707106781186547524400844362105);
   const double* Eld = A.E + ((size_t)t.cell * A.L + t.load) * NC;
   V* gbuf = static_cast<V*>(A.g);
-  const size_t gbase = c.g_off + (size_t)t.load * c.nrows * Hp * DIM + (size_t)t.kx0 * DIM;
-  const size_t grow_stride = DIM == 2 ? (size_t)Hp * DIM : (size_t)n * Hp * DIM;
-  const size_t gfix = DIM == 3 ? (size_t)t.fixed * Hp * DIM : 0;
-  Acc<T> r2acc, rnacc;
+  const size_t gbase = c.g_off + (size_t)t.load * c.nrows * Hp * GC + (size_t)t.kx0 * GC;
+  const size_t grow_stride = DIM == 2 ? (size_t)Hp * GC : (size_t)n * Hp * GC;
+  const size_t gfix = DIM == 3 ? (size_t)t.fixed * Hp * GC : 0;
+  Acc<T> r2acc, rnacc, c2acc;
   // g of the next point is loaded while the current one is processed
   Iter2 gi(threadIdx.x, kThreads, t.d_ntk);
-  V gnext[DIM];
+  V gnext[GC];
+  // every g index of the task lies below the one of its last point
+  if (!HOM_CHECK(A, gbase + gfix + (size_t)(n - 1) * grow_stride + (size_t)(ntk * GC) <= A.n_g,
+                 gbase + gfix + (size_t)(n - 1) * grow_stride + (size_t)(ntk * GC)))
+    gi.a = n;
   if (gi.a < n) {
-    const V* gp0 = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * DIM;
+    const V* gp0 = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * GC;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) gnext[d] = gp0[d];
+    for (int d = 0; d < GC; ++d) gnext[d] = gp0[d];
   }
+  // EM constants: N_v, 2 lam0, and c0^-1 s = (s - a0 tr(s) I) / (2 mu0), a0 = lam0 / (2 mu0 + DIM lam0)
+  const T nvT = EM ? T(c.nv) : T(0);
+  const T em_a0 = EM ? cc.lam0 / (cc.mu2 + T(DIM) * cc.lam0) : T(0);
+  const T inv_mu2_0 = T(0.5) * inv_mu0;
   for (; gi.a < n;) {
     const int kk = gi.a, kxl = gi.b;
-    V gv[DIM];
+    V gv[GC];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) gv[d] = gnext[d];
+    for (int d = 0; d < GC; ++d) gv[d] = gnext[d];
     gi.next();
     if (gi.a < n) {
-      const V* gpn = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * DIM;
+      const V* gpn = gbuf + gbase + gfix + (size_t)gi.a * grow_stride + (size_t)gi.b * GC;
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) gnext[d] = gpn[d];
+      for (int d = 0; d < GC; ++d) gnext[d] = gpn[d];
     }
     const int kx = t.kx0 + kxl;
     const int pos = HOM_LDG(sp.perm + kk);
     V* tv[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) tv[k] = s + (size_t)(kxl * NC + k) * n + pos;
-    V* gp = gbuf + gbase + gfix + (size_t)kk * grow_stride + (size_t)kxl * DIM;
+    V* gp = gbuf + gbase + gfix + (size_t)kk * grow_stride + (size_t)kxl * GC;
     T xi[DIM];
     if (rotated) {  // q_j = 2n sin(pi a_j / n) prod_{m != j} cos(pi a_m / n)
       const V fx = rot_tab[kx], fl = rot_tab[kk];
@@ -420,6 +636,11 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     // even grids: a wave vector with a Nyquist component (n/2) has no conjugate partner in the
     // spectrum of a real field; its strain is set to zero and it is left out of the residual
     const bool nyq = (n & 1) == 0 && (kx == (n >> 1) || kk == (n >> 1) || (DIM == 3 && t.fixed == (n >> 1)));
+    if (EM) {
+      em_point<T, DIM>(tv, gv, gp, xi, k0, nyq, kx == 0 || 2 * kx == n, nvT, inv_nv, cc.lam0, cc.mu2, em_a0,
+                       inv_mu2_0, mu0, lpm, inv_mu0, ratio, Eld, r2acc, rnacc, c2acc);
+      continue;
+    }
     if (k0 || nyq) {
 #pragma unroll
       for (int k = 0; k < NC; ++k) *tv[k] = k0 ? mk((T)Eld[k], T(0)) : mk(T(0), T(0));
@@ -490,7 +711,16 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
       *tv[5] = (-rs2 * inv_nv) * (xi[0] * w[1] + xi[1] * w[0]);
     }
   }
-  {
+  if (EM) {
+    const Acc<T> vv[3] = {r2acc, rnacc, c2acc};
+    double tot[3];
+    block_sum<T, 3>(vv, tot);  // contains the barrier before the inverse transform
+    if (threadIdx.x == 0) {
+      A.partC[2 * (size_t)blockIdx.x] = tot[0];
+      A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
+      A.partE[blockIdx.x] = tot[2];
+    }
+  } else {
     const Acc<T> vv[2] = {r2acc, rnacc};
     double tot[2];
     block_sum<T, 2>(vv, tot);  // contains the barrier before the inverse transform
@@ -505,11 +735,11 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
   for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     const size_t ad = base + (size_t)j * rowstride + w;
-    out[ad] = srcm ? s[(size_t)w * n + j] + srcm[ad] : s[(size_t)w * n + j];
+    if (HOM_CHECK(A, ad < A.n_ws, ad)) out[ad] = srcm ? s[(size_t)w * n + j] + srcm[ad] : s[(size_t)w * n + j];
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + HOM_K_GREEN,
-              (unsigned long long)(2 * (size_t)n * nl * sizeof(V) + 2 * (size_t)n * ntk * DIM * sizeof(V)));
+              (unsigned long long)(2 * (size_t)n * nl * sizeof(V) + 2 * (size_t)n * ntk * GC * sizeof(V)));
 }
 
 // ------------------------------------------------------------------ 3D y passes
@@ -517,6 +747,7 @@ template <typename T, bool FWD, int MAXR>
 __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
   using V = typename Cx<T>::V;
   constexpr int NC = 6;
+  HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Plan sp;
   const TaskL t = A.tY[blockIdx.x];
@@ -536,7 +767,8 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
   for (Iter2 it(threadIdx.x, kThreads, t.d_nl); it.a < n; it.next()) {
     const int j = it.a, w = it.b;
     const int pos = FWD ? j : HOM_LDG(sp.perm + j);
-    s[(size_t)w * n + pos] = in[base + (size_t)j * rowstride + w];
+    const size_t i0 = base + (size_t)j * rowstride + w;
+    s[(size_t)w * n + pos] = HOM_CHECK(A, i0 < A.n_ws, i0) ? in[i0] : mk(T(0), T(0));
   }
   __syncthreads();
   if (FWD) fft_dif<true, MAXR, V, T>(s, nl, n, sp, tw, threadIdx.x, kThreads);
@@ -546,7 +778,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
     const int j = it.a, w = it.b;
     const int pos = FWD ? HOM_LDG(sp.perm + j) : j;
     const size_t ad = base + (size_t)j * rowstride + w;
-    out[ad] = srcm ? s[(size_t)w * n + pos] + srcm[ad] : s[(size_t)w * n + pos];
+    if (HOM_CHECK(A, ad < A.n_ws, ad)) out[ad] = srcm ? s[(size_t)w * n + pos] + srcm[ad] : s[(size_t)w * n + pos];
   }
   if (threadIdx.x == 0)
     atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)n * nl * sizeof(V)));
@@ -559,7 +791,7 @@ __global__ void __launch_bounds__(kThreads) k_ypass(SolveArgs A) {
 constexpr int kCtlThreads = 128;
 __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
   __shared__ bool s_last;
-  __shared__ double s_red[kCtlThreads / 32][8];
+  __shared__ double s_red[kCtlThreads / 32][9];
   __shared__ int s_cnt[kCtlThreads / 32];
   const int pair = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -567,10 +799,11 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
   if (A.active[pair]) {
     const PairDev pr = A.pairs[pair];
     const CellDev c = A.cells[pr.cell];
-    // v[0..nc): sigma sums, v[6]: residual sum, v[7]: normalised residual sum
-    double v[8];
+    // v[0..nc): sigma sums, v[6]: residual sum, v[7]: normalised residual sum, v[8]: compatibility
+    // residual sum (Eyre-Milton scheme)
+    double v[9];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = 0.0;
+    for (int k = 0; k < 9; ++k) v[k] = 0.0;
     for (int tk = pr.rtask0 + (int)threadIdx.x; tk < pr.rtask1; tk += kCtlThreads) {
       const double* p = A.partR + ((size_t)tk * A.L + pr.load) * nc;
       for (int k = 0; k < nc; ++k) v[k] += p[k];
@@ -578,17 +811,18 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
     for (int tk = pr.ctask0 + (int)threadIdx.x; tk < pr.ctask1; tk += kCtlThreads) {
       v[6] += A.partC[2 * (size_t)tk];
       v[7] += A.partC[2 * (size_t)tk + 1];
+      if (A.partE) v[8] += A.partE[tk];
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 9; ++k)
       for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (lane == 0)
 #pragma unroll
-      for (int k = 0; k < 8; ++k) s_red[wid][k] = v[k];
+      for (int k = 0; k < 9; ++k) s_red[wid][k] = v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-      double sum[8];
-      for (int k = 0; k < 8; ++k) {
+      double sum[9];
+      for (int k = 0; k < 9; ++k) {
         sum[k] = 0.0;
         for (int w = 0; w < kCtlThreads / 32; ++w) sum[k] += s_red[w][k];
       }
@@ -614,10 +848,24 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
       }
       A.err[pair] = e;
       A.errn[pair] = en;
-      const double crit = A.criterion == HOM_CRIT_E ? e : en;
+      double crit = A.criterion == HOM_CRIT_E ? e : en;
+      if (A.partE) {  // Eyre-Milton: e_c = |eps_hat - P eps_hat| / (N_v |E|) must pass too
+        const double* Ep = A.E + (size_t)pair * nc;
+        double e2 = 0.0;
+        for (int k = 0; k < nc; ++k) e2 += Ep[k] * Ep[k];
+        const double ec = sqrt(sum[8]) / ((double)c.nv * sqrt(e2));
+        A.errc[pair] = ec;
+        crit = fmax(crit, ec);
+        if (!isfinite(ec)) crit = ec;
+      }
       int st = -1;
+      const bool skip = A.warm && it == 0;  // warm start: g of the caller's field is unknown
+      if (A.hist && !A.inner && it <= A.max_iter)
+        A.hist[(size_t)pair * (A.max_iter + 1) + it] = skip ? (double)NAN : crit;
       if (A.inner) {  // defect-correction inner solve: a fixed number of iterations, no error test
         if (it >= A.kinner[pair]) st = HOM_STATUS_MAX_ITER;
+      } else if (skip) {
+        if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
       } else if (!isfinite(crit)) st = HOM_STATUS_DIVERGED;
       else if (crit < A.tol) st = HOM_STATUS_CONVERGED;
       else if (it >= A.max_iter) st = HOM_STATUS_MAX_ITER;
@@ -637,7 +885,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
           }
         }
       }
-      A.last_err[pair] = crit;
+      if (!skip) A.last_err[pair] = crit;
       if (st >= 0) {
         A.status[pair] = st;
         A.iters[pair] = it;
@@ -675,7 +923,9 @@ __global__ void __launch_bounds__(kCtlThreads) k_control(SolveArgs A, int nc) {
 // ------------------------------------------------------------------ initial state
 // eps = E: the stored x-spectrum holds E at kx = 0 of every row (see the scaling convention in
 // the row pass: stored = (1/n) x-DFT, so the unnormalised inverse gives eps back).
-template <typename T>
+// EM: the state u = 2 c0 : E instead, and its (1/N_v-scaled) spectrum at k = 0 in the private state
+// of the Green pass (zero elsewhere: the caller clears it).
+template <typename T, bool EM = false>
 __global__ void k_init(SolveArgs A, int ncells, int nc) {
   using V = typename Cx<T>::V;
   for (int cell = blockIdx.y; cell < ncells; cell += gridDim.y) {
@@ -687,8 +937,131 @@ __global__ void k_init(SolveArgs A, int ncells, int nc) {
       const long long row = r % c.nrows;
       const int l = (int)(r / c.nrows);
       const size_t ad = c.ws_off + ((size_t)l * c.nrows + row) * c.Hp * nc + comp;
-      static_cast<V*>(A.eps[0])[ad] = mk((T)A.E[((size_t)cell * A.L + l) * nc + comp], T(0));
+      const double* El = A.E + ((size_t)cell * A.L + l) * nc;
+      double v = El[comp];
+      if (EM) {
+        double trE = 0.0;
+        for (int k = 0; k < c.dim; ++k) trE += El[k];
+        v = 2.0 * (2.0 * c.mu0 * El[comp] + (comp < c.dim ? c.lam0 * trE : 0.0));
+        const size_t gi = c.g_off + (size_t)l * c.nrows * c.Hp * nc + comp;
+        if (row == 0 && HOM_CHECK(A, gi < A.n_g, gi)) static_cast<V*>(A.g)[gi] = mk((T)v, T(0));
+      }
+      if (HOM_CHECK(A, ad < A.n_ws, ad)) static_cast<V*>(A.eps[0])[ad] = mk((T)v, T(0));
     }
+  }
+}
+
+// Warm start: the caller's real strain field of every (cell, load) [nc][voxels] (field precision,
+// layout of hom_result.eps) into the stored state eps[0]: per row the half spectrum of its
+// (1/n)-scaled x-DFT, two real rows per complex line (the row pass's transform); one task = rows x
+// every load.
+template <typename T, int DIM, int MAXR>
+__global__ void __launch_bounds__(kThreads) k_state_in(SolveArgs A, const T* eps_in) {
+  using V = typename Cx<T>::V;
+  constexpr int NC = DIM == 2 ? 3 : 6;
+  HOM_DBG_POISON();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Plan sp;
+  const TaskR t = A.tR[blockIdx.x];
+  const CellDev c = A.cells[t.cell];
+  load_plan(A, c.plan, sp);
+  const int n = c.n, Hp = c.Hp, L = A.L;
+  const V* tw = stage_twiddles<V>(smem_raw, sp);
+  V* s = reinterpret_cast<V*>(smem_raw) + n;
+  const int nreal = t.nrows * L * NC;
+  const int nlines = (nreal + 1) >> 1;
+  const size_t load_stride = (size_t)c.nrows * Hp * NC;
+  // real row q = (row, load, component), as in the row pass with every load active
+  auto rowq = [&](int q, int& rl, int& l, int& comp) {
+    rl = q / (L * NC);
+    const int rem = q - rl * L * NC;
+    l = rem / NC;
+    comp = rem - l * NC;
+  };
+  for (Iter2 it(threadIdx.x, kThreads, sp.div_n); it.a < nlines; it.next()) {
+    const int line = it.a, x = it.b;
+    T v[2] = {T(0), T(0)};
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * line + h;
+      if (q >= nreal) break;
+      int rl, l, comp;
+      rowq(q, rl, l, comp);
+      const size_t vox = (size_t)(t.row0 + rl) * n + x;
+      const size_t i0 = c.fld_off + ((size_t)l * NC + comp) * c.nv + vox;
+      if (HOM_CHECK(A, i0 < A.n_fld, i0)) v[h] = eps_in[i0];
+    }
+    s[(size_t)line * n + HOM_LDG(sp.perm + x)] = mk(v[0], v[1]);
+  }
+  __syncthreads();
+  fft_dit<true, MAXR, V, T>(s, nlines, n, sp, tw, threadIdx.x, kThreads);
+  V* out = static_cast<V*>(A.eps[0]);
+  const T inv_n = T(1) / T(n);
+  for (Iter2 it(threadIdx.x, kThreads, sp.div_h); it.a < nlines; it.next()) {
+    const int line = it.a, kx = it.b;
+    const V* z = s + (size_t)line * n;
+    const V zk = z[kx];
+    const V zm = z[kx == 0 ? 0 : n - kx];
+    const V a = mk(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+    const V b = mk(T(0.5) * (zk.y + zm.y), T(0.5) * (zm.x - zk.x));
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * line + h;
+      if (q >= nreal) break;
+      int rl, l, comp;
+      rowq(q, rl, l, comp);
+      const size_t ad = c.ws_off + (size_t)l * load_stride + (size_t)(t.row0 + rl) * Hp * NC + (size_t)kx * NC + comp;
+      if (HOM_CHECK(A, ad < A.n_ws, ad)) out[ad] = inv_n * (h == 0 ? a : b);
+    }
+  }
+}
+
+// EM: (c~ + c0)^-1 of every mixed voxel of every cell (c0 of the voxel's cell), by Cholesky
+// factorisation in FP64, packed like the mixed stiffness table; blockIdx.y = cell.
+template <typename T, int NC>
+__global__ void k_em_minv(SolveArgs A, T* minv) {
+  constexpr int NS = NC * (NC + 1) / 2;
+  const CellDev c = A.cells[blockIdx.y];
+  const double* tab = A.mixed_c64;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < c.nv; v += (long long)gridDim.x * blockDim.x) {
+    const uint32_t lab = A.label[c.vox_off + v];
+    if (!(lab & HOM_MIXED_BIT)) continue;
+    const size_t m = lab & ~HOM_MIXED_BIT;
+    double a[NC][NC];
+    for (int i = 0; i < NC; ++i)
+      for (int j = i; j < NC; ++j) {
+        double x = tab[m * NS + packed_index(NC, i, j)];
+        if (i == j) x += 2.0 * c.mu0;
+        if (i < c.dim && j < c.dim) x += c.lam0;
+        a[i][j] = a[j][i] = x;
+      }
+    // a = L L^T in place (lower triangle)
+    for (int j = 0; j < NC; ++j) {
+      double d = a[j][j];
+      for (int k = 0; k < j; ++k) d -= a[j][k] * a[j][k];
+      d = sqrt(d);
+      a[j][j] = d;
+      for (int i = j + 1; i < NC; ++i) {
+        double x = a[i][j];
+        for (int k = 0; k < j; ++k) x -= a[i][k] * a[j][k];
+        a[i][j] = x / d;
+      }
+    }
+    // columns of the inverse: solve L L^T x = e_col
+    double inv[NC][NC];
+    for (int col = 0; col < NC; ++col) {
+      double y[NC];
+      for (int i = 0; i < NC; ++i) {
+        double x = i == col ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) x -= a[i][k] * y[k];
+        y[i] = x / a[i][i];
+      }
+      for (int i = NC - 1; i >= 0; --i) {
+        double x = y[i];
+        for (int k = i + 1; k < NC; ++k) x -= a[k][i] * inv[k][col];
+        inv[i][col] = x / a[i][i];
+      }
+    }
+    for (int i = 0; i < NC; ++i)
+      for (int j = i; j < NC; ++j) minv[m * NS + packed_index(NC, i, j)] = (T)(0.5 * (inv[i][j] + inv[j][i]));
   }
 }
 
@@ -831,6 +1204,12 @@ struct Layout {
 };
 
 
+long long vox_total(const Layout& lay) {
+  long long v = 0;
+  for (const CellDev& c : lay.cells) v += c.nv;
+  return v;
+}
+
 TaskL make_task(int cell, int load, int kx0, int ntk, int fixed, int nc, int dim) {
   TaskL t{};
   t.cell = cell;
@@ -851,7 +1230,7 @@ constexpr size_t kGreenBudget = (size_t)110 * 1024;
 constexpr size_t kRowBudget = (size_t)96 * 1024;
 
 int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize, int max_radix, const double* c0,
-                 bool external, Layout& lay) {
+                 bool external, Layout& lay, bool em = false) {
   const int nc = nc_of(dim);
   const size_t budget = kRowBudget;
   const size_t kMaxSmem = 227 * 1024;
@@ -940,7 +1319,7 @@ int build_layout(const hom_cell* cells, int ncells, int L, int dim, size_t vsize
     vox += c.nv;
     lay.fld_elems += (size_t)L * nc * c.nv;
     lay.ws_elems += (size_t)L * c.nrows * c.Hp * nc;
-    lay.g_elems += (size_t)L * c.nrows * c.Hp * dim;
+    lay.g_elems += (size_t)L * c.nrows * c.Hp * (em ? nc : dim);  // EM: u_hat (nc) instead of g (dim)
     // row-pass tasks: as many rows as fit in the shared-memory budget with every load active
     const size_t line_bytes = (size_t)k.n * vsize;  // one line; the twiddle table is one more
     auto row_lines = [&](int rows) { return (size_t)((rows * L * nc + 1) / 2) + 1; };
@@ -1181,6 +1560,7 @@ int refine_solve(SolveArgs& A, unsigned char* ws, int npairs, int nc, const hom_
       X.use_cond = 0;
     };
     SolveArgs A64 = A;  // FP64 checks: eps[0] = eps, eps[1] = F(eps)
+    A64.hist = nullptr;  // the history holds the FP32 iteration only
     book(A64, 0);
     A64.plans = reinterpret_cast<const Plan*>(ws + o_plans64);
     A64.eps[0] = ws + o_e64a;
@@ -1190,6 +1570,7 @@ int refine_solve(SolveArgs& A, unsigned char* ws, int npairs, int nc, const hom_
     A64.max_iter = 1 << 30;
     A64.inner = 0;
     SolveArgs Ain = A;  // inner solves: FP32 buffers of the forward solve, zero mean strain, source r
+    Ain.hist = nullptr;
     book(Ain, 1);
     Ain.E = reinterpret_cast<const double*>(ws + o_E0);
     Ain.src_mixed = ws + o_r32;
@@ -1331,9 +1712,13 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   // defect correction (FP32 with FP64 residuals) runs on the generic passes: FP32 and FP64 states
   // then share one layout
   const bool refine = std::is_same<T, float>::value && opts->refine > 0 && !cg && !adj && !ext;
+  // the Eyre-Milton scheme runs on the generic passes
+  const bool em = opts->scheme == HOM_SCHEME_EYRE_MILTON && !cg && !adj && !ext;
+  // a warm start converts the caller's real field on the generic passes' layout
+  const bool warm = opts->warm_start != 0 && !cg && !adj && !ext;
   lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC &&
-             opts->green == HOM_GREEN_CONTINUOUS && !refine;
-  int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay);
+             opts->green == HOM_GREEN_CONTINUOUS && !refine && !em && !warm;
+  int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay, em);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
   const bool want_fields = out->eps || out->sigma;
@@ -1360,6 +1745,14 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t o_dbl = take((size_t)npairs * (4 + nc) * sizeof(double));
   const size_t o_bytes = take(HOM_NKERNEL * sizeof(unsigned long long));
   const size_t o_res0 = adj ? take((size_t)npairs * 2 * sizeof(double)) : 0;
+  constexpr int NS = DIM == 2 ? 6 : 21;
+  const size_t o_partE = em ? take(lay.tC.size() * sizeof(double)) : 0;
+  const size_t o_errc = em ? take((size_t)npairs * sizeof(double)) : 0;
+  const size_t o_minv = em ? take((size_t)std::max<int64_t>(1, mat->mixed_count) * NS * sizeof(T)) : 0;
+  const size_t o_dbg = take(4 * sizeof(unsigned int));
+  const bool hist_dev = is_device_ptr(out->history);
+  const size_t hist_elems = out->history ? (size_t)npairs * ((size_t)opts->max_iter + 1) : 0;
+  const size_t o_hist = out->history && !hist_dev ? take(hist_elems * sizeof(double)) : 0;
   int cg_nchunk = 1;
   for (const CellDev& c : lay.cells)
     cg_nchunk = std::max(cg_nchunk, (c.nrows + cg_rows_per_cta(c.Hp, nc) - 1) / cg_rows_per_cta(c.Hp, nc));
@@ -1463,6 +1856,9 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_eps0, 0, lay.ws_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_g, 0, lay.g_elems * sizeof(V), st));
   HOM_CUDA_TRY(cudaMemsetAsync(ws + o_bytes, 0, HOM_NKERNEL * sizeof(unsigned long long), st));
+  HOM_CUDA_TRY(cudaMemsetAsync(ws + o_dbg, 0, 4 * sizeof(unsigned int), st));
+  if (out->history && !hist_dev)  // staged: the entries the solve does not write keep the caller's values
+    HOM_CUDA_TRY(cudaMemcpyAsync(ws + o_hist, out->history, hist_elems * sizeof(double), cudaMemcpyHostToDevice, st));
   if (refine) {
     HOM_CUDA_TRY(cudaMemsetAsync(ws + o_E0, 0, (size_t)npairs * nc * sizeof(double), st));
     std::vector<Plan> p64(lay.plans.size());
@@ -1525,6 +1921,17 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   A.out_sig = out->sigma ? (sig_dev ? out->sigma : (void*)(ws + o_stage_s)) : nullptr;
   A.src = adj ? adj->source : nullptr;
   A.res0 = adj ? reinterpret_cast<double*>(ws + o_res0) : nullptr;
+  A.scheme = em ? HOM_SCHEME_EYRE_MILTON : HOM_SCHEME_BASIC;
+  A.warm = warm ? 1 : 0;
+  A.dbg = reinterpret_cast<unsigned int*>(ws + o_dbg);
+  A.n_ws = lay.ws_elems;
+  A.n_g = lay.g_elems;
+  A.n_fld = lay.fld_elems;
+  A.n_lab = (size_t)vox_total(lay);
+  A.hist = out->history ? (hist_dev ? out->history : reinterpret_cast<double*>(ws + o_hist)) : nullptr;
+  A.partE = em ? reinterpret_cast<double*>(ws + o_partE) : nullptr;
+  A.errc = em ? reinterpret_cast<double*>(ws + o_errc) : nullptr;
+  A.em_minv = em ? ws + o_minv : nullptr;
   A.fplans = lay.fast ? reinterpret_cast<const FastPlanDev*>(ws + o_fplans) : nullptr;
   A.label8 = lay.fast ? reinterpret_cast<const uint8_t*>(ws + o_lperm) : nullptr;
   A.cell_phases = lay.fast ? reinterpret_cast<const int*>(ws + o_cphase) : nullptr;
@@ -1550,9 +1957,16 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const size_t smem_fy = lay.fast && DIM == 3 ? fast3d_smem_y(lay.fast_nmax) : 0;
   if (lay.fast && (rc = fast2d_permute_labels(A, ncells, nv_max, st)) != HOM_OK) return rc;
 
-  if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
-  if ((rc = allow_smem(k_row<T, DIM, true, MAXR>, lay.smem_row)) != HOM_OK) return rc;
-  if ((rc = allow_smem(k_green<T, DIM, MAXR>, lay.smem_green)) != HOM_OK) return rc;
+  if (warm && (rc = allow_smem(k_state_in<T, DIM, MAXR>, lay.smem_row)) != HOM_OK) return rc;
+  if (em) {
+    if ((rc = allow_smem(k_row<T, DIM, false, MAXR, true>, lay.smem_row)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_row<T, DIM, true, MAXR, true>, lay.smem_row)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_green<T, DIM, MAXR, true>, lay.smem_green)) != HOM_OK) return rc;
+  } else {
+    if ((rc = allow_smem(k_row<T, DIM, false, MAXR>, lay.smem_row)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_row<T, DIM, true, MAXR>, lay.smem_row)) != HOM_OK) return rc;
+    if ((rc = allow_smem(k_green<T, DIM, MAXR>, lay.smem_green)) != HOM_OK) return rc;
+  }
   if (DIM == 3) {
     if ((rc = allow_smem(k_ypass<T, true, MAXR>, lay.smem_y)) != HOM_OK) return rc;
     if ((rc = allow_smem(k_ypass<T, false, MAXR>, lay.smem_y)) != HOM_OK) return rc;
@@ -1560,6 +1974,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
 
   Timer tm{out->stats, st, {}};
   const unsigned nR = (unsigned)lay.tR.size(), nC = (unsigned)lay.tC.size(), nY = (unsigned)lay.tY.size();
+  NvtxRange nvtx_init_("hom_solve: initial state");
   const unsigned nCtl = (unsigned)npairs;  // one control CTA per (cell, load)
   tm.begin(HOM_K_INIT);
   k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
@@ -1567,11 +1982,20 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     fast3d_init(A, ncells, st);
   } else if (lay.fast) {
     fast2d_init(A, ncells, st);
+  } else if (warm) {
+    k_state_in<T, DIM, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A, static_cast<const T*>(out->eps));
+  } else if (em) {
+    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_errc, 0, (size_t)npairs * sizeof(double), st));
+    dim3 grid(64, (unsigned)std::min(ncells, 65535));
+    k_init<T, true><<<grid, 256, 0, st>>>(A, ncells, nc);
+    if (ncells > 65535) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "Eyre-Milton scheme: more than 65535 cells");
+    k_em_minv<T, DIM == 2 ? 3 : 6><<<dim3(64, (unsigned)ncells), 128, 0, st>>>(A, reinterpret_cast<T*>(ws + o_minv));
   } else {
     dim3 grid(64, (unsigned)std::min(ncells, 65535));
     k_init<T><<<grid, 256, 0, st>>>(A, ncells, nc);
   }
   tm.end();
+  nvtx_init_.end();
   HOM_CUDA_TRY(cudaGetLastError());
 
   const int check = opts->check_every > 0 ? opts->check_every : 8;
@@ -1579,9 +2003,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   int launched = 0;
   const dim3 cg_grid((unsigned)npairs, (unsigned)cg_nchunk);
   auto one_pass = [&]() {
+    NvtxRange r_("hom_solve: passes");
     tm.begin(HOM_K_ROW);
     if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, false, st);
     else if (lay.fast) fast2d_row(A, nR, smem_frow, st);
+    else if (em) k_row<T, DIM, false, MAXR, true><<<nR, kThreads, lay.smem_row, st>>>(A);
     else k_row<T, DIM, false, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     if (DIM == 3) {
@@ -1593,6 +2019,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     tm.begin(HOM_K_GREEN);
     if (lay.fast && DIM == 3) fast3d_green(A, nC, smem_fgreen, st);
     else if (lay.fast) fast2d_green(A, nC, smem_fgreen, st);
+    else if (em) k_green<T, DIM, MAXR, true><<<nC, kThreads, lay.smem_green, st>>>(A);
     else k_green<T, DIM, MAXR><<<nC, kThreads, lay.smem_green, st>>>(A);
     tm.end();
     if (DIM == 3) {
@@ -1628,6 +2055,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     HOM_CUDA_TRY(cudaStreamSynchronize(st));
   }
+  NvtxRange nvtx_iter_("hom_solve: iterations");
   if (opts->use_graph && !out->stats && !cg) {
     // The whole solve as one graph launch: a conditional WHILE node whose body is one iteration
     // (the passes and the control kernel); the control kernel clears the condition once no pair is
@@ -1698,6 +2126,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     HOM_CUDA_TRY(cudaMemcpyAsync(&host_nactive, A.nactive, sizeof(int), cudaMemcpyDeviceToHost, st));
     HOM_CUDA_TRY(cudaStreamSynchronize(st));
   }
+  nvtx_iter_.end();
   if (host_nactive > 0) return set_error(HOM_ERR_TIMEOUT, "iteration control did not terminate");
   if (cg) {
     // the returned iterate E + x, in the buffer the output pass reads for each pair
@@ -1706,15 +2135,18 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   }
 
   if (refine) {
+    NvtxRange r_("hom_solve: defect correction");
     rc = refine_solve<T, DIM, MAXR>(A, ws, npairs, nc, opts, lay, o_e64a, o_e64b, o_t64, o_g64, o_r32, o_int2, o_dbl2,
                                     o_mask, o_plans64, o_E0, st);
     if (rc != HOM_OK) return rc;
   }
 
   if (want_fields) {
+    NvtxRange r_("hom_solve: output fields");
     tm.begin(HOM_K_OUTPUT);
     if (lay.fast && DIM == 3) fast3d_row(A, nR, smem_frow, true, st);
     else if (lay.fast) fast2d_out(A, nR, smem_frow, st);
+    else if (em) k_row<T, DIM, true, MAXR, true><<<nR, kThreads, lay.smem_row, st>>>(A);
     else k_row<T, DIM, true, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A);
     tm.end();
     HOM_CUDA_TRY(cudaGetLastError());
@@ -1738,12 +2170,27 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   if (out->status) std::memcpy(out->status, h_st.data(), npairs * sizeof(int));
   if (out->err) std::memcpy(out->err, h_e.data(), npairs * sizeof(double));
   if (out->err_n) std::memcpy(out->err_n, h_en.data(), npairs * sizeof(double));
+  if (out->err_c) {
+    if (em) HOM_CUDA_TRY(cudaMemcpy(out->err_c, A.errc, npairs * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memset(out->err_c, 0, npairs * sizeof(double));
+  }
+  if (out->history && !hist_dev)
+    HOM_CUDA_TRY(cudaMemcpy(out->history, A.hist, hist_elems * sizeof(double), cudaMemcpyDeviceToHost));
   if (out->stats) {
     for (int k = 0; k < HOM_NKERNEL; ++k) out->stats->bytes[k] += (double)h_bytes[k];
     double vi = 0.0;
     for (int p = 0; p < npairs; ++p) vi += (double)lay.cells[lay.pairs[p].cell].nv * h_it[p];
     out->stats->voxel_iterations += vi;
   }
+#ifdef HOM_DEBUG
+  {
+    unsigned int w[4];
+    HOM_CUDA_TRY(cudaMemcpy(w, A.dbg, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w[0])
+      return set_error(HOM_ERR_BOUNDS, "bounds check failed in a solver kernel: file %u, line %u, index %llu", w[1],
+                       w[0], ((unsigned long long)w[2] << 32) | w[3]);
+  }
+#endif
   int worst = HOM_OK;
   for (int p = 0; p < npairs; ++p) {
     if (h_st[p] == HOM_STATUS_DIVERGED) worst = HOM_ERR_DIVERGED;
@@ -1804,6 +2251,21 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   if (opts->refine < 0 || opts->refine_inner < 0) return set_error(HOM_ERR_INVALID_ARG, "hom_solve: negative refine option");
   if (opts->refine > 0 && (opts->precision != HOM_FP32 || cg || adj || ext))
     return set_error(HOM_ERR_NOT_IMPL, "hom_solve: defect correction is for FP32 forward solves of hom_solve");
+  if (opts->scheme != HOM_SCHEME_BASIC && opts->scheme != HOM_SCHEME_EYRE_MILTON)
+    return set_error(HOM_ERR_INVALID_ARG, "hom_solve: unknown scheme %d", opts->scheme);
+  if (opts->warm_start) {
+    if (cg || adj || ext || opts->refine > 0 || opts->scheme != HOM_SCHEME_BASIC)
+      return set_error(HOM_ERR_NOT_IMPL, "hom_solve: a warm start is for the basic scheme of hom_solve without "
+                                         "defect correction");
+    if (!is_device_ptr(out->eps))
+      return set_error(HOM_ERR_INVALID_ARG, "hom_solve: a warm start reads the initial field from device memory "
+                                            "at out->eps");
+  }
+  if (opts->scheme == HOM_SCHEME_EYRE_MILTON &&
+      (cg || adj || ext || opts->refine > 0 || opts->green != HOM_GREEN_CONTINUOUS))
+    return set_error(HOM_ERR_NOT_IMPL,
+                     "hom_solve: the Eyre-Milton scheme is for forward solves of hom_solve with the continuous "
+                     "Green operator and no defect correction");
   if (!mat->label || !mat->phase_c32 || !mat->phase_c64)
     return set_error(HOM_ERR_INVALID_ARG, "hom_solve: material not built");
   const int dim = cells[0].dim;
@@ -1837,7 +2299,7 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   };
   hom_solve_opts o = *opts;
   if (opts->tune && opts->precision == HOM_FP32 && !ext && !adj && !cg && opts->passes == HOM_PASSES_AUTO &&
-      opts->max_radix == 0) {
+      opts->max_radix == 0 && opts->scheme == HOM_SCHEME_BASIC) {
     // Autotuner: the first solve of a batch shape times every candidate plan -- the specialised
     // passes (where every size has one) and the generic passes with register radices up to 15, 27
     // and 45 -- over a few fixed iterations of this very batch, and keeps the fastest for the shape.
@@ -1902,6 +2364,7 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
 
 extern "C" int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
                          const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream) {
+  NvtxRange nvtx_range_("hom_solve");
   return solve_entry(cells, ncells, mat, E, L, c0, opts, out, stream, nullptr);
 }
 
@@ -1917,6 +2380,7 @@ extern "C" int32_t hom_autotune_report(char* buf, int32_t len) {
 
 extern "C" int hom_solve_cg(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E,
                             int32_t L, const hom_solve_opts* opts, hom_result* out, void* stream) {
+  NvtxRange nvtx_range_("hom_solve_cg");
   if (!cells || ncells <= 0) return set_error(HOM_ERR_INVALID_ARG, "hom_solve_cg: null or empty argument");
   std::vector<double> c0(2 * (size_t)ncells, 0.5);  // validated only; the solve uses c0 = identity
   return solve_entry(cells, ncells, mat, E, L, c0.data(), opts, out, stream, nullptr, nullptr, true);
