@@ -221,9 +221,10 @@ template <> struct Radix<243> { static constexpr int m = 3, r0 = 3, r1 = 9, r2 =
 // Radix-9 stages with HOM_TW_POW: of the eight twiddles w^q (q = 1..8) of a butterfly only w and
 // w^4 are read from the table; the others are products of at most three of them (w^2 = w w,
 // w^3 = w^2 w, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3, w^8 = w^4 w^4), so each carries at most three
-// extra roundings, in exchange for six fewer shared-memory reads per butterfly.
+// extra roundings, in exchange for six fewer shared-memory reads per butterfly (HOM_TW_POW = 2:
+// seven fewer, w^4 = w^2 w^2).
 #ifndef HOM_TW_POW
-#define HOM_TW_POW 0
+#define HOM_TW_POW 1
 #endif
 __device__ __forceinline__ float2 cmul1(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -233,8 +234,9 @@ __device__ __forceinline__ float2 tw_scalar(const float2& t) { return t; }
 template <typename TW>
 __device__ __forceinline__ void tw_pow9(const TW* tw, int L, int j, float2 (&w)[9]) {
   w[1] = tw_scalar(tw[j]);
-  w[4] = tw_scalar(tw[3 * L + j]);
   w[2] = cmul1(w[1], w[1]);
+  // HOM_TW_POW = 2 reads w alone and squares w^2 into w^4 (at most three roundings still)
+  w[4] = HOM_TW_POW == 2 ? cmul1(w[2], w[2]) : tw_scalar(tw[3 * L + j]);
   w[3] = cmul1(w[2], w[1]);
   w[5] = cmul1(w[4], w[1]);
   w[6] = cmul1(w[4], w[2]);
