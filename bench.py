@@ -282,6 +282,11 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.skip_cg:
         cg = cg_comparison(hom, dev)
 
+    # ---- the Eyre-Milton scheme on the sweep itself: time to solution against the basic scheme
+    em_sweep = None
+    if rank == 0 and not args.skip_cg:
+        em_sweep = eyre_milton_sweep(hom, cells, phases, c0, fp32_err)
+
     # ---- roofline of the dominant kernel (largest share of kernel time)
     peak, peak_kind = measured_peak_hbm()
     dom = max((k for k in kstats if k in ("row", "green", "yfwd", "yinv")), key=lambda k: kstats[k]["ms"])
@@ -317,7 +322,7 @@ def run_ours(args, rank, world):
                 "fp32_value": value, "fp64_value": fp64["batched_equal_error"]["value"],
                 "fp64_tol": fp64["batched_equal_error"]["tol"], "ratio": value / fp64["batched_equal_error"]["value"],
                 "fp32_ceff_err": fp32_err, "fp64_ceff_err": fp64["batched_equal_error"]["ceff_max_rel_err"]}), "cufft_comparison": comparison, "spheres3d_243": spheres, "spheres3d_135": spheres135, "backward_135": backward,
-            "ensemble2d_256": ensemble, "cg_vs_fixed_point": cg}
+            "ensemble2d_256": ensemble, "cg_vs_fixed_point": cg, "eyre_milton_sweep": em_sweep}
     if rank == 0 and not args.skip_cpu:
         line["cpu_baseline"] = cpu_baseline(args, pool)
     if pool is not None:
@@ -618,6 +623,37 @@ def cg_comparison(hom, dev, sizes=(135, 405), tol=1e-4):
             "ceff_max_rel_diff": diff, "ceff_max_rel_diff_eyre_milton": diff_em}
 
 
+def eyre_milton_sweep(hom, cells, phases, c0, fp32_err, reps=3):
+    """The sweep's cells by the Eyre-Milton scheme (FP32, specialised passes; reference medium: the
+    geometric means of each cell's phase moduli) to max(e_n, e_c) < 1e-6, against the basic scheme
+    to e_n < 1e-6, both solves without fields, timed with CUDA events (best of `reps` after a warm-up);
+    with each one's C_eff error against the oracle's stored values."""
+    import torch
+    c0_em = np.array([H.geometric_lame(phases[c.matrix_phase:c.matrix_phase + 2], 2) for c in cells])
+    mat = hom.hom_filter_build(cells, phases)
+    st = torch.cuda.current_stream()
+    kw = dict(precision=hom.HOM_FP32, criterion=hom.HOM_CRIT_EN, tol=TOL, max_iter=MAX_ITER, fields=False)
+    out = {}
+    for name, c, extra in (("basic", c0, {}), ("eyre_milton", c0_em, {"scheme": hom.HOM_SCHEME_EYRE_MILTON})):
+        hom.hom_solve(mat, np.eye(3), c, **kw, **extra)
+        best, r = None, None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            r = hom.hom_solve(mat, np.eye(3), c, **kw, **extra)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        err, _ = ceff_errors(cells, phases, r["mean_sigma"], golden_ceff())
+        out[name] = {"solve_ms": round(best, 2), "iterations_max": int(r["iterations"].max()),
+                     "status_counts": {str(k): int(v) for k, v in zip(*np.unique(r["status"], return_counts=True))},
+                     "ceff_max_rel_err_vs_oracle": err}
+    out["speedup_time_to_solution"] = round(out["basic"]["solve_ms"] / out["eyre_milton"]["solve_ms"], 2)
+    return out
+
+
 def ensemble_2d(hom, dev, count=256):
     """The batched 2D ensemble: `count` seeded random-disk cells (4-40 disks, volume fraction
     U[0.1, 0.4], grid from {45, 75, 135, 225, 405}, contrast 10^U[-2, 2], Reuss/Voigt/2-layer),
@@ -679,7 +715,7 @@ def ensemble_2d(hom, dev, count=256):
     # the accelerated form: the Eyre-Milton scheme in FP32 (generic passes, one graph launch), the
     # reference medium of each cell the geometric means of its phase moduli
     c0_em = np.array([H.geometric_lame(phases[2 * i:2 * i + 2], 2) for i in range(count)])
-    kw3 = dict(base, use_graph=True, stall_window=50, scheme=hom.HOM_SCHEME_EYRE_MILTON)
+    kw3 = dict(base, use_graph=True, stall_window=50, tune=True, scheme=hom.HOM_SCHEME_EYRE_MILTON)
     r3, em_ms = timed(lambda: hom.hom_solve(mat, np.eye(3), c0_em, **kw3))
     C3 = hom.hom_effective_stiffness(np.eye(3), r3["mean_sigma"], 2)
     agree3 = float(max(np.abs(C[i] - C3[i]).max() / np.abs(C[i]).max() for i in range(count)))
@@ -706,8 +742,8 @@ def ensemble_2d(hom, dev, count=256):
                                                 "median": float(np.median(r3["iterations"]))},
                                  "err_n_max": float(r3["err_n"].max()), "err_c_max": float(r3["err_c"].max()),
                                  "ceff_max_rel_diff_to_production_form": agree3,
-                                 "form": "Eyre-Milton scheme (c0: geometric means of the phase moduli), FP32, generic "
-                                         "passes, one graph launch; stops at max(e_n, e_c) < tol"},
+                                 "form": "Eyre-Milton scheme (c0: geometric means of the phase moduli), FP32, one graph "
+                                         "launch, autotuned plan; stops at max(e_n, e_c) < tol"},
             "ceff_max_rel_diff_between_forms": agree,
             "stalled_cells_min_contrast": float(ctr[redo].min()) if redo else None,
             "achieved_gbs_fp32_specialised": kb}

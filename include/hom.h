@@ -188,9 +188,9 @@ typedef struct hom_solve_opts {
   int32_t refine_inner;   /* FP32 iterations per correction (0: from the FP32 iteration's */
                           /* observed contraction, enough for one correction to bring the */
                           /* error to tol / 5)                                            */
-  int32_t scheme;         /* HOM_SCHEME_BASIC (0) or HOM_SCHEME_EYRE_MILTON: generic passes,  */
-                          /* FP32 or FP64, continuous Green operator, hom_solve only, no   */
-                          /* refine                                                        */
+  int32_t scheme;         /* HOM_SCHEME_BASIC (0) or HOM_SCHEME_EYRE_MILTON: FP32 or FP64     */
+                          /* (specialised FP32 passes in 2D), continuous Green operator,    */
+                          /* hom_solve only, no refine                                      */
   int32_t warm_start;     /* 1: hom_result.eps (device, field type) holds the initial strain */
                           /* field of every load case on entry (state in / out: the returned */
                           /* fields overwrite it).  It need not be compatible: iterate 0 is */
@@ -283,8 +283,10 @@ int hom_filter_build(const hom_cell* cells, int32_t ncells, const hom_phase* pha
  *   so a load case stops only when both its equilibrium error (opts->criterion) and its
  *   compatibility error e_c (hom_result.err_c) are below opts->tol.  Any positive-definite c0
  *   converges; the geometric means of the extreme phase moduli (bulk and shear) give the fastest
- *   contraction.  Generic passes only (opts->passes is ignored), continuous Green operator; returns
- *   HOM_ERR_NOT_IMPL with opts->green = HOM_GREEN_ROTATED or opts->refine > 0. */
+ *   contraction.  FP32 2D batches of specialised sizes run the specialised passes (as the basic
+ *   scheme, unless opts->passes = HOM_PASSES_GENERIC), everything else the generic passes;
+ *   continuous Green operator; returns HOM_ERR_NOT_IMPL with opts->green = HOM_GREEN_ROTATED or
+ *   opts->refine > 0. */
 int hom_solve(const hom_cell* cells, int32_t ncells, const hom_material* mat, const double* E, int32_t L,
               const double* c0, const hom_solve_opts* opts, hom_result* out, void* stream);
 

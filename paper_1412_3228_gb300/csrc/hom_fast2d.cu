@@ -33,6 +33,7 @@
 #include "hom_plan.h"
 #include "hom_solve_args.cuh"
 #include "hom_fastfft.cuh"
+#include "hom_em.cuh"
 
 namespace hom {
 namespace {
@@ -80,7 +81,12 @@ struct RowShared {
   float dc[kMaxLoads][2][kFastRows][NP];     // [load][eps row mean, tau row sum][row][comp]
 };
 
-template <int N, bool OUT, bool SRC>
+// EM (Eyre-Milton scheme): the stored state is u = sigma + c0 : eps.  A pure voxel's tau is then
+// W u with the isotropic W = (c - c0)(c + c0)^-1 (a per-phase pair of constants in place of
+// (lam - lam0, 2 mu - 2 mu0)); a mixed group first solves eps = (c~ + c0)^-1 u per voxel and takes
+// tau = c~ : eps - c0 : eps; the output pass turns u into eps first; the row sums of sigma are
+// (tau + u) / 2.
+template <int N, bool OUT, bool SRC, bool EM = false>
 __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const TaskR& t, const CellDev& c,
                                          const FastPlanDev& fp, float4* s, RowShared& sh) {
   constexpr int H = (N + 1) / 2;
@@ -105,6 +111,7 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
   cell_const(c, cc);
   // OUT: sigma = c~ : eps, i.e. the update with a zero reference medium
   const float lam0 = OUT ? 0.f : cc.lam0, mu2_0 = OUT ? 0.f : cc.mu2;
+  const float lam_em = cc.lam0, mu2_em = cc.mu2;  // EM: the reference medium of (c + c0)^-1, also when OUT
   float4* taub = static_cast<float4*>(A.tau);
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // one-byte labels of the task's rows (transform order) and the twiddle table -> shared memory,
@@ -125,12 +132,24 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
   float4* spare = s + N * NP + kFastRows * NL / 16 + N;
 #endif
   float2* sph = reinterpret_cast<float2*>(spare + kRowSpare);
+  float2* sinv = sph + c.nph;  // EM: per local phase, (c + c0)^-1 as the pair (coefficient of tr(u) I, of u)
   cp_commit();
   // per local phase (lam - lam0, 2 mu - 2 mu0) for the pure-voxel update (visible after the next barrier)
   for (int i = threadIdx.x; i < c.nph; i += kT) {
     const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 6;
     const float lam = __ldg(pc + 1);
-    sph[i] = make_float2(lam - lam0, (__ldg(pc) - lam) - mu2_0);
+    const float mu2 = __ldg(pc) - lam;
+    sph[i] = make_float2(lam - lam0, mu2 - mu2_0);
+    if (EM) {
+      // (c + c0)^-1: volumetric eigenvalue 2 (lam + lam0) + (2 mu + 2 mu0), deviatoric 2 mu + 2 mu0
+      const double l = (double)lam, m2 = (double)mu2, l0 = c.lam0, m20 = 2.0 * c.mu0;
+      const double ms2 = m2 + m20, ks = 2.0 * (l + l0) + ms2;
+      sinv[i] = make_float2((float)((1.0 / ks - 1.0 / ms2) * 0.5), (float)(1.0 / ms2));
+      if (!OUT) {  // W = (c - c0)(c + c0)^-1: volumetric (k - k0)/(k + k0), deviatoric (2mu - 2mu0)/(2mu + 2mu0)
+        const double aK = (m2 - m20) / ms2, aJ = (2.0 * (l - l0) + (m2 - m20)) / ks;
+        sph[i] = make_float2((float)(0.5 * (aJ - aK)), (float)aK);
+      }
+    }
   }
 
   for (int la = 0; la < nal; ++la) {
@@ -243,6 +262,9 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
         lab[r] = r < nr ? (uint32_t)slab[r * NL + pos] : 0u;
         mixed |= lab[r] == kLabel8Mixed;
       }
+      uint32_t loc[kFastRows];  // the one-byte labels (EM: per-phase constants of pure voxels)
+#pragma unroll
+      for (int r = 0; r < kFastRows; ++r) loc[r] = lab[r];
       if (mixed) {  // full labels: the material's for mixed voxels, global phases for the others
         const int x = __ldg(fp.iperm + pos);
 #pragma unroll
@@ -253,6 +275,38 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
       float4 e[NP];
 #pragma unroll
       for (int k = 0; k < NP; ++k) e[k] = s[pos * NP + k];
+      if (EM && (OUT || mixed)) {
+        // e holds u: eps = (c~ + c0)^-1 u, per voxel (mixed: the per-call table; pure: in closed form)
+        float ev[NP][kFastRows];
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          float u[NP];
+#pragma unroll
+          for (int k = 0; k < NP; ++k) u[k] = r == 0 ? e[k].x : r == 1 ? e[k].z : r == 2 ? e[k].y : e[k].w;
+          if (mixed && (lab[r] & HOM_MIXED_BIT)) {
+            const float* M = static_cast<const float*>(A.em_minv) + (size_t)(lab[r] & ~HOM_MIXED_BIT) * 6;
+            ev[0][r] = __ldg(M) * u[0] + __ldg(M + 1) * u[1] + __ldg(M + 2) * u[2];
+            ev[1][r] = __ldg(M + 1) * u[0] + __ldg(M + 3) * u[1] + __ldg(M + 4) * u[2];
+            ev[2][r] = __ldg(M + 2) * u[0] + __ldg(M + 4) * u[1] + __ldg(M + 5) * u[2];
+          } else {
+            float2 d;
+            if (loc[r] == kLabel8Mixed) {  // a pure voxel whose phase is not in the cell's list (rare)
+              const float* pc = A.phase_c32 + (size_t)lab[r] * 6;
+              const float l = __ldg(pc + 1), m2 = __ldg(pc) - l;
+              const float ms2 = m2 + mu2_em, ks = 2.f * (l + lam_em) + ms2;
+              d = make_float2((1.f / ks - 1.f / ms2) * 0.5f, 1.f / ms2);
+            } else {
+              d = sinv[loc[r]];
+            }
+            const float tr = u[0] + u[1];
+            ev[0][r] = d.y * u[0] + d.x * tr;
+            ev[1][r] = d.y * u[1] + d.x * tr;
+            ev[2][r] = d.y * u[2];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) e[k] = make_float4(ev[k][0], ev[k][2], ev[k][1], ev[k][3]);
+      }
       float4 o[NP];
       if (!mixed) {
         // pure voxels: tau = (lam - lam0) tr(eps) I + (2 mu - 2 mu0) eps
@@ -403,6 +457,10 @@ __device__ __forceinline__ void row_body(const SolveArgs& A, int task, const Tas
     const int la = threadIdx.x / NP, k = threadIdx.x - la * NP;
     double acc = 0.0;
     for (int r = 0; r < nr; ++r) {
+      if (EM) {  // sigma = (tau + u) / 2
+        acc += 0.5 * ((double)s_dc[la][1][r][k] + (double)N * (double)s_dc[la][0][r][k]);
+        continue;
+      }
       const double tr = (double)s_dc[la][0][r][0] + (double)s_dc[la][0][r][1];
       const double se = (double)N * (2.0 * c.mu0 * (double)s_dc[la][0][r][k] + (k < 2 ? c.lam0 * tr : 0.0));
       acc += (double)s_dc[la][1][r][k] + se;
@@ -432,7 +490,7 @@ __device__ __forceinline__ void prefetch_row_task(const SolveArgs& A, int task) 
 
 // One CTA per task.  `ahead` is the number of CTAs resident on the device at once: task b + ahead
 // is about the one that starts when this CTA ends, so CTA b prefetches its first load into L2.
-template <bool OUT, bool SRC>
+template <bool OUT, bool SRC, bool EM = false>
 __global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A, int ntasks, int ahead) {
   HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -448,17 +506,20 @@ __global__ void __launch_bounds__(kT, HOM_ROW_TW2 ? 3 : 2) k_row_f2d(SolveArgs A
     return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 45: row_body<45, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 75: row_body<75, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 135: row_body<135, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 225: row_body<225, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 405: row_body<405, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 1215: row_body<1215, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 45: row_body<45, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 75: row_body<75, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 135: row_body<135, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 225: row_body<225, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 405: row_body<405, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 1215: row_body<1215, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
     default: break;
   }
 }
 
 // eps = E: the stored x-spectrum holds E at kx = 0 of every row (lane A of pair 0), zero elsewhere.
+// EM: u = 2 c0 : E instead, and its 1/N_v-scaled spectrum at k = 0 in the Green pass's private state
+// (pair 0, position 0; the rest is cleared by the caller).
+template <bool EM = false>
 __global__ void k_init_f2d(SolveArgs A, int ncells) {
   for (int cell = blockIdx.y; cell < ncells; cell += gridDim.y) {
     const CellDev c = A.cells[cell];
@@ -468,15 +529,66 @@ __global__ void k_init_f2d(SolveArgs A, int ncells) {
       const long long r = i / NP;
       const int y = (int)(r % c.n);
       const int l = (int)(r / c.n);
-      static_cast<float4*>(A.eps[0])[tile_index(c, c.n, l, 0, y) + k] =
-          make_float4((float)A.E[((size_t)cell * A.L + l) * NP + k], 0.f, 0.f, 0.f);
+      const double* El = A.E + ((size_t)cell * A.L + l) * NP;
+      double v = El[k];
+      if (EM) {
+        v = 2.0 * (2.0 * c.mu0 * El[k] + (k < 2 ? c.lam0 * (El[0] + El[1]) : 0.0));
+        if (y == 0) {  // u_hat(0): component k of lane A at position 0, (re, im) in float2 slot k
+          float2* ub = reinterpret_cast<float2*>(static_cast<float4*>(A.g) + (c.g_off + (size_t)l * (c.Hp / 2) * c.n * 6) / 2);
+          ub[k] = make_float2((float)v, 0.f);
+        }
+      }
+      static_cast<float4*>(A.eps[0])[tile_index(c, c.n, l, 0, y) + k] = make_float4((float)v, 0.f, 0.f, 0.f);
     }
   }
 }
 
 // ------------------------------------------------------------------ Green pass
-// tau (mixed domain) -> forward y-DFT -> Gamma0 and the residual on J (eq. 2) -> inverse y-DFT -> eps.
+// Eyre-Milton scheme: the positions of one thread, lane by lane through em_core (hom_em.cuh); the
+// private state is u_hat of the current iterate, [position][6 complex] = (kx0 components 0..2, kx0+1
+// components 0..2) as three float4, in place of g.  Returns the three compensated sums.
 template <int N>
+__device__ __forceinline__ void green_em(const SolveArgs& A, int kx0, bool hasB, const CellDev& c, const float* sx,
+                                         const FastPlanDev& fp, float4* s, float4* ub, const double* Eld,
+                                         Acc<float> (&acc)[3]) {
+  CellConst<float> cc;
+  cell_const(c, cc);
+  const float nvT = (float)c.nv, inv_nv = cc.inv_nv, lam0 = cc.lam0, mu2_0 = cc.mu2;
+  const float a0 = cc.lam0 / (cc.mu2 + 2.f * cc.lam0), inv_mu2_0 = 0.5f * cc.inv_mu0;
+  const float X[2] = {__ldg(fp.xinat + kx0), hasB ? __ldg(fp.xinat + kx0 + 1) : 0.f};
+  float* sf = reinterpret_cast<float*>(s);
+  float2* u2 = reinterpret_cast<float2*>(ub);  // [position][lane A comps 0..2, lane B comps 0..2]
+  // one (position, lane) per item: lane h reads and writes its own floats of the lane pairs
+  for (int i = threadIdx.x; i < 2 * N; i += kT) {
+    const int pos = i >> 1, h = i & 1;
+    if (h && !hasB) continue;
+    float2 th[NP], uh[NP], un[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const float* T = sf + 4 * (pos * NP + k);  // (re A, re B, im A, im B)
+      th[k] = make_float2(T[h], T[2 + h]);
+      uh[k] = u2[6 * pos + 3 * h + k];
+    }
+    const float xi[2] = {X[h], sx[pos]};
+    em_core<float, 2>(th, uh, un, xi, h == 0 && kx0 == 0 && pos == 0, false, h == 0 && kx0 == 0, nvT, inv_nv, lam0,
+                      mu2_0, a0, inv_mu2_0, cc.inv_mu0, cc.ratio, Eld, acc[0], acc[1], acc[2]);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      float* T = sf + 4 * (pos * NP + k);
+      T[h] = un[k].x;
+      T[2 + h] = un[k].y;
+      u2[6 * pos + 3 * h + k] = un[k];
+    }
+  }
+  if (!hasB)  // the missing lane B of the last pair stays zero
+    for (int i = threadIdx.x; i < N * NP; i += kT) {
+      sf[4 * i + 1] = 0.f;
+      sf[4 * i + 3] = 0.f;
+    }
+}
+
+// tau (mixed domain) -> forward y-DFT -> Gamma0 and the residual on J (eq. 2) -> inverse y-DFT -> eps.
+template <int N, bool EM = false>
 __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const TaskL& t, const CellDev& c,
                                            const FastPlanDev& fp, float4* s) {
   constexpr int H = (N + 1) / 2;
@@ -509,6 +621,26 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const T
   cp_wait_all();
   __syncthreads();
   fft_dif_p<NP, N, true>(s, tws);  // forward: bin ky at position perm(ky)
+
+  if constexpr (EM) {
+    float4* ub = static_cast<float4*>(A.g) + (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 6) / 2;
+    Acc<float> acc[3];
+    green_em<N>(A, kx0, hasB, c, sx, fp, s, ub, A.E + (size_t)cl * NP, acc);
+    double tot[3];
+    block_sum<float, 3, kT>(acc, tot);  // contains the barrier before the inverse transform
+    if (threadIdx.x == 0) {
+      A.partC[2 * (size_t)task] = tot[0];
+      A.partC[2 * (size_t)task + 1] = tot[1];
+      A.partE[task] = tot[2];
+    }
+    fft_dit_p<NP, N, false>(s, tws);  // inverse: natural order
+    for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
+    if (threadIdx.x == 0) {
+      const int ntk = hasB ? 2 : 1;
+      atomicAdd(A.bytes + HOM_K_GREEN, (unsigned long long)(4 * (size_t)N * ntk * NP * sizeof(float2)));
+    }
+    return;
+  }
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -632,7 +764,7 @@ __device__ __forceinline__ void prefetch_green_task(const SolveArgs& A, int task
   const char* tau = reinterpret_cast<const char*>(static_cast<const float4*>(A.tau) + tile_index(c, c.n, t.load, t.kx0 / 2, 0));
   const char* g = reinterpret_cast<const char*>(static_cast<const float4*>(A.g) +
                                                 (c.g_off + ((size_t)t.load * (c.Hp / 2) + (size_t)(t.kx0 / 2)) * c.n * 4) / 2);
-  const unsigned bt = (unsigned)c.n * NP * sizeof(float4), bg = (unsigned)c.n * 2 * sizeof(float4);
+  const unsigned bt = (unsigned)c.n * NP * sizeof(float4), bg = (unsigned)c.n * 2 * sizeof(float4);  // basic scheme's g
   constexpr unsigned kPiece = 4096;
   const unsigned nt = (bt + kPiece - 1) / kPiece, ng = (bg + kPiece - 1) / kPiece;
   for (unsigned i = threadIdx.x; i < nt + ng; i += kT) {
@@ -643,6 +775,7 @@ __device__ __forceinline__ void prefetch_green_task(const SolveArgs& A, int task
 }
 
 // One CTA per task; CTA b prefetches task b + ahead into L2 (see k_row_f2d).
+template <bool EM = false>
 __global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveArgs A, int ntasks, int ahead) {
   HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -656,12 +789,12 @@ __global__ void __launch_bounds__(kT, HOM_GREEN_TW2 ? 3 : 2) k_green_f2d(SolveAr
     return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 45: green_body<45>(A, task, t, c, fp, s); break;
-    case 75: green_body<75>(A, task, t, c, fp, s); break;
-    case 135: green_body<135>(A, task, t, c, fp, s); break;
-    case 225: green_body<225>(A, task, t, c, fp, s); break;
-    case 405: green_body<405>(A, task, t, c, fp, s); break;
-    case 1215: green_body<1215>(A, task, t, c, fp, s); break;
+    case 45: green_body<45, EM>(A, task, t, c, fp, s); break;
+    case 75: green_body<75, EM>(A, task, t, c, fp, s); break;
+    case 135: green_body<135, EM>(A, task, t, c, fp, s); break;
+    case 225: green_body<225, EM>(A, task, t, c, fp, s); break;
+    case 405: green_body<405, EM>(A, task, t, c, fp, s); break;
+    case 1215: green_body<1215, EM>(A, task, t, c, fp, s); break;
     default: break;
   }
 }
@@ -815,7 +948,7 @@ size_t fast2d_smem_row(int nmax, int nphase_cell) {
   const size_t labels = (size_t)kFastRows * ((nmax + 15) / 16 * 16);
   const size_t tw = HOM_ROW_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
   return (size_t)nmax * NP * sizeof(float4) + labels + tw + (size_t)kRowSpare * sizeof(float4) +
-         ((size_t)nphase_cell * 8 + 15) / 16 * 16;
+         ((size_t)nphase_cell * 16 + 15) / 16 * 16;  // two float2 per phase (the second for the Eyre-Milton scheme)
 }
 size_t fast2d_smem_green(int nmax) {
   const size_t tw = HOM_GREEN_TW2 ? ((size_t)nmax + 1) / 2 * 16 : (size_t)nmax * sizeof(float4);
@@ -831,6 +964,13 @@ int opt_in(K kernel, size_t bytes) {
 }  // namespace
 
 int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) {
+    int rc = opt_in(k_row_f2d<false, false, true>, smem);
+    if (rc != HOM_OK) return rc;
+    k_row_f2d<false, false, true><<<ntasks, kT, smem, st>>>(A, (int)ntasks,
+                                                            resident_ctas(k_row_f2d<false, false, true>, kT, smem));
+    return HOM_OK;
+  }
   if (A.src) {  // adjoint solve: the constitutive step takes the source term
     int rc = opt_in(k_row_f2d<false, true>, smem);
     if (rc != HOM_OK) return rc;
@@ -844,6 +984,13 @@ int fast2d_row(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st
 }
 
 int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) {
+    int rc = opt_in(k_row_f2d<true, false, true>, smem);
+    if (rc != HOM_OK) return rc;
+    k_row_f2d<true, false, true><<<ntasks, kT, smem, st>>>(A, (int)ntasks,
+                                                           resident_ctas(k_row_f2d<true, false, true>, kT, smem));
+    return HOM_OK;
+  }
   int rc = opt_in(k_row_f2d<true, false>, smem);
   if (rc != HOM_OK) return rc;
   k_row_f2d<true, false><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f2d<true, false>, kT, smem));
@@ -852,14 +999,21 @@ int fast2d_out(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st
 
 int fast2d_init(const SolveArgs& A, int ncells, cudaStream_t st) {
   dim3 grid(64, (unsigned)std::min(ncells, 65535));
-  k_init_f2d<<<grid, 256, 0, st>>>(A, ncells);
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) k_init_f2d<true><<<grid, 256, 0, st>>>(A, ncells);
+  else k_init_f2d<false><<<grid, 256, 0, st>>>(A, ncells);
   return HOM_OK;
 }
 
 int fast2d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
-  int rc = opt_in(k_green_f2d, smem);
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) {
+    int rc = opt_in(k_green_f2d<true>, smem);
+    if (rc != HOM_OK) return rc;
+    k_green_f2d<true><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_green_f2d<true>, kT, smem));
+    return HOM_OK;
+  }
+  int rc = opt_in(k_green_f2d<false>, smem);
   if (rc != HOM_OK) return rc;
-  k_green_f2d<<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_green_f2d, kT, smem));
+  k_green_f2d<false><<<ntasks, kT, smem, st>>>(A, (int)ntasks, resident_ctas(k_green_f2d<false>, kT, smem));
   return HOM_OK;
 }
 

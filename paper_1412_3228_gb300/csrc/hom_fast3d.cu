@@ -23,6 +23,7 @@
 #include "hom_fast2d.h"
 #include "hom_solve_args.cuh"
 #include "hom_fastfft.cuh"
+#include "hom_em.cuh"
 
 namespace hom {
 namespace {
@@ -51,7 +52,10 @@ struct RowShared3 {
 
 constexpr int kRowSpare3 = 2 * NP * kFastRows;  // float4 entries of the row pass's spare landing area
 
-template <int N, bool OUT, bool SRC>
+// EM (Eyre-Milton scheme): as in the 2D row pass, the state is u = sigma + c0 : eps; pure voxels take
+// tau = W u with a per-phase isotropic W, mixed groups and the output pass solve eps = (c~ + c0)^-1 u
+// first, and the row sums of sigma are (tau + u) / 2.
+template <int N, bool OUT, bool SRC, bool EM = false>
 __device__ __forceinline__ void row3_body(const SolveArgs& A, int task, const TaskR& t, const CellDev& c,
                                           const FastPlanDev& fp, float4* s, RowShared3& sh) {
   constexpr int H = (N + 1) / 2;
@@ -82,11 +86,23 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, int task, const Ta
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   float4* spare = s + N * SP + kFastRows * NL / 16 + (N + 1) / 2;
   float2* sph = reinterpret_cast<float2*>(spare + kRowSpare3);
+  float2* sinv = sph + c.nph;  // EM: per local phase, (c + c0)^-1 as (coefficient of tr(u) I, of u)
   cp_commit();
   for (int i = threadIdx.x; i < c.nph; i += kT3) {
     const float* pc = A.phase_c32 + (size_t)__ldg(A.cell_phases + c.ph_off + i) * 21;
     const float lam = __ldg(pc + 1);
-    sph[i] = make_float2(lam - lam0, (__ldg(pc) - lam) - mu2_0);
+    const float mu2 = __ldg(pc) - lam;
+    sph[i] = make_float2(lam - lam0, mu2 - mu2_0);
+    if (EM) {
+      // (c + c0)^-1: volumetric eigenvalue 3 (lam + lam0) + (2 mu + 2 mu0), deviatoric 2 mu + 2 mu0
+      const double l = (double)lam, m2 = (double)mu2, l0 = c.lam0, m20 = 2.0 * c.mu0;
+      const double ms2 = m2 + m20, ks = 3.0 * (l + l0) + ms2;
+      sinv[i] = make_float2((float)((1.0 / ks - 1.0 / ms2) / 3.0), (float)(1.0 / ms2));
+      if (!OUT) {  // W = (c - c0)(c + c0)^-1
+        const double aK = (m2 - m20) / ms2, aJ = (3.0 * (l - l0) + (m2 - m20)) / ks;
+        sph[i] = make_float2((float)((aJ - aK) / 3.0), (float)aK);
+      }
+    }
   }
 
   for (int la = 0; la < nal; ++la) {
@@ -150,6 +166,48 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, int task, const Ta
       float4 e[NP], o[NP];
 #pragma unroll
       for (int k = 0; k < NP; ++k) e[k] = s[pos * SP + k];
+      if (EM && (OUT || mixed)) {
+        // e holds u: eps = (c~ + c0)^-1 u per voxel (mixed: the per-call table; pure: closed form)
+        const int x = __ldg(fp.iperm + pos);
+#pragma unroll
+        for (int r = 0; r < kFastRows; ++r) {
+          float u[NP], ev[NP];
+#pragma unroll
+          for (int k = 0; k < NP; ++k) u[k] = r == 0 ? e[k].x : r == 1 ? e[k].z : r == 2 ? e[k].y : e[k].w;
+          const uint32_t L = !mixed ? 0u : lab[r] == kLabel8Mixed ? __ldg(A.label + c.vox_off + (size_t)(t.row0 + r) * N + x)
+                                                                  : (uint32_t)__ldg(A.cell_phases + c.ph_off + lab[r]);
+          if (mixed && (L & HOM_MIXED_BIT)) {
+            const float* M = static_cast<const float*>(A.em_minv) + (size_t)(L & ~HOM_MIXED_BIT) * 21;
+#pragma unroll
+            for (int I = 0; I < NP; ++I) {
+              float acc = 0.f;
+#pragma unroll
+              for (int J = 0; J < NP; ++J) acc = fmaf(__ldg(M + packed_index(NP, I, J)), u[J], acc);
+              ev[I] = acc;
+            }
+          } else {
+            float2 d;
+            if (lab[r] == kLabel8Mixed) {  // a pure voxel whose phase is not in the cell's list (rare)
+              const float* pc = A.phase_c32 + (size_t)L * 21;
+              const float l = __ldg(pc + 1), m2 = __ldg(pc) - l;
+              const float ms2 = m2 + cc.mu2, ks = 3.f * (l + cc.lam0) + ms2;
+              d = make_float2((1.f / ks - 1.f / ms2) / 3.f, 1.f / ms2);
+            } else {
+              d = sinv[lab[r]];
+            }
+            const float tr = u[0] + u[1] + u[2];
+#pragma unroll
+            for (int k = 0; k < NP; ++k) ev[k] = d.y * u[k] + (k < 3 ? d.x * tr : 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < NP; ++k) {
+            if (r == 0) e[k].x = ev[k];
+            else if (r == 1) e[k].z = ev[k];
+            else if (r == 2) e[k].y = ev[k];
+            else e[k].w = ev[k];
+          }
+        }
+      }
       if (!mixed) {
         float2 dl_lo, dl_hi, dm_lo, dm_hi;
         {
@@ -298,6 +356,10 @@ __device__ __forceinline__ void row3_body(const SolveArgs& A, int task, const Ta
     const int la = threadIdx.x / NP, k = threadIdx.x - la * NP;
     double acc = 0.0;
     for (int r = 0; r < nr; ++r) {
+      if (EM) {  // sigma = (tau + u) / 2
+        acc += 0.5 * ((double)sh.dc[la][1][r][k] + (double)N * (double)sh.dc[la][0][r][k]);
+        continue;
+      }
       const double tr = (double)sh.dc[la][0][r][0] + (double)sh.dc[la][0][r][1] + (double)sh.dc[la][0][r][2];
       const double se = (double)N * (2.0 * c.mu0 * (double)sh.dc[la][0][r][k] + (k < 3 ? c.lam0 * tr : 0.0));
       acc += (double)sh.dc[la][1][r][k] + se;
@@ -327,7 +389,7 @@ __device__ __forceinline__ void prefetch_row3_task(const SolveArgs& A, int task)
 
 // One CTA per task; CTA b prefetches the first load of task b + ahead (about the task that starts
 // when this CTA ends: `ahead` CTAs are resident at once) into L2.
-template <bool OUT, bool SRC>
+template <bool OUT, bool SRC, bool EM = false>
 __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks, int ahead) {
   HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -343,11 +405,11 @@ __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks
     return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 27: row3_body<27, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 45: row3_body<45, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 81: row3_body<81, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 135: row3_body<135, OUT, SRC>(A, task, t, c, fp, s, sh); break;
-    case 243: row3_body<243, OUT, SRC>(A, task, t, c, fp, s, sh); break;
+    case 27: row3_body<27, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 45: row3_body<45, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 81: row3_body<81, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 135: row3_body<135, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
+    case 243: row3_body<243, OUT, SRC, EM>(A, task, t, c, fp, s, sh); break;
     default: break;
   }
 }
@@ -400,7 +462,54 @@ __global__ void __launch_bounds__(kT3, 1024 / kT3) k_ypass_f3d(SolveArgs A) {
 }
 
 // ------------------------------------------------------------------ Green pass (z lines)
+// Eyre-Milton scheme: the positions of one thread, lane by lane through em_core (hom_em.cuh); the
+// private state is u_hat of the current iterate, [z position][6 components] as lane pairs (the
+// layout of the tile), in place of g.
 template <int N>
+__device__ __forceinline__ void green3_em(int kx0, bool hasB, int py, const CellDev& c, const float* sx,
+                                          const FastPlanDev& fp, float4* s, float4* ub, const double* Eld,
+                                          Acc<float> (&acc)[3]) {
+  CellConst<float> cc;
+  cell_const(c, cc);
+  const float nvT = (float)c.nv, inv_nv = cc.inv_nv, lam0 = cc.lam0, mu2_0 = cc.mu2;
+  const float a0 = cc.lam0 / (cc.mu2 + 3.f * cc.lam0), inv_mu2_0 = 0.5f * cc.inv_mu0;
+  const float X[2] = {__ldg(fp.xinat + kx0), hasB ? __ldg(fp.xinat + kx0 + 1) : 0.f}, Y = sx[py];
+  float* sf = reinterpret_cast<float*>(s);
+  float* uf = reinterpret_cast<float*>(ub);  // lane pairs, like the tile: [position][component]
+  // one (position, lane) per item: lane h reads and writes its own floats of the lane pairs
+  for (int i = threadIdx.x; i < 2 * N; i += kT3) {
+    const int pos = i >> 1, h = i & 1;
+    if (h && !hasB) continue;
+    float2 th[NP], uh[NP], un[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const float* T = sf + 4 * (pos * SP + k);
+      const float* U = uf + 4 * (NP * pos + k);
+      th[k] = make_float2(T[h], T[2 + h]);
+      uh[k] = make_float2(U[h], U[2 + h]);
+    }
+    const float xi[3] = {X[h], Y, sx[pos]};
+    em_core<float, 3>(th, uh, un, xi, h == 0 && kx0 == 0 && py == 0 && pos == 0, false, h == 0 && kx0 == 0, nvT,
+                      inv_nv, lam0, mu2_0, a0, inv_mu2_0, cc.inv_mu0, cc.ratio, Eld, acc[0], acc[1], acc[2]);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      float* T = sf + 4 * (pos * SP + k);
+      float* U = uf + 4 * (NP * pos + k);
+      T[h] = un[k].x;
+      T[2 + h] = un[k].y;
+      U[h] = un[k].x;
+      U[2 + h] = un[k].y;
+    }
+  }
+  if (!hasB)  // the missing lane B of the last pair stays zero
+    for (int i = threadIdx.x; i < N * NP; i += kT3) {
+      const int pos = i / NP, k = i - pos * NP;
+      sf[4 * (pos * SP + k) + 1] = 0.f;
+      sf[4 * (pos * SP + k) + 3] = 0.f;
+    }
+}
+
+template <int N, bool EM = false>
 __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, const CellDev& c,
                                             const FastPlanDev& fp, float4* s) {
   constexpr int H = (N + 1) / 2;
@@ -423,6 +532,30 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   cp_wait_all();
   __syncthreads();
   fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);  // forward: bin kz at position perm(kz)
+
+  if constexpr (EM) {
+    float4* ub = static_cast<float4*>(A.g) +
+                 (c.g_off + (((size_t)t.load * (c.Hp / 2) + p) * N + py) * (size_t)N * 12) / 2;
+    Acc<float> acc[3];
+    green3_em<N>(kx0, hasB, py, c, sx, fp, s, ub, A.E + (size_t)cl * NP, acc);
+    double tot[3];
+    block_sum<float, 3, kT3>(acc, tot);  // contains the barrier before the inverse transform
+    if (threadIdx.x == 0) {
+      A.partC[2 * (size_t)blockIdx.x] = tot[0];
+      A.partC[2 * (size_t)blockIdx.x + 1] = tot[1];
+      A.partE[blockIdx.x] = tot[2];
+    }
+    fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: natural z order
+    for (int i = threadIdx.x; i < N * NP; i += kT3) {
+      const int zz = i / NP, k = i - zz * NP;
+      st[b0 + zz * zs + k] = s[zz * SP + k];
+    }
+    if (threadIdx.x == 0) {
+      const int ntk = hasB ? 2 : 1;
+      atomicAdd(A.bytes + HOM_K_GREEN, (unsigned long long)(4 * (size_t)N * ntk * NP * sizeof(float2)));
+    }
+    return;
+  }
 
   CellConst<float> cc;
   cell_const(c, cc);
@@ -552,6 +685,7 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   }
 }
 
+template <bool EM = false>
 __global__ void __launch_bounds__(kT3, kMinB3) k_green_f3d(SolveArgs A) {
   HOM_DBG_POISON();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -563,16 +697,19 @@ __global__ void __launch_bounds__(kT3, kMinB3) k_green_f3d(SolveArgs A) {
     return;
   const FastPlanDev fp = A.fplans[c.fplan];
   switch (c.n) {
-    case 27: green3_body<27>(A, t, c, fp, s); break;
-    case 45: green3_body<45>(A, t, c, fp, s); break;
-    case 81: green3_body<81>(A, t, c, fp, s); break;
-    case 135: green3_body<135>(A, t, c, fp, s); break;
-    case 243: green3_body<243>(A, t, c, fp, s); break;
+    case 27: green3_body<27, EM>(A, t, c, fp, s); break;
+    case 45: green3_body<45, EM>(A, t, c, fp, s); break;
+    case 81: green3_body<81, EM>(A, t, c, fp, s); break;
+    case 135: green3_body<135, EM>(A, t, c, fp, s); break;
+    case 243: green3_body<243, EM>(A, t, c, fp, s); break;
     default: break;
   }
 }
 
 // eps = E: the stored x-spectrum holds E at kx = 0 (lane A of pair 0) of every row, zero elsewhere.
+// EM: u = 2 c0 : E instead, and its 1/N_v-scaled spectrum at k = 0 in the Green pass's private state
+// (pair 0, ky = 0, position 0, lane A; the rest is cleared by the caller).
+template <bool EM = false>
 __global__ void k_init_f3d(SolveArgs A, int ncells) {
   for (int cell = blockIdx.y; cell < ncells; cell += gridDim.y) {
     const CellDev c = A.cells[cell];
@@ -583,8 +720,15 @@ __global__ void k_init_f3d(SolveArgs A, int ncells) {
       const int row = (int)(r % c.nrows);
       const int l = (int)(r / c.nrows);
       const int z = row / c.n, y = row - z * c.n;
-      static_cast<float4*>(A.eps[0])[idx3(c, c.n, l, 0, z, y) + k] =
-          make_float4((float)A.E[((size_t)cell * A.L + l) * NP + k], 0.f, 0.f, 0.f);
+      const double* El = A.E + ((size_t)cell * A.L + l) * NP;
+      double v = El[k];
+      if (EM) {
+        v = 2.0 * (2.0 * c.mu0 * El[k] + (k < 3 ? c.lam0 * (El[0] + El[1] + El[2]) : 0.0));
+        if (row == 0)
+          static_cast<float4*>(A.g)[(c.g_off + (size_t)l * (c.Hp / 2) * c.n * c.n * 12) / 2 + k] =
+              make_float4((float)v, 0.f, 0.f, 0.f);
+      }
+      static_cast<float4*>(A.eps[0])[idx3(c, c.n, l, 0, z, y) + k] = make_float4((float)v, 0.f, 0.f, 0.f);
     }
   }
 }
@@ -608,7 +752,7 @@ bool fast3d_size(int n) {
 // Green: tile | twiddles | wave numbers
 size_t fast3d_smem_row(int nmax, int nphase_cell) {
   return (size_t)nmax * SP * sizeof(float4) + (size_t)kFastRows * ((nmax + 15) / 16 * 16) +
-         ((size_t)nmax + 1) / 2 * 16 + (size_t)kRowSpare3 * sizeof(float4) + ((size_t)nphase_cell * 8 + 15) / 16 * 16;
+         ((size_t)nmax + 1) / 2 * 16 + (size_t)kRowSpare3 * sizeof(float4) + ((size_t)nphase_cell * 16 + 15) / 16 * 16;
 }
 size_t fast3d_smem_y(int nmax) { return (size_t)nmax * SP * sizeof(float4) + ((size_t)nmax + 1) / 2 * 16; }
 size_t fast3d_smem_green(int nmax) {
@@ -617,7 +761,15 @@ size_t fast3d_smem_green(int nmax) {
 
 int fast3d_row(const SolveArgs& A, unsigned ntasks, size_t smem, bool out, cudaStream_t st) {
   int rc;
-  if (out) {
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON && out) {
+    if ((rc = opt_in3(k_row_f3d<true, false, true>, smem)) != HOM_OK) return rc;
+    k_row_f3d<true, false, true><<<ntasks, kT3, smem, st>>>(A, (int)ntasks,
+                                                            resident_ctas(k_row_f3d<true, false, true>, kT3, smem));
+  } else if (A.scheme == HOM_SCHEME_EYRE_MILTON) {
+    if ((rc = opt_in3(k_row_f3d<false, false, true>, smem)) != HOM_OK) return rc;
+    k_row_f3d<false, false, true><<<ntasks, kT3, smem, st>>>(A, (int)ntasks,
+                                                             resident_ctas(k_row_f3d<false, false, true>, kT3, smem));
+  } else if (out) {
     if ((rc = opt_in3(k_row_f3d<true, false>, smem)) != HOM_OK) return rc;
     k_row_f3d<true, false><<<ntasks, kT3, smem, st>>>(A, (int)ntasks, resident_ctas(k_row_f3d<true, false>, kT3, smem));
   } else if (A.src) {  // adjoint solve: the constitutive step takes the source term
@@ -643,15 +795,22 @@ int fast3d_ypass(const SolveArgs& A, unsigned ntasks, size_t smem, bool fwd, cud
 }
 
 int fast3d_green(const SolveArgs& A, unsigned ntasks, size_t smem, cudaStream_t st) {
-  int rc = opt_in3(k_green_f3d, smem);
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) {
+    int rc = opt_in3(k_green_f3d<true>, smem);
+    if (rc != HOM_OK) return rc;
+    k_green_f3d<true><<<ntasks, kT3, smem, st>>>(A);
+    return HOM_OK;
+  }
+  int rc = opt_in3(k_green_f3d<false>, smem);
   if (rc != HOM_OK) return rc;
-  k_green_f3d<<<ntasks, kT3, smem, st>>>(A);
+  k_green_f3d<false><<<ntasks, kT3, smem, st>>>(A);
   return HOM_OK;
 }
 
 int fast3d_init(const SolveArgs& A, int ncells, cudaStream_t st) {
   dim3 grid(64, (unsigned)std::min(ncells, 65535));
-  k_init_f3d<<<grid, 256, 0, st>>>(A, ncells);
+  if (A.scheme == HOM_SCHEME_EYRE_MILTON) k_init_f3d<true><<<grid, 256, 0, st>>>(A, ncells);
+  else k_init_f3d<false><<<grid, 256, 0, st>>>(A, ncells);
   return HOM_OK;
 }
 

@@ -30,6 +30,7 @@
 #include "hom_internal.h"
 #include "hom_plan.h"
 #include "hom_solve_args.cuh"
+#include "hom_em.cuh"
 #include "hom_fast2d.h"
 #include "hom_cg.cuh"
 
@@ -346,153 +347,25 @@ __global__ void __launch_bounds__(kThreads) k_row(SolveArgs A) {
 }
 
 // ------------------------------------------------------------------ Green pass
-// Mandel vector (nc complex entries) <-> symmetric tensor; the shear entries carry sqrt(2).
-template <typename T, int DIM, typename V>
-__device__ __forceinline__ void mandel_tensor(const V* m, V (&t)[DIM][DIM]) {
-  const T rs2 = T(0.707106781186547524400844362105);
-  if (DIM == 2) {
-    t[0][0] = m[0];
-    t[1][1] = m[1];
-    t[0][1] = t[1][0] = rs2 * m[2];
-  } else {
-    t[0][0] = m[0];
-    t[1][1] = m[1];
-    t[DIM - 1][DIM - 1] = m[2];
-    t[1][DIM - 1] = t[DIM - 1][1] = rs2 * m[3];
-    t[0][DIM - 1] = t[DIM - 1][0] = rs2 * m[4];
-    t[0][1] = t[1][0] = rs2 * m[5];
-  }
-}
-// sym(xi (x) w) in Mandel form
-template <typename T, int DIM, typename V>
-__device__ __forceinline__ void sym_xi_w(const T* xi, const V* w, V* out) {
-  const T rs2 = T(0.707106781186547524400844362105);
-  out[0] = xi[0] * w[0];
-  out[1] = xi[1] * w[1];
-  if (DIM == 2) {
-    out[2] = rs2 * (xi[0] * w[1] + xi[1] * w[0]);
-  } else {
-    out[2] = xi[2] * w[2];
-    out[3] = rs2 * (xi[1] * w[2] + xi[2] * w[1]);
-    out[4] = rs2 * (xi[0] * w[2] + xi[2] * w[0]);
-    out[5] = rs2 * (xi[0] * w[1] + xi[1] * w[0]);
-  }
-}
-// K0(xi)^-1 (s . xi) for a symmetric tensor s: the displacement-like vector whose symmetric
-// gradient sym(xi (x) w) is Gamma0(xi) : s (eq. 2)
-template <typename T, int DIM, typename V>
-__device__ __forceinline__ void kinv_div(const V (&s)[DIM][DIM], const T* xi, T inv_mq, T rq, V* w) {
-  V v[DIM];
-  V xv = mk(T(0), T(0));
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    V acc = mk(T(0), T(0));
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) acc = acc + xi[b] * s[a][b];
-    v[a] = acc;
-    xv = xv + xi[a] * acc;
-  }
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) w[a] = inv_mq * (v[a] - (rq * xi[a]) * xv);
-}
-
-// One wave vector of the Eyre-Milton Green pass (see k_green).  tv: the nc entries of tau_hat
-// (overwritten by the new u_hat, 1/N_v-scaled, for the inverse transform), uh / up: the stored u_hat
-// of the current iterate (read / overwritten with the new one).  Accumulates (weight 2 for kx > 0
-// columns other than the Nyquist column, whose conjugates are not stored) |sigma_hat . xi|^2,
-// |sigma_hat . xi|^2 / |xi|^2 and the compatibility residual's |.|^2.
+// One wave vector of the Eyre-Milton Green pass (see k_green and em_core): tv holds the nc
+// entries of tau_hat (overwritten by the new u_hat for the inverse transform), up the stored u_hat
+// of the current iterate (overwritten with the new one); uh is its value, read ahead.
 template <typename T, int DIM, typename V>
 __device__ __forceinline__ void em_point(V* const (&tv)[DIM == 2 ? 3 : 6], const V* uh, V* up, const T* xi, bool k0,
                                          bool nyq, bool self_conj, T nvT, T inv_nv, T lam0, T mu2_0, T a0,
-                                         T inv_mu2_0, T mu0, T lpm, T inv_mu0, T ratio, const double* Eld,
-                                         Acc<T>& r2acc, Acc<T>& rnacc, Acc<T>& c2acc) {
+                                         T inv_mu2_0, T inv_mu0, T ratio, const double* Eld, Acc<T>& r2acc,
+                                         Acc<T>& rnacc, Acc<T>& c2acc) {
   constexpr int NC = DIM == 2 ? 3 : 6;
-  V th[NC], sh[NC], ce[NC], eh[NC];
+  V th[NC], un[NC];
 #pragma unroll
-  for (int k = 0; k < NC; ++k) {
-    th[k] = *tv[k];
-    const V nu = nvT * uh[k];
-    sh[k] = T(0.5) * (nu + th[k]);  // sigma_hat
-    ce[k] = T(0.5) * (nu - th[k]);  // c0 : eps_hat
-  }
-  {  // eps_hat = c0^-1 : (c0 : eps_hat)
-    V tr = mk(T(0), T(0));
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) tr = tr + ce[k];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) eh[k] = inv_mu2_0 * (k < DIM ? ce[k] - a0 * tr : ce[k]);
-  }
-  const T wgt = self_conj ? T(1) : T(2);
-  V un[NC];  // new u_hat, 1/N_v-scaled
-  if (k0 || nyq) {
-    // k = 0: compatibility residual eps_hat(0) - N_v E, new state tau_hat(0) / N_v + 2 c0 : E.
-    // Nyquist bins: Gamma0 is left out: residual eps_hat, new state tau_hat / N_v.
-    T c2 = T(0);
-    T trE = T(0);
-    if (k0)
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) trE += (T)Eld[k];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const V r = k0 ? eh[k] - mk(nvT * (T)Eld[k], T(0)) : eh[k];
-      c2 += r.x * r.x + r.y * r.y;
-      un[k] = inv_nv * th[k];
-      if (k0) un[k].x += T(2) * (mu2_0 * (T)Eld[k] + (k < DIM ? lam0 * trE : T(0)));
-    }
-    c2acc.add(wgt * c2);
-  } else {
-    T q2 = T(0);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) q2 += xi[a] * xi[a];
-    const T inv_q2 = recip(q2);
-    const T inv_mq = inv_mu0 * inv_q2;
-    const T rq = ratio * inv_q2;
-    // equilibrium residual of the current iterate: sigma_hat . xi
-    V st[DIM][DIM];
-    mandel_tensor<T, DIM>(sh, st);
-    T r2 = T(0);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      V r = mk(T(0), T(0));
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) r = r + xi[b] * st[a][b];
-      r2 += r.x * r.x + r.y * r.y;
-    }
-    r2acc.add(wgt * r2);
-    rnacc.add(wgt * r2 * inv_q2);
-    // compatibility residual: eps_hat - Gamma0 : (c0 : eps_hat)
-    V ct[DIM][DIM], w[DIM], pc[NC];
-    mandel_tensor<T, DIM>(ce, ct);
-    kinv_div<T, DIM>(ct, xi, inv_mq, rq, w);
-    sym_xi_w<T, DIM>(xi, w, pc);
-    T c2 = T(0);
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const V r = eh[k] - pc[k];
-      c2 += r.x * r.x + r.y * r.y;
-    }
-    c2acc.add(wgt * c2);
-    // new state: tau_hat - 2 c0 : Gamma0 : tau_hat, scaled by 1/N_v
-    V tt[DIM][DIM], gt[NC];
-    mandel_tensor<T, DIM>(th, tt);
-    kinv_div<T, DIM>(tt, xi, inv_mq, rq, w);
-    sym_xi_w<T, DIM>(xi, w, gt);  // Gamma0 : tau_hat
-    V tr = mk(T(0), T(0));
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) tr = tr + gt[k];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const V c0g = mu2_0 * gt[k] + (k < DIM ? lam0 * tr : mk(T(0), T(0)));
-      un[k] = inv_nv * (th[k] - T(2) * c0g);
-    }
-  }
+  for (int k = 0; k < NC; ++k) th[k] = *tv[k];
+  em_core<T, DIM>(th, uh, un, xi, k0, nyq, self_conj, nvT, inv_nv, lam0, mu2_0, a0, inv_mu2_0, inv_mu0, ratio, Eld,
+                  r2acc, rnacc, c2acc);
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     *tv[k] = un[k];
     up[k] = un[k];
   }
-  (void)mu0;
-  (void)lpm;
 }
 
 // Lines along the last axis (y in 2D, z in 3D with ky fixed) for a tile of kx and one load.
@@ -638,7 +511,7 @@ __global__ void __launch_bounds__(kThreads) k_green(SolveArgs A) {
     const bool nyq = (n & 1) == 0 && (kx == (n >> 1) || kk == (n >> 1) || (DIM == 3 && t.fixed == (n >> 1)));
     if (EM) {
       em_point<T, DIM>(tv, gv, gp, xi, k0, nyq, kx == 0 || 2 * kx == n, nvT, inv_nv, cc.lam0, cc.mu2, em_a0,
-                       inv_mu2_0, mu0, lpm, inv_mu0, ratio, Eld, r2acc, rnacc, c2acc);
+                       inv_mu2_0, inv_mu0, ratio, Eld, r2acc, rnacc, c2acc);
       continue;
     }
     if (k0 || nyq) {
@@ -1717,7 +1590,7 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   // a warm start converts the caller's real field on the generic passes' layout
   const bool warm = opts->warm_start != 0 && !cg && !adj && !ext;
   lay.fast = std::is_same<T, float>::value && !cg && opts->passes != HOM_PASSES_GENERIC &&
-             opts->green == HOM_GREEN_CONTINUOUS && !refine && !em && !warm;
+             opts->green == HOM_GREEN_CONTINUOUS && !refine && !warm;
   int rc = build_layout(cells, ncells, L, DIM, sizeof(V), MAXR, c0, ext != nullptr, lay, em);
   if (rc != HOM_OK) return rc;
   const int npairs = ncells * L;
@@ -1978,6 +1851,11 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   const unsigned nCtl = (unsigned)npairs;  // one control CTA per (cell, load)
   tm.begin(HOM_K_INIT);
   k_init_pairs<<<(npairs + 255) / 256, 256, 0, st>>>(A);
+  if (em) {
+    if (ncells > 65535) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "Eyre-Milton scheme: more than 65535 cells");
+    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_errc, 0, (size_t)npairs * sizeof(double), st));
+    k_em_minv<T, DIM == 2 ? 3 : 6><<<dim3(64, (unsigned)ncells), 128, 0, st>>>(A, reinterpret_cast<T*>(ws + o_minv));
+  }
   if (lay.fast && DIM == 3) {
     fast3d_init(A, ncells, st);
   } else if (lay.fast) {
@@ -1985,11 +1863,8 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
   } else if (warm) {
     k_state_in<T, DIM, MAXR><<<nR, kThreads, lay.smem_row, st>>>(A, static_cast<const T*>(out->eps));
   } else if (em) {
-    HOM_CUDA_TRY(cudaMemsetAsync(ws + o_errc, 0, (size_t)npairs * sizeof(double), st));
     dim3 grid(64, (unsigned)std::min(ncells, 65535));
     k_init<T, true><<<grid, 256, 0, st>>>(A, ncells, nc);
-    if (ncells > 65535) return set_error(HOM_ERR_UNSUPPORTED_SIZE, "Eyre-Milton scheme: more than 65535 cells");
-    k_em_minv<T, DIM == 2 ? 3 : 6><<<dim3(64, (unsigned)ncells), 128, 0, st>>>(A, reinterpret_cast<T*>(ws + o_minv));
   } else {
     dim3 grid(64, (unsigned)std::min(ncells, 65535));
     k_init<T><<<grid, 256, 0, st>>>(A, ncells, nc);
@@ -2299,7 +2174,7 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
   };
   hom_solve_opts o = *opts;
   if (opts->tune && opts->precision == HOM_FP32 && !ext && !adj && !cg && opts->passes == HOM_PASSES_AUTO &&
-      opts->max_radix == 0 && opts->scheme == HOM_SCHEME_BASIC) {
+      opts->max_radix == 0) {
     // Autotuner: the first solve of a batch shape times every candidate plan -- the specialised
     // passes (where every size has one) and the generic passes with register radices up to 15, 27
     // and 45 -- over a few fixed iterations of this very batch, and keeps the fastest for the shape.
@@ -2309,7 +2184,7 @@ int solve_entry(const hom_cell* cells, int ncells, const hom_material* mat, cons
     for (int c = 0; c < ncells; ++c) ns.push_back(cells[c].n);
     std::sort(ns.begin(), ns.end());
     std::string key = "dev" + std::to_string(dev) + " dim" + std::to_string(dim) + " L" + std::to_string(L) +
-                      " green" + std::to_string(opts->green) + " n";
+                      " green" + std::to_string(opts->green) + " scheme" + std::to_string(opts->scheme) + " n";
     for (size_t i = 0; i < ns.size(); ++i) {
       size_t j = i;
       while (j + 1 < ns.size() && ns[j + 1] == ns[i]) ++j;

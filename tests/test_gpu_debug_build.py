@@ -48,6 +48,10 @@ def run():
     solve("generic3d_fp64_even", [sph(10)], 3, precision=hom.HOM_FP64, tol=1e-9)
     solve("em_fp64", [disk(21)], 2, precision=hom.HOM_FP64, tol=1e-9, scheme=hom.HOM_SCHEME_EYRE_MILTON,
           c0=[H.geometric_lame(ph, 2)])
+    solve("em_fp32_fast2d", [disk(45), disk(135, H.RULE_VOIGT)], 2, precision=hom.HOM_FP32, tol=1e-6,
+          scheme=hom.HOM_SCHEME_EYRE_MILTON, c0=[H.geometric_lame(ph, 2)] * 2)
+    solve("em_fp32_fast3d", [sph(27)], 3, precision=hom.HOM_FP32, tol=1e-6, scheme=hom.HOM_SCHEME_EYRE_MILTON,
+          c0=[H.geometric_lame(ph, 3)])
     rng = np.random.default_rng(3)
     eps0 = torch.tensor(rng.standard_normal(3 * 3 * 21 * 21), dtype=torch.float64, device="cuda")
     solve("warm_fp64", [disk(21)], 2, precision=hom.HOM_FP64, tol=1e-9, eps0=eps0)

@@ -141,3 +141,69 @@ def test_em_rejects_unsupported_combinations():
             hom.hom_solve(mat, np.eye(3), [H.geometric_lame(phases, 2)], scheme=hom.HOM_SCHEME_EYRE_MILTON,
                           allow_not_converged=True, **kw)
         assert ei.value.code == 9  # HOM_ERR_NOT_IMPL
+
+
+def test_em_fp32_specialised_passes_match_generic_and_oracle():
+    """The specialised FP32 2D passes run the scheme too (a per-phase W for pure voxels, the
+    (c~ + c0)^-1 table for mixed ones, u_hat beside the Green tile): a batch of specialised sizes at
+    contrasts 100 and 0.01 gives the generic passes' iterate (iteration counts within 2, C_eff and
+    fields within FP32 rounding) and the oracle's C_eff."""
+    cells = [H.centred_disk_cell(45, rule=H.RULE_TWO_LAYER), H.centred_disk_cell(135, rule=H.RULE_VOIGT),
+             H.centred_disk_cell(75, rule=H.RULE_REUSS)]
+    contrasts = [100.0, 0.01, 10.0]
+    phases, cs = [], []
+    for cell, k in zip(cells, contrasts):
+        cs.append(H.remap_phases(cell, len(phases)))
+        phases.extend(H.two_phases(k))
+    c0 = [H.geometric_lame(phases[2 * i:2 * i + 2], 2) for i in range(len(cs))]
+    E = np.eye(3)
+    mat = hom.hom_filter_build(cs, phases)
+    fast = _em(mat, E, c0, precision=hom.HOM_FP32, tol=1e-6, max_iter=2000)
+    gen = _em(mat, E, c0, precision=hom.HOM_FP32, tol=1e-6, max_iter=2000, passes=hom.HOM_PASSES_GENERIC)
+    assert (fast["status"] == 0).all() and (gen["status"] == 0).all()
+    # FP32 paths that round differently: near the floor (contrast 100) the counts may differ a little
+    it_f, it_g = fast["iterations"].astype(int), gen["iterations"].astype(int)
+    assert (np.abs(it_f - it_g) <= np.maximum(2, 0.15 * it_g)).all(), (it_f, it_g)
+    Cf = hom.hom_effective_stiffness(E, fast["mean_sigma"], 2)
+    Cg = hom.hom_effective_stiffness(E, gen["mean_sigma"], 2)
+    for i, cell in enumerate(cs):
+        assert _rel(Cf[i], Cg[i]) < 2e-6
+        ph = phases[2 * i:2 * i + 2]
+        fb = O.filter_build(H.remap_phases(cell, -2 * i), ph)
+        ref = O.solve_em(fb["ctilde"], 2, cell.n, c0[i][0], c0[i][1], E, tol=1e-10, max_iter=3000)
+        assert _rel(Cf[i], O.effective_stiffness(ref["mean_sigma"], E)) < 2e-5
+    for key in ("eps", "sigma"):
+        for a, b in zip(cell_fields(fast, cs, 2, key), cell_fields(gen, cs, 2, key)):
+            assert np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)) < 2e-5
+
+
+def test_em_fp32_specialised_3d_passes_match_generic_and_oracle():
+    """The specialised FP32 3D passes (27^3 and 45^3 sphere cells, contrasts 100 and 0.1): the
+    generic passes' iterate and the oracle's C_eff."""
+    cells = [H.rsa_spheres_cell(27, seed=27, vf=0.2, rmin=0.1, rmax=0.15, subgrid=4, gap_voxels=1.0),
+             H.rsa_spheres_cell(45, seed=45, vf=0.25, rmin=0.1, rmax=0.15, rule=H.RULE_VOIGT, subgrid=2,
+                                gap_voxels=1.0)]
+    contrasts = [100.0, 0.1]
+    phases, cs = [], []
+    for cell, k in zip(cells, contrasts):
+        cs.append(H.remap_phases(cell, len(phases)))
+        phases.extend(H.two_phases(k))
+    c0 = [H.geometric_lame(phases[2 * i:2 * i + 2], 3) for i in range(len(cs))]
+    E = np.eye(6)
+    mat = hom.hom_filter_build(cs, phases)
+    fast = _em(mat, E, c0, precision=hom.HOM_FP32, tol=1e-6, max_iter=2000)
+    gen = _em(mat, E, c0, precision=hom.HOM_FP32, tol=1e-6, max_iter=2000, passes=hom.HOM_PASSES_GENERIC)
+    assert (fast["status"] == 0).all() and (gen["status"] == 0).all()
+    it_f, it_g = fast["iterations"].astype(int), gen["iterations"].astype(int)
+    assert (np.abs(it_f - it_g) <= np.maximum(2, 0.15 * it_g)).all(), (it_f, it_g)
+    Cf = hom.hom_effective_stiffness(E, fast["mean_sigma"], 3)
+    Cg = hom.hom_effective_stiffness(E, gen["mean_sigma"], 3)
+    for i, cell in enumerate(cs):
+        assert _rel(Cf[i], Cg[i]) < 2e-6
+    # the oracle on the 27^3 cell (the 45^3 one is checked through the generic passes)
+    fb = O.filter_build(cells[0], phases[0:2])
+    ref = O.solve_em(fb["ctilde"], 3, 27, c0[0][0], c0[0][1], E, tol=1e-7, max_iter=3000)
+    assert _rel(Cf[0], O.effective_stiffness(ref["mean_sigma"], E)) < 2e-5
+    for key in ("eps", "sigma"):
+        for a, b in zip(cell_fields(fast, cs, 3, key), cell_fields(gen, cs, 3, key)):
+            assert np.sqrt(np.mean((a - b) ** 2)) / np.sqrt(np.mean(b ** 2)) < 2e-5
