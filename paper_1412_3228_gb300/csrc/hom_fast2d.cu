@@ -50,6 +50,9 @@ namespace {
 #ifndef HOM_ROW_PREFETCH
 #define HOM_ROW_PREFETCH 0  // row pass L2 prefetch: 1 = the next load, 2 = the next task (bit mask)
 #endif
+#ifndef HOM_GREEN_BULK
+#define HOM_GREEN_BULK 1  // Green pass: its contiguous tile in and out by one bulk copy each (TMA unit)
+#endif
 #ifndef HOM_GREEN_PREFETCH
 #define HOM_GREEN_PREFETCH 0  // Green pass: L2 prefetch of the task that starts next
 #endif
@@ -587,6 +590,22 @@ __device__ __forceinline__ void green_em(const SolveArgs& A, int kx0, bool hasB,
     }
 }
 
+// The finished tile (natural order after the inverse transform) -> the next eps buffer.
+template <int N>
+__device__ __forceinline__ void green_store(const SolveArgs& A, const float4* s, float4* out) {
+#if HOM_GREEN_BULK
+  fence_proxy_async();  // this thread's tile writes, visible to the bulk copy
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bulk_store(out, s, (unsigned)(N * NP * sizeof(float4)));
+    bulk_store_wait_read();  // the CTA keeps its shared memory until the copy has read it
+  }
+#else
+  for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
+#endif
+  (void)A;
+}
+
 // tau (mixed domain) -> forward y-DFT -> Gamma0 and the residual on J (eq. 2) -> inverse y-DFT -> eps.
 template <int N, bool EM = false>
 __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const TaskL& t, const CellDev& c,
@@ -615,10 +634,28 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const T
   float* sx = reinterpret_cast<float*>(tws + N);
   for (int i = threadIdx.x; i < N; i += kT) cp16(tws + i, fp.tw4 + i);
 #endif
+#if HOM_GREEN_BULK
+  // the tile (N NP float4, contiguous in HBM and in shared memory) by one bulk copy
+  __shared__ __align__(8) unsigned long long tile_bar;
+  fence_proxy_async();  // earlier generic writes to this shared memory are ordered before the copy's
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_init(&tile_bar, 1);
+    bulk_load(s, in, (unsigned)(N * NP * sizeof(float4)), &tile_bar);
+  }
+#else
   for (int i = threadIdx.x; i < N * NP; i += kT) cp16(s + i, in + i);
+#endif
   for (int i = threadIdx.x; i < (N + 3) / 4; i += kT) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
   cp_wait_all();
+#if HOM_GREEN_BULK
+  __syncthreads();  // the barrier's initialisation is visible before anyone waits on it
+  // bounded wait (a copy of 60 KB lands in microseconds); running out is recorded, never a hang
+  if (!mbar_wait(&tile_bar, 0, 1 << 22) && A.dbg) atomicCAS(A.dbg, 0u, 0xFFFFFFFFu);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(&tile_bar);
+#endif
   __syncthreads();
   fft_dif_p<NP, N, true>(s, tws);  // forward: bin ky at position perm(ky)
 
@@ -634,7 +671,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const T
       A.partE[task] = tot[2];
     }
     fft_dit_p<NP, N, false>(s, tws);  // inverse: natural order
-    for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
+    green_store<N>(A, s, out);
     if (threadIdx.x == 0) {
       const int ntk = hasB ? 2 : 1;
       atomicAdd(A.bytes + HOM_K_GREEN, (unsigned long long)(4 * (size_t)N * ntk * NP * sizeof(float2)));
@@ -748,7 +785,7 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const T
     }
   }
   fft_dit_p<NP, N, false>(s, tws);  // inverse: natural order
-  for (int f = threadIdx.x; f < N * NP; f += kT) out[f] = s[f];
+  green_store<N>(A, s, out);
   if (threadIdx.x == 0) {
     const int ntk = hasB ? 2 : 1;
     atomicAdd(A.bytes + HOM_K_GREEN,

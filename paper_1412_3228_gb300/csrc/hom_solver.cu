@@ -2057,15 +2057,15 @@ int run_solve(const hom_cell* cells, int ncells, const hom_material* mat, const 
     for (int p = 0; p < npairs; ++p) vi += (double)lay.cells[lay.pairs[p].cell].nv * h_it[p];
     out->stats->voxel_iterations += vi;
   }
-#ifdef HOM_DEBUG
   {
+    // the error word: a bounded wait that ran out (every build), a failed bounds check (debug builds)
     unsigned int w[4];
     HOM_CUDA_TRY(cudaMemcpy(w, A.dbg, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w[0] == 0xFFFFFFFFu) return set_error(HOM_ERR_TIMEOUT, "a shared-memory bulk copy did not complete in time");
     if (w[0])
       return set_error(HOM_ERR_BOUNDS, "bounds check failed in a solver kernel: file %u, line %u, index %llu", w[1],
                        w[0], ((unsigned long long)w[2] << 32) | w[3]);
   }
-#endif
   int worst = HOM_OK;
   for (int p = 0; p < npairs; ++p) {
     if (h_st[p] == HOM_STATUS_DIVERGED) worst = HOM_ERR_DIVERGED;
