@@ -414,6 +414,56 @@ __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks
   }
 }
 
+#ifndef HOM_3D_BULK
+#define HOM_3D_BULK 1  // y passes: the tile in and out by bulk copies of one position each
+#endif
+#ifndef HOM_3D_GREEN_BULK
+#define HOM_3D_GREEN_BULK 0  // the same for the Green pass, whose positions are a z plane apart in HBM
+#endif
+
+// Bulk copies of the N positions of a tile (NP float4 each, contiguous in HBM at stride gs float4,
+// at stride SP in shared memory) in or out; threads issue one position each in turn.  `load`
+// waits (bounded) for all of them on `bar`, initialised here; running out is recorded in A.dbg.
+template <int N>
+__device__ __forceinline__ void tile_bulk_load(const SolveArgs& A, float4* s, const float4* g, size_t gs,
+                                               unsigned long long* bar) {
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((unsigned)(N * NP * sizeof(float4)))
+                 : "memory");
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < N; p += kT3)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(s + (size_t)p * SP)),
+                 "l"(g + (size_t)p * gs), "r"((unsigned)(NP * sizeof(float4))), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tile_bulk_wait(const SolveArgs& A, unsigned long long* bar) {
+  if (!mbar_wait(bar, 0, 1 << 22) && A.dbg) atomicCAS(A.dbg, 0u, 0xFFFFFFFFu);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(bar);
+}
+template <int N>
+__device__ __forceinline__ void tile_bulk_store(float4* g, size_t gs, const float4* s) {
+  fence_proxy_async();
+  __syncthreads();
+  bool any = false;
+  for (int p = threadIdx.x; p < N; p += kT3) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g + (size_t)p * gs),
+                 "r"(smem_u32(s + (size_t)p * SP)), "r"((unsigned)(NP * sizeof(float4)))
+                 : "memory");
+    any = true;
+  }
+  if (any) {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    bulk_store_wait_read();
+  }
+}
+
 // ------------------------------------------------------------------ y passes
 // FWD: tau -> forward y-DFT -> tau (digit-reversed y positions).  Inverse: tau -> inverse y-DFT
 // -> the next eps buffer (natural order).  One contiguous tile per task: [y][component].
@@ -426,14 +476,26 @@ __device__ __forceinline__ void ypass3_body(const SolveArgs& A, const TaskL& t, 
   const float4* in = static_cast<const float4*>(A.tau) + tb;
   float4* out = static_cast<float4*>(FWD ? A.tau : A.eps[(it + 1) & 1]) + tb;
   float2* tws = reinterpret_cast<float2*>(s + N * SP);
+#if HOM_3D_BULK
+  __shared__ __align__(8) unsigned long long ybar;
+  tile_bulk_load<N>(A, s, in, NP, &ybar);
+#else
   for (int i = threadIdx.x; i < N * NP; i += kT3) cp16(s + (i / NP) * SP + i % NP, in + i);
+#endif
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   cp_commit();
   cp_wait_all();
+#if HOM_3D_BULK
+  tile_bulk_wait(A, &ybar);
+#endif
   __syncthreads();
   if (FWD) fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);
   else fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);
+#if HOM_3D_BULK
+  tile_bulk_store<N>(out, NP, s);
+#else
   for (int i = threadIdx.x; i < N * NP; i += kT3) out[i] = s[(i / NP) * SP + i % NP];
+#endif
   if (threadIdx.x == 0) {
     const int ntk = t.kx0 + 1 < c.H ? 2 : 1;
     atomicAdd(A.bytes + (FWD ? HOM_K_YFWD : HOM_K_YINV), (unsigned long long)(2 * (size_t)N * ntk * NP * sizeof(float2)));
@@ -522,14 +584,22 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   const size_t b0 = idx3(c, N, t.load, p, 0, py);
   float2* tws = reinterpret_cast<float2*>(s + N * SP);
   float* sx = reinterpret_cast<float*>(s + N * SP + (N + 1) / 2);
+#if HOM_3D_GREEN_BULK
+  __shared__ __align__(8) unsigned long long gbar;
+  tile_bulk_load<N>(A, s, st + b0, zs, &gbar);
+#else
   for (int i = threadIdx.x; i < N * NP; i += kT3) {
     const int zz = i / NP, k = i - zz * NP;
     cp16(s + zz * SP + k, st + b0 + zz * zs + k);
   }
+#endif
   for (int i = threadIdx.x; i < (N + 1) / 2; i += kT3) cp16(tws + 2 * i, fp.tw2 + 2 * i);
   for (int i = threadIdx.x; i < (N + 3) / 4; i += kT3) cp16(sx + 4 * i, fp.xipos + 4 * i);
   cp_commit();
   cp_wait_all();
+#if HOM_3D_GREEN_BULK
+  tile_bulk_wait(A, &gbar);
+#endif
   __syncthreads();
   fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);  // forward: bin kz at position perm(kz)
 
@@ -546,10 +616,14 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
       A.partE[blockIdx.x] = tot[2];
     }
     fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: natural z order
+#if HOM_3D_GREEN_BULK
+    tile_bulk_store<N>(st + b0, zs, s);
+#else
     for (int i = threadIdx.x; i < N * NP; i += kT3) {
       const int zz = i / NP, k = i - zz * NP;
       st[b0 + zz * zs + k] = s[zz * SP + k];
     }
+#endif
     if (threadIdx.x == 0) {
       const int ntk = hasB ? 2 : 1;
       atomicAdd(A.bytes + HOM_K_GREEN, (unsigned long long)(4 * (size_t)N * ntk * NP * sizeof(float2)));
@@ -674,10 +748,14 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
     }
   }
   fft_dit_p<NP, N, false, float2, SP, kT3>(s, tws);  // inverse: natural z order
+#if HOM_3D_GREEN_BULK
+  tile_bulk_store<N>(st + b0, zs, s);
+#else
   for (int i = threadIdx.x; i < N * NP; i += kT3) {
     const int zz = i / NP, k = i - zz * NP;
     st[b0 + zz * zs + k] = s[zz * SP + k];
   }
+#endif
   if (threadIdx.x == 0) {
     const int ntk = hasB ? 2 : 1;
     atomicAdd(A.bytes + HOM_K_GREEN,
