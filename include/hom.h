@@ -168,14 +168,16 @@ typedef struct hom_solve_opts {
   int32_t max_iter;       /* maximum number of Green-operator applications              */
   int32_t check_every;    /* iterations launched between host polls (>= 1; 0 = default) */
   int32_t diverge_window; /* consecutive error increases that flag divergence (0 = off)  */
-  int32_t use_graph;      /* 1: replay each poll interval as a captured CUDA graph       */
+  int32_t use_graph;      /* 1: the whole solve as one launch of a cached CUDA graph (see  */
+                          /* hom_solve); ignored when stats are requested                 */
   int32_t passes;         /* HOM_PASSES_AUTO or HOM_PASSES_GENERIC                       */
   int32_t max_radix;      /* largest register radix of the generic FP32 FFT stages: 15, 27 or
                              45 (0 = 27; FP64 always uses 15)                             */
   int32_t green;          /* HOM_GREEN_CONTINUOUS or HOM_GREEN_ROTATED (generic passes;   */
                           /* not with hom_solve_cg)                                       */
-  int32_t tune;           /* 1: autotune the FFT plan of FP32 solves with passes = AUTO and */
-                          /* max_radix = 0 (see hom_autotune_report); 0: fixed defaults   */
+  int32_t tune;           /* 1: autotune the passes and FFT plan of FP32 solves with passes */
+                          /* = AUTO and max_radix = 0, per batch shape and scheme (see     */
+                          /* hom_autotune_report); 0: fixed defaults                       */
   int32_t stall_window;   /* > 0: stop a load case whose error has not reached a new minimum */
                           /* for this many iterations (HOM_STATUS_STALLED: FP32 rounding  */
                           /* floor above tol); 0 = off                                    */
