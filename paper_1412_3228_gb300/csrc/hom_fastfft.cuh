@@ -90,14 +90,26 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned
                : "memory");
 }
 // Waits for phase `parity` of the barrier to complete, at most `budget` polls; false if it ran out.
+// HOM_MBAR_SUSPEND_NS > 0 lets each poll suspend the thread up to that many nanoseconds.
+#ifndef HOM_MBAR_SUSPEND_NS
+#define HOM_MBAR_SUSPEND_NS 0
+#endif
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int budget) {
   for (int i = 0; i < budget; ++i) {
     unsigned done;
+#if HOM_MBAR_SUSPEND_NS > 0
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"((unsigned)HOM_MBAR_SUSPEND_NS)
+        : "memory");
+#else
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
+#endif
     if (done) return true;
   }
   return false;
