@@ -53,6 +53,9 @@ namespace {
 #ifndef HOM_GREEN_BULK
 #define HOM_GREEN_BULK 1  // Green pass: its contiguous tile in and out by one bulk copy each (TMA unit)
 #endif
+#ifndef HOM_GREEN_GPF
+#define HOM_GREEN_GPF 1  // Green pass: L2 prefetch of the task's own g (or u_hat) block before its forward FFT
+#endif
 #ifndef HOM_GREEN_PREFETCH
 #define HOM_GREEN_PREFETCH 0  // Green pass: L2 prefetch of the task that starts next
 #endif
@@ -657,6 +660,18 @@ __device__ __forceinline__ void green_body(const SolveArgs& A, int task, const T
   if (threadIdx.x == 0) mbar_inval(&tile_bar);
 #endif
   __syncthreads();
+#if HOM_GREEN_GPF
+  // the private state of this column pair (contiguous: N positions x 2 or 3 float4) -> L2, so that
+  // its reads after the transform hit L2
+  if (threadIdx.x < 32) {
+    const size_t per = EM ? 3 : 2;
+    const char* gsrc = reinterpret_cast<const char*>(static_cast<const float4*>(A.g) +
+                                                     (c.g_off + ((size_t)t.load * (Hp / 2) + (size_t)(kx0 / 2)) * N * 2 * per) / 2);
+    const unsigned bytes = (unsigned)(N * per * sizeof(float4));
+    constexpr unsigned kPiece = 4096;
+    for (unsigned o = threadIdx.x * kPiece; o < bytes; o += 32 * kPiece) prefetch_l2(gsrc + o, min(kPiece, bytes - o));
+  }
+#endif
   fft_dif_p<NP, N, true>(s, tws);  // forward: bin ky at position perm(ky)
 
   if constexpr (EM) {

@@ -417,6 +417,9 @@ __global__ void __launch_bounds__(kT3, kMinB3) k_row_f3d(SolveArgs A, int ntasks
 #ifndef HOM_3D_BULK
 #define HOM_3D_BULK 1  // y passes: the tile in and out by bulk copies of one position each
 #endif
+#ifndef HOM_3D_GREEN_GPF
+#define HOM_3D_GREEN_GPF 1  // Green pass: L2 prefetch of the task's own g (or u_hat) block before its forward FFT
+#endif
 #ifndef HOM_3D_GREEN_BULK
 #define HOM_3D_GREEN_BULK 0  // the same for the Green pass, whose positions are a z plane apart in HBM
 #endif
@@ -601,6 +604,17 @@ __device__ __forceinline__ void green3_body(const SolveArgs& A, const TaskL& t, 
   tile_bulk_wait(A, &gbar);
 #endif
   __syncthreads();
+#if HOM_3D_GREEN_GPF
+  // the private state of this (kx pair, ky) (contiguous: N positions x 3 or 6 float4) -> L2
+  if (threadIdx.x < 32) {
+    const size_t per = EM ? 6 : 3;
+    const char* gsrc = reinterpret_cast<const char*>(
+        static_cast<const float4*>(A.g) + (c.g_off + (((size_t)t.load * (c.Hp / 2) + p) * N + py) * (size_t)N * 2 * per) / 2);
+    const unsigned bytes = (unsigned)(N * per * sizeof(float4));
+    constexpr unsigned kPiece = 4096;
+    for (unsigned o = threadIdx.x * kPiece; o < bytes; o += 32 * kPiece) prefetch_l2(gsrc + o, min(kPiece, bytes - o));
+  }
+#endif
   fft_dif_p<NP, N, true, float2, SP, kT3>(s, tws);  // forward: bin kz at position perm(kz)
 
   if constexpr (EM) {
