@@ -126,7 +126,7 @@ def measured_peak_hbm():
 # --set full capture of the profile case (--profile-case: two 1215^2 cells x 3 loads; traffic grows
 # with the tiles processed, so a launch's traffic is this ratio times its bytes).
 # Valid for the kernels as captured there; None for kernels without a capture.
-TRAFFIC_RATIO = {"row": (110.238 + 52.541) / 215.77, "green": (177.531 + 116.245) / 354.61}
+TRAFFIC_RATIO = {"row": (110.233 + 52.886) / 215.77, "green": (177.580 + 116.155) / 354.61}
 
 
 def golden_ceff():
