@@ -125,3 +125,12 @@ def test_basic_scheme_iterates_are_compatible():
     em = O.solve_em(fb["ctilde"], 2, 15, l0, m0, E, tol=1e-8, max_iter=2000)
     for i in range(3):
         assert em["errors_c"][i][-1] < 1e-8 and em["errors_c"][i][0] > 1e-4
+
+
+def test_em_reference_media_agree():
+    """The input generators' reference medium for the scheme and the oracle's are the same
+    geometric means (written independently on each side)."""
+    for contrast in (0.01, 10.0, 1e3):
+        ph = H.two_phases(contrast)
+        for dim in (2, 3):
+            np.testing.assert_allclose(H.geometric_lame(ph, dim), O.em_reference(ph, dim), rtol=1e-14)
