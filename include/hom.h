@@ -359,6 +359,9 @@ int hom_solve_backward(const hom_cell* cells, int32_t ncells, const hom_material
  * takes 195 MB and does not); FP64 needs twice that, 3D cells n times more.
  *   - opts->use_graph must be 0 and out->stats must be NULL (both would allocate);
  *     HOM_ERR_INVALID_ARG otherwise.  Outputs in host memory are staged through the same array.
+ *   - The basic scheme only, from eps = E: opts->scheme = HOM_SCHEME_EYRE_MILTON, opts->warm_start
+ *     and opts->refine return HOM_ERR_NOT_IMPL.  A host out->history is staged through the array
+ *     too (it counts towards the 64 MiB).
  *   - Every call looks up the array's device address in the current context
  *     (cudaGetSymbolAddress); the first call on a device may load the library's device code, so
  *     make it outside any stream capture.
