@@ -134,3 +134,19 @@ def test_em_reference_media_agree():
         ph = H.two_phases(contrast)
         for dim in (2, 3):
             np.testing.assert_allclose(H.geometric_lame(ph, dim), O.em_reference(ph, dim), rtol=1e-14)
+
+
+def test_em_on_an_even_grid_reaches_the_cg_solution():
+    """Even grids (the Nyquist convention: Gamma0 left out at bins with a Nyquist component): the
+    scheme's fixed point has zero Nyquist strain, so it is the same discrete solution as conjugate
+    gradients on the projected equilibrium equation."""
+    n = 16
+    ct, ph = _disk(n, 10.0, H.RULE_TWO_LAYER)
+    l0, m0 = O.em_reference(ph, 2)
+    r = O.solve_em(ct, 2, n, l0, m0, np.eye(3), tol=1e-11, max_iter=3000)
+    assert all(s == "converged" for s in r["status"])
+    rc = O.solve_cg(ct, 2, n, np.eye(3), tol=1e-11, max_iter=3000)
+    np.testing.assert_allclose(r["mean_sigma"], rc["mean_sigma"], rtol=0, atol=1e-9 * np.abs(rc["mean_sigma"]).max())
+    np.testing.assert_allclose(r["eps"], rc["eps"], rtol=0, atol=1e-8 * np.abs(rc["eps"]).max())
+    eps_hat = np.fft.fft2(r["eps"])
+    assert np.abs(eps_hat[:, :, n // 2, :]).max() < 1e-8 * n * n and np.abs(eps_hat[:, :, :, n // 2]).max() < 1e-8 * n * n
